@@ -1,0 +1,120 @@
+"""Seeded synthetic shape-matching instances.
+
+Each instance is a pair of meshes X, Y (Y a deformed, relabelled copy of X),
+per-vertex FP32 features F_X, F_Y (Y's = X's permuted by the relabelling plus
+Gaussian noise), the ground-truth vertex map and the candidate rule
+parameters. They stand in for the paper's learned URSSM features on FAUST_r /
+SMAL / DT4D-H pairs (Sec. 4), which are not available here.
+
+Nothing in this module computes any part of the matching method: costs,
+candidates, product space, constraints and the solver are implemented twice,
+independently, by ``oracle/`` and by the CUDA path, from these raw arrays.
+
+Workloads (seed = config index XOR pair index):
+
+* ``config1``  icosahedron vs relabelled copy + N(0, 0.01^2) vertex noise,
+  16-d features, noise 0.05, full product space, 200 dual iterations.
+* ``config2``  icosphere subdivision 2 (162 V / 320 T), smooth radial
+  spherical-harmonic deformation (8 terms, degree <= 4, amplitude 0.1),
+  relabelled, 64-d features, noise 0.05, top-k = 10, 500 iterations.
+* ``config3``  icosphere subdivision 4 (2562 V / 5120 T), same deformation,
+  128-d features, top-k = 16, run to a converged bound.
+* ``config4``  64 uneven pairs (icospheres 80/320/1280 T, tori 96..1536 T),
+  64-d features, top-k ~ U{8..24}, 300 iterations each.
+* ``tet``      tetrahedron vs relabelled copy (exhaustive-search size).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import meshes as M
+
+
+@dataclass
+class Instance:
+    name: str
+    X: M.Mesh
+    Y: M.Mesh
+    FX: np.ndarray  # (nvX, D) float32
+    FY: np.ndarray  # (nvY, D) float32
+    perm: np.ndarray  # ground truth: X vertex v <-> Y vertex perm[v]
+    topk: int | None  # None = full product space
+    iters: int | None  # None = run until converged
+    meta: dict = field(default_factory=dict)
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def make_pair(X: M.Mesh, rng: np.random.Generator, dim: int, feat_noise: float,
+              vertex_noise: float = 0.0, deform: bool = False) -> tuple[M.Mesh, np.ndarray, np.ndarray, np.ndarray]:
+    Y0 = M.deform_radial(X, rng) if deform else X.copy()
+    if vertex_noise > 0:
+        Y0 = M.Mesh((Y0.V + vertex_noise * rng.standard_normal(Y0.V.shape)).astype(np.float32), Y0.T)
+    Y, perm = M.relabel(Y0, rng)
+    FX = rng.standard_normal((X.nv, dim)).astype(np.float32)
+    FY = np.empty_like(FX)
+    FY[perm] = FX + (feat_noise * rng.standard_normal(FX.shape)).astype(np.float32)
+    return Y, FX, FY, perm
+
+
+def tet(seed: int = 0, feat_noise: float = 0.05, dim: int = 16) -> Instance:
+    rng = _rng(1000 + seed)
+    X = M.tetrahedron()
+    Y, FX, FY, perm = make_pair(X, rng, dim, feat_noise)
+    return Instance("tet", X, Y, FX, FY, perm, None, 200)
+
+
+def config1(pair: int = 0) -> Instance:
+    rng = _rng(1 ^ pair)
+    X = M.icosahedron()
+    Y, FX, FY, perm = make_pair(X, rng, 16, 0.05, vertex_noise=0.01)
+    return Instance("icosahedron-20T-full", X, Y, FX, FY, perm, None, 200)
+
+
+def config2(pair: int = 0) -> Instance:
+    rng = _rng(2 ^ pair)
+    X = M.icosphere(2)
+    Y, FX, FY, perm = make_pair(X, rng, 64, 0.05, deform=True)
+    return Instance("icosphere2-320T-top10", X, Y, FX, FY, perm, 10, 500)
+
+
+def config3(pair: int = 0) -> Instance:
+    rng = _rng(3 ^ pair)
+    X = M.icosphere(4)
+    Y, FX, FY, perm = make_pair(X, rng, 128, 0.05, deform=True)
+    return Instance("icosphere4-5120T-top16", X, Y, FX, FY, perm, 16, None)
+
+
+def icosphere_pair(subdiv: int, dim: int, topk: int | None, seed: int, iters: int | None = None) -> Instance:
+    """A generic deformed/relabelled icosphere pair (used for scaled variants)."""
+    rng = _rng(seed)
+    X = M.icosphere(subdiv)
+    Y, FX, FY, perm = make_pair(X, rng, dim, 0.05, deform=True)
+    return Instance(f"icosphere{subdiv}-{X.nt}T-top{topk}", X, Y, FX, FY, perm, topk, iters)
+
+
+def config4(n_pairs: int = 64) -> list[Instance]:
+    out = []
+    for p in range(n_pairs):
+        rng = _rng(4 ^ p)
+        if rng.random() < 0.5:
+            X = M.icosphere(int(rng.integers(1, 4)))
+        else:
+            # tori with 96..1536 triangles: 2*n*m in that range, n, m >= 4
+            while True:
+                n = int(rng.integers(4, 40))
+                m = int(rng.integers(4, 40))
+                if 96 <= 2 * n * m <= 1536:
+                    break
+            X = M.torus(n, m)
+        Y, FX, FY, perm = make_pair(X, rng, 64, 0.05, deform=True)
+        k = int(rng.integers(8, 25))
+        out.append(Instance(f"batch{p}-{X.nt}T-top{k}", X, Y, FX, FY, perm, k, 300))
+    return out
+
+
+CONFIGS = {"config1": config1, "config2": config2, "config3": config3, "tet": tet}
