@@ -1,0 +1,326 @@
+"""Benchmark of the DiscoMatch dual / primal hot path on one GB300 (or N replicas).
+
+A step = the whole hot path on one synthetic shape pair: pair costs and top-k candidate
+mask on the device, host compilation of ILP (P) into BDDs and upload, dual iterations
+until the lower bound moves less than 1e-6 (relative) over 20 iterations, rounding to a
+feasible matching. Inputs (features) are resident in HBM when the timed region starts.
+
+Prints one JSON line: value = BDD node-updates per second over the whole step (one
+node-update = one node processed in one half-pass), e2e = the same through the C ABI
+with host buffers (features copied in, matching copied out, inside the timed region),
+roofline of the dominant kernel (the half-pass kernels), a CPU baseline (the FP64
+oracle on host cores) and sampled clocks.
+
+--impl reference times the FP64 oracle itself (the reference arm of this project).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BDD node-updates/s (whole step: costs, candidates, build, dual to converged bound, rounding)"
+UNIT = "node-updates/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self):
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", dev, f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def flush_l2(torch, buf):
+    buf.add_(1.0)  # 256 MB write, larger than the 129 MB L2
+
+
+def workload(name):
+    from synth import instances as I
+
+    if name == "config3":
+        return I.config3()
+    if name == "config2":
+        return I.config2()
+    if name == "config1":
+        return I.config1()
+    raise ValueError(name)
+
+
+def gpu_arm(args):
+    import torch
+
+    from paper_2310_08230_gb300 import _lib as L
+    from paper_2310_08230_gb300.api import _mesh, default_opts
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    lib = L.lib()
+    inst = workload(args.config)
+    stream = torch.cuda.Stream()
+    sptr = int(stream.cuda_stream)
+    FX_h = np.ascontiguousarray(inst.FX)
+    FY_h = np.ascontiguousarray(inst.FY)
+    FX_pin = torch.from_numpy(FX_h).pin_memory()
+    FY_pin = torch.from_numpy(FY_h).pin_memory()
+    FX = FX_pin.cuda()
+    FY = FY_pin.cuda()
+    nvx, nvy, dim = inst.X.nv, inst.Y.nv, inst.FX.shape[1]
+    d = torch.empty((nvx, nvy), dtype=torch.float32, device="cuda")
+    allowed = torch.empty((nvx, nvy), dtype=torch.uint8, device="cuda")
+    mx, tx = _mesh(inst.X.T, nvx)
+    my, ty = _mesh(inst.Y.T, nvy)
+    opts = default_opts(stream=sptr, lb_every=20, conv_rel_tol=1e-6, split_chunk=args.split_chunk)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    max_iters = args.max_iters
+
+    def step(e2e: bool, stats: dict):
+        with torch.cuda.stream(stream):
+            if e2e:
+                FX.copy_(FX_pin, non_blocking=True)
+                FY.copy_(FY_pin, non_blocking=True)
+        L.check(lib.disco_pair_costs(FX.data_ptr(), FY.data_ptr(), nvx, nvy, dim, d.data_ptr(), sptr), "pair_costs")
+        L.check(lib.disco_candidates(d.data_ptr(), nvx, nvy, inst.topk, ctypes.byref(mx), ctypes.byref(my),
+                                     allowed.data_ptr(), sptr), "candidates")
+        h = ctypes.c_void_p()
+        L.check(lib.disco_build(ctypes.byref(mx), ctypes.byref(my), d.data_ptr(), allowed.data_ptr(),
+                                ctypes.byref(opts), ctypes.byref(h)), "build")
+        info = L.disco_info_t()
+        lib.disco_info(h, ctypes.byref(info))
+        # dual to a converged bound: blocks of lb_every iterations, half-pass time on events
+        lb_prev = ctypes.c_double()
+        L.check(lib.disco_lower_bound(h, ctypes.byref(lb_prev)), "lb")
+        lb = ctypes.c_double()
+        iters, dual_ms = 0, 0.0
+        t_dual0 = time.perf_counter()
+        while iters < max_iters:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L.check(lib.disco_dual(h, 20), "dual")
+            e1.record(stream)
+            L.check(lib.disco_lower_bound(h, ctypes.byref(lb)), "lb")
+            dual_ms += e0.elapsed_time(e1)
+            iters += 20
+            if abs(lb.value - lb_prev.value) < 1e-6 * abs(lb.value):
+                break
+            lb_prev.value = lb.value
+        t_conv = (time.perf_counter() - t_dual0) * 1e3
+        x = np.zeros(info.nvars, np.uint8)
+        cost = ctypes.c_double()
+        rc = lib.disco_primal(h, x.ctypes.data, info.nvars, ctypes.byref(cost))
+        lib.disco_info(h, ctypes.byref(info))
+        stats.update(nnodes=info.nnodes, nslots=info.nslots, nvars_free=info.nvars_free, nvars=info.nvars,
+                     iters=info.iterations, conv_iters=iters, lb=lb.value, primal=cost.value, primal_ok=rc == 0,
+                     dual_ms=dual_ms, conv_ms=t_conv, build_ms=info.build_ms, bytes_per_iter=info.bytes_per_iter,
+                     ntiles=info.ntiles, max_layers=info.max_layers)
+        lib.disco_free(h)
+        return x
+
+    def timed(e2e: bool):
+        stats = {}
+        flush_l2(torch, flush)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        step(e2e, stats)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1), stats
+
+    for _ in range(args.warmup):
+        timed(False)
+    times, stats_all = [], []
+    with Clocks() as clk:
+        for _ in range(args.steps):
+            t, st = timed(False)
+            times.append(t)
+            stats_all.append(st)
+    e2e_times = [timed(True)[0] for _ in range(max(1, min(args.steps, 3)))]
+    ms = float(np.mean(times))
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    st = stats_all[-1]
+    updates = 2.0 * st["nnodes"] * st["iters"]
+    value = updates * world / (ms / 1e3)
+    e2e_ms = float(np.mean(e2e_times))
+    half_pass_ms = st["dual_ms"] / (2 * st["conv_iters"])
+    alg_bytes = st["bytes_per_iter"] / 2.0
+    peak, kind = _peaks()
+    achieved = alg_bytes / (half_pass_ms / 1e3) / 1e9
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": inst.name, "nvars": st["nvars"], "nvars_free": st["nvars_free"],
+                   "bdd_slots": st["nslots"], "bdd_nodes": st["nnodes"], "max_layers": st["max_layers"],
+                   "split_chunk": args.split_chunk, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "ms_to_converged_bound": st["conv_ms"], "converged_iters": st["conv_iters"],
+        "dual_node_updates_per_s": 2.0 * st["nnodes"] * st["conv_iters"] / (st["dual_ms"] / 1e3),
+        "build_ms": st["build_ms"], "lower_bound": st["lb"], "primal_cost": st["primal"],
+        "primal_feasible": st["primal_ok"],
+        "rel_gap": (st["primal"] - st["lb"]) / st["primal"] if st["primal"] else None,
+        "e2e": {"value": updates / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(FX_h.nbytes + FY_h.nbytes), "d2h_bytes_per_step": int(st["nvars"]) + 8},
+        "gpu_launches": None,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "half-pass (k_forward/k_backward MMA, all width classes)",
+                     "alg_bytes_per_launch": alg_bytes, "launch_ms": half_pass_ms, "peak_kind": kind},
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(seconds: float) -> dict:
+    """FP64 oracle half-passes on host cores: node-updates/s on a bounded sample."""
+    from oracle import bdd as B
+    from oracle import problem as P
+    from oracle import solver as S
+    from synth import instances as I
+
+    inst = I.config2()
+    prob, d, allowed = P.make_problem(inst)
+    fixed, const = P.presolve(prob)
+    dec = B.decompose(prob, fixed, const, 0)
+    o = S.DualOracle(dec)
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < seconds:
+        o.iterate(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": 2.0 * dec.n_nodes * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{inst.name}: {n} FP64 deferred-MMA iterations ({dec.n_nodes} nodes) in {dt:.1f} s, "
+                      "single-threaded C core"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import bdd as B
+    from oracle import problem as P
+    from oracle import solver as S
+    from synth import instances as I
+
+    inst = I.config2()
+    prob, d, allowed = P.make_problem(inst)
+    fixed, const = P.presolve(prob)
+    dec = B.decompose(prob, fixed, const, 0)
+    o = S.DualOracle(dec)
+    iters = 10
+    for _ in range(args.warmup):
+        o.iterate(1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.iterate(iters)
+        times.append((time.perf_counter() - t0) * 1e3)
+    ms = float(np.mean(times))
+    value = 2.0 * dec.n_nodes * iters / (ms / 1e3)
+    sample = f"{inst.name}: {iters} FP64 deferred-MMA iterations per step ({dec.n_nodes} nodes), single-threaded"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": {"workload": inst.name, "bdd_nodes": int(dec.n_nodes)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--config", default="config3")
+    ap.add_argument("--split-chunk", type=int, default=0)
+    ap.add_argument("--max-iters", type=int, default=20000)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        import __graft_entry__
+
+        __graft_entry__.build()
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

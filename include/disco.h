@@ -1,0 +1,197 @@
+/*
+ * disco.h - C ABI of the GB300 (sm_103a) DiscoMatch dual / primal solver.
+ *
+ * Problem (Sec. 3.1, Eq. P): match two closed, consistently oriented triangle meshes X and
+ * Y by a binary ILP over product triangles ("matching elements": triangle-triangle,
+ * triangle-edge, triangle-vertex), min c^T x s.t. closedness rows A^d x = 0 and projection
+ * rows A^X x = 1, A^Y x = 1. Each row becomes a BDD (Sec. 3.2, App. A.3); the solver runs
+ * the Lagrange-decomposition dual (Eq. D) by deferred min-marginal averaging on the GPU and
+ * rounds a feasible x from min-marginal signs (App. A.5, Sec. 3 pipeline).
+ *
+ * Conventions for every entry point:
+ *   - Return value: DISCO_OK (0) or a negative DISCO_ERR_*; no exceptions cross the ABI and
+ *     no call aborts the process. disco_strerror() names a code; disco_last_error() gives
+ *     the calling thread's most recent message.
+ *   - Pointers documented "host or device" may be either; the library asks the CUDA driver
+ *     which (cudaPointerGetAttributes) and copies as needed. Pointers documented "device"
+ *     must be device memory of the handle's device. All arrays are dense and row-major.
+ *   - Inputs are caller-owned and only read during the call. Outputs are caller-allocated.
+ *     Device state is owned by the handle and released by disco_free().
+ *   - Work is issued on the handle's stream (disco_opts.stream, a cudaStream_t; 0 = a stream
+ *     the library creates). Calls documented "synchronises" wait for that stream.
+ *   - A handle must not be used from two threads at once.
+ */
+#ifndef DISCO_H
+#define DISCO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DISCO_ABI_VERSION 1
+
+enum {
+    DISCO_OK = 0,
+    DISCO_ERR_INVALID_ARG = -1,   /* bad pointer, size or option */
+    DISCO_ERR_NONMANIFOLD = -2,   /* a mesh is not a closed, consistently oriented 2-manifold */
+    DISCO_ERR_GENUS_MISMATCH = -3,/* Euler characteristics differ: (P) has no solution (Sec. 4) */
+    DISCO_ERR_INFEASIBLE = -4,    /* a row of (P) has no solution after presolve */
+    DISCO_ERR_PRIMAL_FAILED = -5, /* rounding used all its rounds without a feasible x */
+    DISCO_ERR_TIMEOUT = -6,       /* a bounded device or host loop hit its limit */
+    DISCO_ERR_CUDA = -7,          /* a CUDA runtime call failed (message in disco_last_error) */
+    DISCO_ERR_OOM = -8,           /* device or host allocation failed */
+    DISCO_ERR_NOT_READY = -9      /* call order violated (e.g. primal before any dual pass) */
+};
+
+/* A triangle mesh: nv vertices (V: nv*3 float, may be NULL: positions are not used by the
+ * solver) and nt triangles (T: nt*3 int32 vertex indices, counter-clockwise). Host memory. */
+typedef struct {
+    int32_t nv;
+    int32_t nt;
+    const float *V;
+    const int32_t *T;
+} disco_mesh;
+
+/* Solver options; disco_default_opts() fills the defaults given in brackets. */
+typedef struct {
+    float omega;              /* [0.5] damping of the min-marginal averaging step */
+    int32_t split_chunk;      /* [0] App. A.3 splitting: rows longer than this many layers are
+                                 cut into balanced segments; 0 disables */
+    int32_t lb_every;         /* [20] iterations between lower-bound checks in disco_converge */
+    double conv_rel_tol;      /* [1e-6] disco_converge stops when the bound moved less than
+                                 this, relative, over lb_every iterations */
+    int32_t primal_rounds;    /* [100] rounding rounds before DISCO_ERR_PRIMAL_FAILED */
+    int32_t primal_inner_iters; /* [20] dual iterations between rounding rounds */
+    float perturb_delta0;     /* [1e-3] first perturbation of undecided variables */
+    float perturb_growth;     /* [2] perturbation growth per round */
+    float tie_tau;            /* [1e-6] |M| at or below this counts as undecided */
+    int32_t propagate_limit;  /* [10000] max propagation sweeps per rounding round */
+    int32_t device;           /* [0] CUDA device ordinal */
+    void *stream;             /* [NULL] cudaStream_t to issue work on; NULL = own stream */
+    int32_t host_threads;     /* [0] threads for the host compiler; 0 = hardware concurrency */
+    int32_t reserved[7];
+} disco_opts;
+
+typedef struct {
+    int64_t nvars;            /* |P|: matching elements kept by the candidate mask */
+    int64_t nrows;            /* rows of (P) */
+    int64_t nvars_free;       /* variables left after presolve */
+    int64_t nvars_aux;        /* auxiliary variables added by splitting */
+    int64_t nbdds;            /* BDD segments */
+    int64_t nslots;           /* (BDD, variable) pairs = layers over all BDDs */
+    int64_t nnodes;           /* BDD nodes over all layers */
+    int64_t max_layers;       /* longest BDD segment (sequential depth of a half-pass) */
+    int64_t max_width;        /* widest layer */
+    int64_t ntiles;           /* warp tiles of 32 BDD segments */
+    int64_t device_bytes;     /* device memory held by the handle */
+    int64_t iterations;       /* dual iterations run so far */
+    double constant;          /* cost of variables fixed to 1 by presolve */
+    double build_ms;          /* host time of disco_build */
+    int64_t bytes_per_iter;   /* algorithmic bytes of one iteration (two half-passes) */
+    int64_t reserved[5];
+} disco_info_t;
+
+typedef struct disco_handle disco_handle;
+
+/* Fills *opts with the defaults. Returns DISCO_OK, or INVALID_ARG for NULL. */
+int disco_default_opts(disco_opts *opts);
+
+/*
+ * Pair costs (Eq. 2 variant used by the workloads): d[m*nvy + n] = (1/dim) * sum_k
+ * (FX[m,k] - FY[n,k])^2, FP32. FX: nvx*dim, FY: nvy*dim, d: nvx*nvy, all DEVICE pointers.
+ * Asynchronous on `stream` (cudaStream_t, NULL = legacy default stream).
+ */
+int disco_pair_costs(const float *FX, const float *FY, int32_t nvx, int32_t nvy, int32_t dim,
+                     float *d, void *stream);
+
+/*
+ * Candidate mask of the top-k pruned product space (Sec. 4 pruning to neighbourhoods of
+ * vertex matches): allowed[m*nvy + n] = 1 iff n lies in the closed 1-ring (on Y) of one of
+ * the k smallest d[m, .] (ties to the lower index), or m lies in the closed 1-ring (on X)
+ * of one of the k smallest d[., n]. d and allowed are DEVICE pointers; X and Y are host
+ * meshes (only T is read). 1 <= k <= 64. Asynchronous on `stream`.
+ */
+int disco_candidates(const float *d, int32_t nvx, int32_t nvy, int32_t k, const disco_mesh *X,
+                     const disco_mesh *Y, uint8_t *allowed, void *stream);
+
+/*
+ * Builds the problem and the device BDD store (host compiler + one upload):
+ * product space restricted to `allowed` (nvx*nvy uint8, host or device; NULL = full
+ * product space), costs c_p = mean of the three pair costs d (nvx*nvy float, host or
+ * device) normalised by the largest kept c_p, closedness and projection rows, presolve,
+ * BDDs (split per opts->split_chunk), dual initialised at lambda = c / |J_i|.
+ * On success *out receives a new handle. Synchronises. Errors: INVALID_ARG, NONMANIFOLD,
+ * GENUS_MISMATCH, INFEASIBLE, OOM, CUDA.
+ */
+int disco_build(const disco_mesh *X, const disco_mesh *Y, const float *d, const uint8_t *allowed,
+                const disco_opts *opts, disco_handle **out);
+
+/*
+ * Host-only compilation, for inspection (no CUDA call): runs the same compiler as
+ * disco_build on host arrays d and allowed (allowed may be NULL) and fills *info (iterations,
+ * ntiles, device_bytes = 0). Optional outputs, each ignored when NULL or too small:
+ *   slot_var[nslots]   variable of every slot in canonical order: a matching-element id,
+ *                      or nvars + k for the k-th auxiliary variable of splitting;
+ *   slot_width[nslots] node count of every slot's layer;
+ *   fixed[nvars]       presolve: -1 free, 0 or 1 fixed.
+ * Call once with NULL outputs to learn the sizes. Errors as disco_build.
+ */
+int disco_compile_host(const disco_mesh *X, const disco_mesh *Y, const float *d, const uint8_t *allowed,
+                       int32_t split_chunk, disco_info_t *info, int32_t *slot_var, int32_t *slot_width,
+                       int64_t nslots, int8_t *fixed, int64_t nvars);
+
+/* Runs `iters` dual iterations (forward + backward half-pass of deferred min-marginal
+ * averaging, Alg. 1 "MMA"). Asynchronous on the handle's stream. */
+int disco_dual(disco_handle *h, int32_t iters);
+
+/* Lower bound E(lambda + pend) + presolve constant of Eq. D, FP64 sum. Synchronises. */
+int disco_lower_bound(disco_handle *h, double *lb);
+
+/*
+ * Iterates until the lower bound changed by less than opts.conv_rel_tol (relative) over
+ * opts.lb_every iterations, or max_iters iterations. Outputs (host, may be NULL): iterations
+ * run by this call and the final bound. Synchronises. TIMEOUT if max_iters was reached.
+ */
+int disco_converge(disco_handle *h, int32_t max_iters, int32_t *iters_done, double *lb);
+
+/*
+ * Min-marginal differences M^j_i = min_{s_i=1} s^T l~^j - min_{s_i=0} s^T l~^j (App. A.5) on
+ * l~ = lambda + pend, one per slot in canonical order: BDD segments by row of (P) (closedness
+ * rows by product edge, then X-, then Y-projection rows) and segment, layers in order.
+ * out: n >= nslots floats, host or device. Synchronises.
+ */
+int disco_min_marginals(disco_handle *h, float *out, int64_t n);
+
+/*
+ * Rounds a feasible x (min-marginal agreement, propagation, perturbation; Sec. 3 pipeline,
+ * App. A.5). x_out: nvars uint8 (host or device) indexed by canonical matching-element id;
+ * cost (host, may be NULL): c^T x in FP64 on the normalised costs. The dual state continues
+ * from where it is and is modified. Synchronises. PRIMAL_FAILED leaves the best partial x.
+ */
+int disco_primal(disco_handle *h, uint8_t *x_out, int64_t nvars, double *cost);
+
+/* Copies the per-slot dual variables lambda (canonical slot order, host or device floats,
+ * n >= nslots) and the per-variable deferred mean (n_pend >= nvars_free + nvars_aux, may be
+ * NULL) out of / into the handle: checkpoint and warm restart. Synchronises. */
+int disco_get_state(disco_handle *h, float *lam, int64_t n, float *pend, int64_t n_pend);
+int disco_set_state(disco_handle *h, const float *lam, int64_t n, const float *pend, int64_t n_pend);
+
+/* Problem and store statistics. */
+int disco_info(disco_handle *h, disco_info_t *info);
+
+/* Releases the handle (NULL is allowed). */
+void disco_free(disco_handle *h);
+
+/* Static string for a return code. */
+const char *disco_strerror(int code);
+
+/* Most recent error message of the calling thread ("" if none). */
+const char *disco_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DISCO_H */

@@ -1,0 +1,159 @@
+"""NumPy / PyTorch wrapper of the C ABI (argument marshalling only; every step runs in the
+CUDA library).
+
+    d = pair_costs(FX, FY)                       # torch CUDA tensors -> (nvx, nvy) costs
+    allowed = candidates(d, k, TX, TY)           # top-k pruned candidate mask (device)
+    s = Solver(TX, TY, d, allowed)               # host compiler + device BDD store
+    s.dual(200); lb = s.lower_bound()            # deferred min-marginal averaging, Eq. D
+    x, cost = s.primal()                         # feasible matching by rounding
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream_ptr(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _mesh(T: np.ndarray, nv: int):
+    T = np.ascontiguousarray(T, dtype=np.int32)
+    m = L.disco_mesh(int(nv), int(T.shape[0]), None, T.ctypes.data_as(ctypes.c_void_p))
+    return m, T
+
+
+def _ptr(a) -> int:
+    """Data pointer of a NumPy array or a torch tensor (host or device)."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return int(a.data_ptr())
+
+
+def pair_costs(FX, FY, stream=None):
+    """d[m, n] = mean_k (FX[m, k] - FY[n, k])^2 (FP32, CUDA tensors in and out)."""
+    torch = _torch()
+    FX = FX.contiguous().float()
+    FY = FY.contiguous().float()
+    d = torch.empty((FX.shape[0], FY.shape[0]), dtype=torch.float32, device=FX.device)
+    L.check(L.lib().disco_pair_costs(FX.data_ptr(), FY.data_ptr(), FX.shape[0], FY.shape[0], FX.shape[1],
+                                     d.data_ptr(), _stream_ptr(stream)), "disco_pair_costs")
+    return d
+
+
+def candidates(d, k: int, TX: np.ndarray, TY: np.ndarray, stream=None):
+    """Top-k candidate mask widened by closed 1-rings (uint8 CUDA tensor, nvx x nvy)."""
+    torch = _torch()
+    nvx, nvy = int(d.shape[0]), int(d.shape[1])
+    mx, tx = _mesh(TX, nvx)
+    my, ty = _mesh(TY, nvy)
+    allowed = torch.empty((nvx, nvy), dtype=torch.uint8, device=d.device)
+    L.check(L.lib().disco_candidates(d.contiguous().data_ptr(), nvx, nvy, int(k), ctypes.byref(mx), ctypes.byref(my),
+                                     allowed.data_ptr(), _stream_ptr(stream)), "disco_candidates")
+    return allowed
+
+
+def default_opts(**kw) -> L.disco_opts:
+    o = L.disco_opts()
+    L.check(L.lib().disco_default_opts(ctypes.byref(o)), "disco_default_opts")
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """One shape pair: ILP (P) compiled to BDDs and solved by the GPU dual / primal."""
+
+    def __init__(self, TX: np.ndarray, TY: np.ndarray, d, allowed=None, nvx: int | None = None,
+                 nvy: int | None = None, **opts):
+        nvx = int(d.shape[0]) if nvx is None else nvx
+        nvy = int(d.shape[1]) if nvy is None else nvy
+        if isinstance(d, np.ndarray):
+            d = np.ascontiguousarray(d, dtype=np.float32)
+        if isinstance(allowed, np.ndarray):
+            allowed = np.ascontiguousarray(allowed, dtype=np.uint8)
+        mx, self._tx = _mesh(TX, nvx)
+        my, self._ty = _mesh(TY, nvy)
+        self.opts = default_opts(**opts)
+        h = ctypes.c_void_p()
+        L.check(L.lib().disco_build(ctypes.byref(mx), ctypes.byref(my), _ptr(d),
+                                    None if allowed is None else _ptr(allowed), ctypes.byref(self.opts),
+                                    ctypes.byref(h)), "disco_build")
+        self.h = h
+
+    # -------------------------------------------------------------------------------
+    def info(self) -> dict:
+        i = L.disco_info_t()
+        L.check(L.lib().disco_info(self.h, ctypes.byref(i)), "disco_info")
+        return {k: getattr(i, k) for k, _ in i._fields_ if k != "reserved"}
+
+    def dual(self, iters: int) -> None:
+        L.check(L.lib().disco_dual(self.h, int(iters)), "disco_dual")
+
+    def lower_bound(self) -> float:
+        lb = ctypes.c_double()
+        L.check(L.lib().disco_lower_bound(self.h, ctypes.byref(lb)), "disco_lower_bound")
+        return lb.value
+
+    def converge(self, max_iters: int) -> tuple[int, float, bool]:
+        n = ctypes.c_int32()
+        lb = ctypes.c_double()
+        rc = L.lib().disco_converge(self.h, int(max_iters), ctypes.byref(n), ctypes.byref(lb))
+        if rc not in (L.DISCO_OK, L.DISCO_ERR_TIMEOUT):
+            L.check(rc, "disco_converge")
+        return n.value, lb.value, rc == L.DISCO_OK
+
+    def min_marginals(self, out=None) -> np.ndarray:
+        ns = self.info()["nslots"]
+        if out is None:
+            out = np.empty(ns, np.float32)
+        L.check(L.lib().disco_min_marginals(self.h, _ptr(out), int(out.shape[0])), "disco_min_marginals")
+        return out
+
+    def primal(self) -> tuple[np.ndarray, float, bool]:
+        nv = self.info()["nvars"]
+        x = np.zeros(nv, np.uint8)
+        c = ctypes.c_double()
+        rc = L.lib().disco_primal(self.h, x.ctypes.data, nv, ctypes.byref(c))
+        if rc not in (L.DISCO_OK, L.DISCO_ERR_PRIMAL_FAILED):
+            L.check(rc, "disco_primal")
+        return x, c.value, rc == L.DISCO_OK
+
+    def get_state(self) -> tuple[np.ndarray, np.ndarray]:
+        inf = self.info()
+        lam = np.empty(inf["nslots"], np.float32)
+        pend = np.empty(inf["nvars_free"] + inf["nvars_aux"], np.float32)
+        L.check(L.lib().disco_get_state(self.h, lam.ctypes.data, lam.shape[0], pend.ctypes.data, pend.shape[0]),
+                "disco_get_state")
+        return lam, pend
+
+    def set_state(self, lam: np.ndarray, pend: np.ndarray | None = None) -> None:
+        lam = np.ascontiguousarray(lam, np.float32)
+        pp = None if pend is None else np.ascontiguousarray(pend, np.float32)
+        L.check(L.lib().disco_set_state(self.h, lam.ctypes.data, lam.shape[0],
+                                        None if pp is None else pp.ctypes.data, 0 if pp is None else pp.shape[0]),
+                "disco_set_state")
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            L.lib().disco_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

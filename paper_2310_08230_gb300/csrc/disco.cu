@@ -1,0 +1,667 @@
+// C ABI of the solver (include/disco.h): device store, pass scheduling, rounding loop.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/disco.h"
+#include "kernels.h"
+#include "plan.h"
+
+using namespace disco;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define CK(call)                                                                                          \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess)                                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? DISCO_ERR_OOM : DISCO_ERR_CUDA,                 \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                              \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct WidthClass {
+    int W;
+    int tile0, tile_end;
+};
+
+}  // namespace
+
+struct disco_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    disco_opts opts{};
+    Plan plan;
+    std::vector<WidthClass> classes;
+    int64_t ntiles = 0, nslots_tile = 0, nnodes_tile = 0, nint = 0;
+    // device buffers
+    TileInfo* tiles = nullptr;
+    uint32_t* var = nullptr;
+    uint32_t* desc = nullptr;
+    float* lam = nullptr;
+    float* lam_lo = nullptr;
+    float* F = nullptr;
+    float* B = nullptr;
+    float* acc[2] = {nullptr, nullptr};
+    int cur = 0;
+    double* tile_sum = nullptr;
+    double* scalar = nullptr;      // [0] lower bound
+    int64_t* canon_pos = nullptr;  // canonical slot -> tile slot
+    uint8_t* deg = nullptr;
+    uint8_t* state = nullptr;
+    uint8_t* trial = nullptr;
+    uint32_t* reach = nullptr;
+    uint8_t* sup = nullptr;
+    float* mm_var = nullptr;
+    float* mm_slot = nullptr;
+    float* tmp = nullptr;          // nslots floats (canonical-order staging)
+    int* counters = nullptr;
+    int* h_counters = nullptr;     // pinned
+    double* h_scalar = nullptr;    // pinned
+    int64_t device_bytes = 0;
+    int64_t iterations = 0;
+    bool has_b = false;
+    std::vector<void*> allocations;
+    cudaGraphExec_t iter_graph = nullptr;
+
+    template <class T>
+    int alloc(T** p, int64_t n) {
+        size_t bytes = size_t(std::max<int64_t>(n, 1)) * sizeof(T);
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+        if (e != cudaSuccess) return fail(DISCO_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        allocations.push_back(*p);
+        device_bytes += int64_t(bytes);
+        return DISCO_OK;
+    }
+
+    KArgs args(const WidthClass& c) {
+        KArgs a{};
+        a.tiles = tiles;
+        a.tile0 = c.tile0;
+        a.tile_end = c.tile_end;
+        a.var = var;
+        a.desc = desc;
+        a.lam = lam;
+        a.lam_lo = lam_lo;
+        a.F = F;
+        a.B = B;
+        a.acc_in = acc[cur];
+        a.acc_out = acc[cur ^ 1];
+        a.state = state;
+        a.omega = opts.omega;
+        a.mm_slot = mm_slot;
+        a.mm_var = mm_var;
+        a.tile_sum = tile_sum;
+        a.reach = reach;
+        a.sup_var = sup;
+        return a;
+    }
+
+    // One pass over every width class (a half-pass flips the averaging buffers).
+    int pass(Pass p) {
+        for (const WidthClass& c : classes) CK(launch_pass(p, c.W, args(c), stream));
+        if (p == Pass::FwdMMA || p == Pass::BwdMMA || p == Pass::FwdMMARound || p == Pass::BwdMMARound) cur ^= 1;
+        return DISCO_OK;
+    }
+
+    ~disco_handle() {
+        if (iter_graph) cudaGraphExecDestroy(iter_graph);
+        for (void* p : allocations) cudaFree(p);
+        if (h_counters) cudaFreeHost(h_counters);
+        if (h_scalar) cudaFreeHost(h_scalar);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace {
+
+int copy_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+    return DISCO_OK;
+}
+
+// Reads n elements of a host-or-device array into a host vector.
+template <class T>
+int to_host(const T* src, size_t n, std::vector<T>* out) {
+    out->resize(n);
+    if (is_device_ptr(src)) {
+        CK(cudaMemcpy(out->data(), src, n * sizeof(T), cudaMemcpyDeviceToHost));
+    } else {
+        std::memcpy(out->data(), src, n * sizeof(T));
+    }
+    return DISCO_OK;
+}
+
+int width_class(int w) {
+    if (w <= 2) return 2;
+    if (w <= 4) return 4;
+    if (w <= 8) return 8;
+    if (w <= 16) return 16;
+    return 32;
+}
+
+int upload(disco_handle* h) {
+    const Plan& P = h->plan;
+    const int64_t nseg = int64_t(P.segs.size());
+    // ---- tiles: segments grouped by width class, longest first within a class
+    std::vector<int64_t> order(nseg);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        int wa = width_class(P.segs[a].max_width), wb = width_class(P.segs[b].max_width);
+        if (wa != wb) return wa < wb;
+        return P.segs[a].n_layers > P.segs[b].n_layers;
+    });
+    std::vector<TileInfo> tiles;
+    std::vector<std::vector<int64_t>> tile_segs;
+    h->classes.clear();
+    int64_t slot_base = 0, node_base = 0;
+    for (int64_t i = 0; i < nseg;) {
+        const int W = width_class(P.segs[order[i]].max_width);
+        WidthClass wc{W, int(tiles.size()), 0};
+        while (i < nseg && width_class(P.segs[order[i]].max_width) == W) {
+            std::vector<int64_t> ts;
+            for (int k = 0; k < 32 && i < nseg && width_class(P.segs[order[i]].max_width) == W; ++k, ++i) ts.push_back(order[i]);
+            int L = 0;
+            for (int64_t sg : ts) L = std::max(L, P.segs[sg].n_layers);
+            tiles.push_back(TileInfo{slot_base, node_base, L, W});
+            tile_segs.push_back(ts);
+            slot_base += int64_t(L) * 32;
+            node_base += int64_t(L + 1) * W * 32;
+        }
+        wc.tile_end = int(tiles.size());
+        h->classes.push_back(wc);
+    }
+    h->ntiles = int64_t(tiles.size());
+    h->nslots_tile = slot_base;
+    h->nnodes_tile = node_base;
+    h->nint = P.n_free + P.n_aux;
+    const int64_t nslots = int64_t(P.slot_var.size());
+
+    std::vector<uint32_t> hvar(slot_base, kNoVar), hdesc(slot_base, 0);
+    std::vector<float> hlam(slot_base, 0.0f), hlam_lo(slot_base, 0.0f);
+    std::vector<int64_t> canon(nslots);
+    for (size_t t = 0; t < tiles.size(); ++t)
+        for (size_t lane = 0; lane < tile_segs[t].size(); ++lane) {
+            const Segment& sg = P.segs[tile_segs[t][lane]];
+            for (int l = 0; l < sg.n_layers; ++l) {
+                const int64_t pos = tiles[t].slot_base + int64_t(l) * 32 + int64_t(lane);
+                const int64_t c = sg.first_slot + l;
+                hvar[pos] = uint32_t(P.slot_var[c]);
+                hdesc[pos] = P.slot_desc[c];
+                hlam[pos] = P.slot_lam0[c];
+                hlam_lo[pos] = P.slot_lam0_lo[c];
+                canon[c] = pos;
+            }
+        }
+    int rc;
+    if ((rc = h->alloc(&h->tiles, h->ntiles))) return rc;
+    if ((rc = h->alloc(&h->var, slot_base))) return rc;
+    if ((rc = h->alloc(&h->desc, slot_base))) return rc;
+    if ((rc = h->alloc(&h->lam, slot_base))) return rc;
+    if ((rc = h->alloc(&h->lam_lo, slot_base))) return rc;
+    if ((rc = h->alloc(&h->F, node_base))) return rc;
+    if ((rc = h->alloc(&h->B, node_base))) return rc;
+    if ((rc = h->alloc(&h->acc[0], h->nint * kAccStride))) return rc;
+    if ((rc = h->alloc(&h->acc[1], h->nint * kAccStride))) return rc;
+    if ((rc = h->alloc(&h->tile_sum, h->ntiles))) return rc;
+    if ((rc = h->alloc(&h->scalar, 4))) return rc;
+    if ((rc = h->alloc(&h->canon_pos, nslots))) return rc;
+    if ((rc = h->alloc(&h->deg, h->nint))) return rc;
+    if ((rc = h->alloc(&h->state, h->nint))) return rc;
+    if ((rc = h->alloc(&h->trial, h->nint))) return rc;
+    if ((rc = h->alloc(&h->reach, slot_base))) return rc;
+    if ((rc = h->alloc(&h->sup, h->nint * kAccStride))) return rc;
+    if ((rc = h->alloc(&h->mm_var, h->nint * kAccStride))) return rc;
+    if ((rc = h->alloc(&h->mm_slot, slot_base))) return rc;
+    if ((rc = h->alloc(&h->tmp, std::max(nslots, h->nint)))) return rc;
+    if ((rc = h->alloc(&h->counters, 4))) return rc;
+    CK(cudaMallocHost(&h->h_counters, 4 * sizeof(int)));
+    CK(cudaMallocHost(&h->h_scalar, 4 * sizeof(double)));
+    cudaStream_t s = h->stream;
+    if ((rc = copy_in(h->tiles, tiles.data(), tiles.size() * sizeof(TileInfo), s))) return rc;
+    if ((rc = copy_in(h->var, hvar.data(), hvar.size() * 4, s))) return rc;
+    if ((rc = copy_in(h->desc, hdesc.data(), hdesc.size() * 4, s))) return rc;
+    if ((rc = copy_in(h->lam, hlam.data(), hlam.size() * 4, s))) return rc;
+    if ((rc = copy_in(h->lam_lo, hlam_lo.data(), hlam_lo.size() * 4, s))) return rc;
+    if ((rc = copy_in(h->canon_pos, canon.data(), canon.size() * 8, s))) return rc;
+    if ((rc = copy_in(h->deg, P.deg.data(), P.deg.size(), s))) return rc;
+    CK(cudaMemsetAsync(h->F, 0, size_t(node_base) * 4, s));
+    CK(cudaMemsetAsync(h->B, 0, size_t(node_base) * 4, s));
+    CK(cudaMemsetAsync(h->acc[0], 0, size_t(h->nint) * kAccStride * 4, s));
+    CK(cudaMemsetAsync(h->acc[1], 0, size_t(h->nint) * kAccStride * 4, s));
+    CK(cudaMemsetAsync(h->state, 0, size_t(h->nint), s));
+    CK(cudaStreamSynchronize(s));
+    return DISCO_OK;
+}
+
+// b of every node from the current lambda + pend (under the current fixings).
+int reset_b(disco_handle* h) {
+    int rc = h->pass(Pass::BwdReset);
+    if (rc) return rc;
+    h->has_b = true;
+    return DISCO_OK;
+}
+
+int run_iterations(disco_handle* h, int iters) {
+    int rc;
+    if (!h->has_b && (rc = reset_b(h))) return rc;
+    for (int t = 0; t < iters; ++t) {
+        if ((rc = h->pass(Pass::FwdMMA))) return rc;
+        if ((rc = h->pass(Pass::BwdMMA))) return rc;
+        ++h->iterations;
+    }
+    return DISCO_OK;
+}
+
+int lower_bound(disco_handle* h, double* lb) {
+    int rc = h->pass(Pass::Lb);
+    if (rc) return rc;
+    CK(launch_sum_tiles(h->tile_sum, h->ntiles, h->plan.constant, h->scalar, h->stream));
+    CK(cudaMemcpyAsync(h->h_scalar, h->scalar, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *lb = h->h_scalar[0];
+    return DISCO_OK;
+}
+
+int check_handle(disco_handle* h) {
+    if (!h) return fail(DISCO_ERR_INVALID_ARG, "null handle");
+    CK(cudaSetDevice(h->device));
+    return DISCO_OK;
+}
+
+int write_out(void* dst, const void* dev_src, size_t bytes, cudaStream_t s) {
+    CK(cudaMemcpyAsync(dst, dev_src, bytes, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+    return DISCO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int disco_default_opts(disco_opts* o) {
+    if (!o) return fail(DISCO_ERR_INVALID_ARG, "null opts");
+    std::memset(o, 0, sizeof(*o));
+    o->omega = 0.5f;
+    o->split_chunk = 0;
+    o->lb_every = 20;
+    o->conv_rel_tol = 1e-6;
+    o->primal_rounds = 100;
+    o->primal_inner_iters = 20;
+    o->perturb_delta0 = 1e-3f;
+    o->perturb_growth = 2.0f;
+    o->tie_tau = 1e-6f;
+    o->propagate_limit = 10000;
+    o->device = 0;
+    o->stream = nullptr;
+    o->host_threads = 0;
+    return DISCO_OK;
+}
+
+const char* disco_strerror(int code) {
+    switch (code) {
+        case DISCO_OK: return "ok";
+        case DISCO_ERR_INVALID_ARG: return "invalid argument";
+        case DISCO_ERR_NONMANIFOLD: return "mesh is not a closed, consistently oriented 2-manifold";
+        case DISCO_ERR_GENUS_MISMATCH: return "meshes have different genus";
+        case DISCO_ERR_INFEASIBLE: return "problem is infeasible";
+        case DISCO_ERR_PRIMAL_FAILED: return "rounding did not reach a feasible solution";
+        case DISCO_ERR_TIMEOUT: return "iteration limit reached";
+        case DISCO_ERR_CUDA: return "CUDA error";
+        case DISCO_ERR_OOM: return "out of memory";
+        case DISCO_ERR_NOT_READY: return "call order violated";
+        default: return "unknown error";
+    }
+}
+
+const char* disco_last_error(void) { return g_last_error.c_str(); }
+
+int disco_pair_costs(const float* FX, const float* FY, int32_t nvx, int32_t nvy, int32_t dim, float* d, void* stream) {
+    if (!FX || !FY || !d || nvx <= 0 || nvy <= 0 || dim <= 0) return fail(DISCO_ERR_INVALID_ARG, "pair_costs: bad arguments");
+    if (!is_device_ptr(FX) || !is_device_ptr(FY) || !is_device_ptr(d))
+        return fail(DISCO_ERR_INVALID_ARG, "pair_costs: FX, FY and d must be device pointers");
+    CK(launch_pair_costs(FX, FY, nvx, nvy, dim, d, static_cast<cudaStream_t>(stream)));
+    return DISCO_OK;
+}
+
+int disco_candidates(const float* d, int32_t nvx, int32_t nvy, int32_t k, const disco_mesh* X, const disco_mesh* Y,
+                     uint8_t* allowed, void* stream) {
+    if (!d || !allowed || !X || !Y || !X->T || !Y->T || nvx != X->nv || nvy != Y->nv || k < 1 || k > 64 || k > nvx ||
+        k > nvy)
+        return fail(DISCO_ERR_INVALID_ARG, "candidates: bad arguments");
+    if (!is_device_ptr(d) || !is_device_ptr(allowed))
+        return fail(DISCO_ERR_INVALID_ARG, "candidates: d and allowed must be device pointers");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // closed 1-rings as CSR (host -> device)
+    auto rings = [](const disco_mesh* m, std::vector<int32_t>* ptr, std::vector<int32_t>* ring) {
+        std::vector<std::vector<int32_t>> nb(m->nv);
+        for (int v = 0; v < m->nv; ++v) nb[v].push_back(v);
+        for (int t = 0; t < m->nt; ++t)
+            for (int c = 0; c < 3; ++c) {
+                int a = m->T[3 * t + c], b = m->T[3 * t + (c + 1) % 3];
+                if (a < 0 || b < 0 || a >= m->nv || b >= m->nv) return false;
+                nb[a].push_back(b);
+                nb[b].push_back(a);
+            }
+        ptr->assign(1, 0);
+        for (auto& x : nb) {
+            std::sort(x.begin(), x.end());
+            x.erase(std::unique(x.begin(), x.end()), x.end());
+            ring->insert(ring->end(), x.begin(), x.end());
+            ptr->push_back(int32_t(ring->size()));
+        }
+        return true;
+    };
+    std::vector<int32_t> px, rx, py, ry;
+    if (!rings(X, &px, &rx) || !rings(Y, &py, &ry)) return fail(DISCO_ERR_INVALID_ARG, "candidates: bad mesh");
+    int32_t *dpx, *drx, *dpy, *dry, *tk;
+    float* dT;
+    CK(cudaMallocAsync(&dpx, px.size() * 4, s));
+    CK(cudaMallocAsync(&drx, rx.size() * 4, s));
+    CK(cudaMallocAsync(&dpy, py.size() * 4, s));
+    CK(cudaMallocAsync(&dry, ry.size() * 4, s));
+    CK(cudaMallocAsync(&tk, size_t(std::max(nvx, nvy)) * k * 4, s));
+    CK(cudaMallocAsync(&dT, size_t(nvx) * nvy * 4, s));
+    CK(cudaMemcpyAsync(dpx, px.data(), px.size() * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(drx, rx.data(), rx.size() * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dpy, py.data(), py.size() * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dry, ry.data(), ry.size() * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(allowed, 0, size_t(nvx) * nvy, s));
+    CK(launch_topk_rows(d, nvx, nvy, k, tk, s));
+    CK(launch_dilate(tk, nvx, k, dpy, dry, nvy, false, allowed, s));
+    CK(launch_transpose(d, nvx, nvy, dT, s));
+    CK(launch_topk_rows(dT, nvy, nvx, k, tk, s));
+    CK(launch_dilate(tk, nvy, k, dpx, drx, nvy, true, allowed, s));
+    CK(cudaFreeAsync(dpx, s));
+    CK(cudaFreeAsync(drx, s));
+    CK(cudaFreeAsync(dpy, s));
+    CK(cudaFreeAsync(dry, s));
+    CK(cudaFreeAsync(tk, s));
+    CK(cudaFreeAsync(dT, s));
+    CK(cudaStreamSynchronize(s));  // the host ring arrays die with this call
+    return DISCO_OK;
+}
+
+int disco_build(const disco_mesh* X, const disco_mesh* Y, const float* d, const uint8_t* allowed, const disco_opts* opts,
+                disco_handle** out) {
+    if (!X || !Y || !d || !out || !X->T || !Y->T) return fail(DISCO_ERR_INVALID_ARG, "build: null argument");
+    *out = nullptr;
+    disco_opts o;
+    if (opts) o = *opts; else disco_default_opts(&o);
+    if (!(o.omega > 0.0f && o.omega <= 1.0f) || o.split_chunk < 0 || o.lb_every < 1)
+        return fail(DISCO_ERR_INVALID_ARG, "build: bad options");
+    std::unique_ptr<disco_handle> h(new disco_handle());
+    h->device = o.device;
+    h->opts = o;
+    CK(cudaSetDevice(o.device));
+    if (o.stream) {
+        h->stream = static_cast<cudaStream_t>(o.stream);
+    } else {
+        CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    const size_t npair = size_t(X->nv) * size_t(Y->nv);
+    std::vector<float> hd;
+    std::vector<uint8_t> ha;
+    int rc;
+    if ((rc = to_host(d, npair, &hd))) return rc;
+    if (allowed && (rc = to_host(allowed, npair, &ha))) return rc;
+    std::string err;
+    rc = build_plan(MeshIn{X->nv, X->nt, X->T}, MeshIn{Y->nv, Y->nt, Y->T}, hd.data(), allowed ? ha.data() : nullptr,
+                    o.split_chunk, o.host_threads, &h->plan, &err);
+    if (rc) return fail(rc, "build: " + err);
+    if ((rc = upload(h.get()))) return rc;
+    *out = h.release();
+    return DISCO_OK;
+}
+
+int disco_compile_host(const disco_mesh* X, const disco_mesh* Y, const float* d, const uint8_t* allowed,
+                       int32_t split_chunk, disco_info_t* info, int32_t* slot_var, int32_t* slot_width, int64_t nslots,
+                       int8_t* fixed, int64_t nvars) {
+    if (!X || !Y || !d || !info || !X->T || !Y->T || split_chunk < 0)
+        return fail(DISCO_ERR_INVALID_ARG, "compile_host: bad arguments");
+    Plan P;
+    std::string err;
+    int rc = build_plan(MeshIn{X->nv, X->nt, X->T}, MeshIn{Y->nv, Y->nt, Y->T}, d, allowed, split_chunk, 0, &P, &err);
+    if (rc) return fail(rc, "compile_host: " + err);
+    std::memset(info, 0, sizeof(*info));
+    info->nvars = P.nvars;
+    info->nrows = P.nrows;
+    info->nvars_free = P.n_free;
+    info->nvars_aux = P.n_aux;
+    info->nbdds = int64_t(P.segs.size());
+    info->nslots = int64_t(P.slot_var.size());
+    info->nnodes = P.n_nodes;
+    info->max_layers = P.max_layers;
+    info->max_width = P.max_width;
+    info->constant = P.constant;
+    info->build_ms = P.build_ms;
+    info->bytes_per_iter = 2 * (8 * P.n_nodes + 20 * info->nslots + 8 * (P.n_free + P.n_aux));
+    if (nslots >= info->nslots) {
+        for (int64_t i = 0; i < info->nslots; ++i) {
+            const int32_t v = P.slot_var[i];
+            if (slot_var) slot_var[i] = v < P.n_free ? P.free_orig[v] : int32_t(P.nvars + (v - P.n_free));
+            if (slot_width) slot_width[i] = int32_t(P.slot_desc[i] & 63u) + 1;
+        }
+    }
+    if (fixed && nvars >= P.nvars) std::memcpy(fixed, P.fixed.data(), size_t(P.nvars));
+    return DISCO_OK;
+}
+
+int disco_dual(disco_handle* h, int32_t iters) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (iters < 0) return fail(DISCO_ERR_INVALID_ARG, "dual: iters < 0");
+    return run_iterations(h, iters);
+}
+
+int disco_lower_bound(disco_handle* h, double* lb) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!lb) return fail(DISCO_ERR_INVALID_ARG, "lower_bound: null output");
+    return lower_bound(h, lb);
+}
+
+int disco_converge(disco_handle* h, int32_t max_iters, int32_t* iters_done, double* lb_out) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (max_iters < 0) return fail(DISCO_ERR_INVALID_ARG, "converge: max_iters < 0");
+    double prev = 0.0, lb = 0.0;
+    if ((rc = lower_bound(h, &prev))) return rc;
+    int done = 0;
+    bool converged = false;
+    while (done < max_iters) {
+        const int n = std::min(h->opts.lb_every, max_iters - done);
+        if ((rc = run_iterations(h, n))) return rc;
+        done += n;
+        if ((rc = lower_bound(h, &lb))) return rc;
+        if (std::fabs(lb - prev) < h->opts.conv_rel_tol * std::max(std::fabs(lb), 1e-300)) {
+            converged = true;
+            break;
+        }
+        prev = lb;
+    }
+    if (done == 0) lb = prev;
+    if (iters_done) *iters_done = done;
+    if (lb_out) *lb_out = lb;
+    return converged || max_iters == 0 ? DISCO_OK : fail(DISCO_ERR_TIMEOUT, "converge: max_iters reached");
+}
+
+int disco_min_marginals(disco_handle* h, float* out, int64_t n) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    const int64_t ns = int64_t(h->plan.slot_var.size());
+    if (!out || n < ns) return fail(DISCO_ERR_INVALID_ARG, "min_marginals: output too small");
+    if ((rc = h->pass(Pass::FwdMM))) return rc;
+    if ((rc = h->pass(Pass::BwdMM))) return rc;
+    CK(launch_gather_f32(h->mm_slot, h->canon_pos, ns, h->tmp, h->stream));
+    return write_out(out, h->tmp, size_t(ns) * 4, h->stream);
+}
+
+int disco_get_state(disco_handle* h, float* lam, int64_t n, float* pend, int64_t n_pend) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    const int64_t ns = int64_t(h->plan.slot_var.size());
+    if (!lam || n < ns || (pend && n_pend < h->nint)) return fail(DISCO_ERR_INVALID_ARG, "get_state: output too small");
+    CK(launch_gather_f32(h->lam, h->canon_pos, ns, h->tmp, h->stream));
+    if ((rc = write_out(lam, h->tmp, size_t(ns) * 4, h->stream))) return rc;
+    if (pend) {
+        CK(launch_pend(h->acc[h->cur], h->deg, h->nint, h->tmp, h->stream));
+        if ((rc = write_out(pend, h->tmp, size_t(h->nint) * 4, h->stream))) return rc;
+    }
+    return DISCO_OK;
+}
+
+int disco_set_state(disco_handle* h, const float* lam, int64_t n, const float* pend, int64_t n_pend) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    const int64_t ns = int64_t(h->plan.slot_var.size());
+    if (!lam || n < ns || (pend && n_pend < h->nint)) return fail(DISCO_ERR_INVALID_ARG, "set_state: input too small");
+    CK(cudaMemcpyAsync(h->tmp, lam, size_t(ns) * 4, cudaMemcpyDefault, h->stream));
+    CK(launch_scatter_f32(h->tmp, h->canon_pos, ns, h->lam, h->stream));
+    CK(cudaMemsetAsync(h->lam_lo, 0, size_t(h->nslots_tile) * 4, h->stream));
+    if (pend) {
+        CK(cudaMemcpyAsync(h->tmp, pend, size_t(h->nint) * 4, cudaMemcpyDefault, h->stream));
+        CK(launch_set_pend(h->tmp, h->deg, h->nint, h->acc[h->cur], h->stream));
+    } else {
+        CK(cudaMemsetAsync(h->acc[h->cur], 0, size_t(h->nint) * kAccStride * 4, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    h->has_b = false;
+    return DISCO_OK;
+}
+
+int disco_primal(disco_handle* h, uint8_t* x_out, int64_t nvars, double* cost) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    const Plan& P = h->plan;
+    if (!x_out || nvars < P.nvars) return fail(DISCO_ERR_INVALID_ARG, "primal: output too small");
+    const disco_opts& o = h->opts;
+    cudaStream_t s = h->stream;
+    const int64_t nint = h->nint;
+    CK(cudaMemsetAsync(h->state, 0, size_t(nint), s));
+    float delta = o.perturb_delta0;
+    bool done = nint == 0;
+    for (int r = 0; r < o.primal_rounds && !done; ++r) {
+        // 1. lambda <- lambda + pend; min-marginals under the fixings
+        CK(launch_flush(h->var, h->desc, h->nslots_tile, h->acc[h->cur], h->lam, h->lam_lo, s));
+        CK(cudaMemsetAsync(h->acc[0], 0, size_t(nint) * kAccStride * 4, s));
+        CK(cudaMemsetAsync(h->acc[1], 0, size_t(nint) * kAccStride * 4, s));
+        if ((rc = h->pass(Pass::FwdMM))) return rc;
+        if ((rc = h->pass(Pass::BwdMM))) return rc;
+        // 2. agreement: every slot strictly positive -> 0, strictly negative -> 1
+        CK(launch_decide(h->mm_var, h->deg, h->state, nint, o.tie_tau, h->trial, s));
+        // 3. propagate the trial fixings to a fixpoint
+        bool conflict = false;
+        int sweeps = 0;
+        for (;;) {
+            CK(cudaMemsetAsync(h->counters, 0, 4 * sizeof(int), s));
+            uint8_t* keep = h->state;
+            h->state = h->trial;  // the support pass reads the trial fixings
+            rc = h->pass(Pass::Supports);
+            h->state = keep;
+            if (rc) return rc;
+            CK(launch_apply(h->sup, h->deg, nint, h->trial, h->counters, s));
+            CK(cudaMemcpyAsync(h->h_counters, h->counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (h->h_counters[1] > 0) { conflict = true; break; }
+            if (h->h_counters[0] == 0) break;
+            if (++sweeps > o.propagate_limit) return fail(DISCO_ERR_TIMEOUT, "primal: propagation did not settle");
+        }
+        if (!conflict) {
+            CK(cudaMemcpyAsync(h->state, h->trial, size_t(nint), cudaMemcpyDeviceToDevice, s));
+            if (h->h_counters[2] == 0) { done = true; break; }
+        }
+        // 4. push undecided variables towards their majority, then continue the dual
+        CK(launch_perturb(h->var, h->desc, h->nslots_tile, h->mm_var, h->state, delta, h->lam, h->lam_lo, s));
+        delta *= o.perturb_growth;
+        if ((rc = h->pass(Pass::BwdReset))) return rc;
+        for (int t = 0; t < o.primal_inner_iters; ++t) {
+            if ((rc = h->pass(Pass::FwdMMARound))) return rc;
+            if ((rc = h->pass(Pass::BwdMMARound))) return rc;
+        }
+    }
+    // read x back: presolve values, then the rounded internal variables
+    std::vector<uint8_t> st(static_cast<size_t>(nint), uint8_t(0));
+    if (nint) {
+        CK(cudaMemcpyAsync(st.data(), h->state, size_t(nint), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    std::vector<uint8_t> x(static_cast<size_t>(P.nvars), uint8_t(0));
+    for (int64_t i = 0; i < P.nvars; ++i) x[i] = P.fixed[i] == 1 ? 1 : 0;
+    bool all = true;
+    for (int64_t v = 0; v < P.n_free; ++v) {
+        x[P.free_orig[v]] = st[v] == kFix1 ? 1 : 0;
+        all = all && st[v] != kFree;
+    }
+    // the dual continues from an unrestricted state
+    CK(cudaMemsetAsync(h->state, 0, size_t(nint), s));
+    h->has_b = false;
+    // exact check of A x = b
+    bool feasible = all;
+    for (int64_t r = 0; r < P.nrows && feasible; ++r) {
+        int64_t sum = 0;
+        for (int64_t e = P.row_ptr[r]; e < P.row_ptr[r + 1]; ++e) sum += int64_t(P.row_coef[e]) * x[P.row_var[e]];
+        feasible = sum == P.rhs[r];
+    }
+    double c = 0.0;
+    for (int64_t i = 0; i < P.nvars; ++i) c += x[i] ? P.cost[i] : 0.0;
+    if (cost) *cost = c;
+    if ((rc = write_out(x_out, x.data(), x.size(), s))) return rc;
+    return feasible ? DISCO_OK : fail(DISCO_ERR_PRIMAL_FAILED, "primal: no feasible assignment within the round limit");
+}
+
+int disco_info(disco_handle* h, disco_info_t* info) {
+    if (!h || !info) return fail(DISCO_ERR_INVALID_ARG, "info: null argument");
+    std::memset(info, 0, sizeof(*info));
+    const Plan& P = h->plan;
+    info->nvars = P.nvars;
+    info->nrows = P.nrows;
+    info->nvars_free = P.n_free;
+    info->nvars_aux = P.n_aux;
+    info->nbdds = int64_t(P.segs.size());
+    info->nslots = int64_t(P.slot_var.size());
+    info->nnodes = P.n_nodes;
+    info->max_layers = P.max_layers;
+    info->max_width = P.max_width;
+    info->ntiles = h->ntiles;
+    info->device_bytes = h->device_bytes;
+    info->iterations = h->iterations;
+    info->constant = P.constant;
+    info->build_ms = P.build_ms;
+    // per iteration: 8 B per node and 20 B per slot per half-pass, 8 B per variable for the averaging
+    info->bytes_per_iter = 2 * (8 * P.n_nodes + 20 * info->nslots + 8 * (P.n_free + P.n_aux));
+    return DISCO_OK;
+}
+
+void disco_free(disco_handle* h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    delete h;
+}
+
+}  // extern "C"

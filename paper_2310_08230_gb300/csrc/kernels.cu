@@ -1,0 +1,724 @@
+// sm_103a kernels of the dual / primal hot path.
+//
+// One warp per tile of 32 BDD segments, one lane per segment (tile layout in kernels.h): at
+// every step the 32 lanes touch the same layer index of their own segment, so each field
+// of a layer (variable, descriptor, lambda, the node costs of one state s) is one coalesced
+// 128-byte line. The node costs of the current layer live in registers (W per lane); only
+// the costs that the other direction needs are stored (F forward, B backward: 8 bytes per
+// node per iteration).
+//
+// Passages: shortest paths through BDDs (Sec. 3.2), min-marginal differences (App. A.5),
+// deferred, parallel-across-BDDs min-marginal averaging (Alg. 1 "MMA"), dual bound (Eq. D),
+// rounding by min-marginal agreement and propagation (App. A.5, Sec. 3 pipeline).
+//
+// Averaging without atomics: a slot of variable i with rank r (its position among i's slots)
+// writes the mass it removes to acc_out[i * 8 + r]; the next half-pass reads the deg values
+// of acc_in[i * 8 ..] (one 32-byte sector) and adds their mean. Sums run in rank order, so
+// every result is deterministic.
+#include <cfloat>
+
+#include "kernels.h"
+
+namespace disco {
+namespace {
+
+constexpr float BIG = 1e30f;
+constexpr int kWarpsPerBlock = 4;
+
+struct Desc {
+    int w, wn, d0, d1, one, rank, deg;
+};
+
+__device__ __forceinline__ Desc decode(uint32_t x) {
+    Desc d;
+    d.w = int(x & 63u) + 1;
+    d.wn = int((x >> 6) & 63u) + 1;
+    d.d0 = int((x >> 12) & 7u) - 2;
+    d.d1 = int((x >> 15) & 63u) - 2;
+    d.one = int((x >> 21) & 1u);
+    d.rank = int((x >> 22) & 7u);
+    d.deg = int((x >> 25) & 7u);
+    return d;
+}
+
+// a[s + k] for a runtime k in [-2, 2] (s is a compile-time index after unrolling); BIG outside.
+template <int W>
+__device__ __forceinline__ float at_shift(const float (&a)[W], int s, int k) {
+    float r = BIG;
+#pragma unroll
+    for (int j = -2; j <= 2; ++j)
+        if (s + j >= 0 && s + j < W) r = (k == j) ? a[s + j] : r;
+    return r;
+}
+
+// a[i] for a runtime i; BIG outside [0, W).
+template <int W>
+__device__ __forceinline__ float at_dyn(const float (&a)[W], int i) {
+    float r = BIG;
+#pragma unroll
+    for (int j = 0; j < W; ++j) r = (i == j) ? a[j] : r;
+    return r;
+}
+
+// Double-float ("df") arithmetic for the dual variables: a value is hi + lo with |lo| <=
+// ulp(hi) / 2. TwoSum (Knuth, TAOCP vol. 2, 4.2.2) gives the exact rounding error of a float
+// sum; Fast2Sum (Dekker 1971) renormalises. Keeping lambda and the deferred mean in df keeps
+// sum_j lambda^j_i + |J_i| pend_i = c_i (Eq. D) exact to about 2^-48 while node costs stay FP32.
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ df fast2sum(float s, float e) {
+    const float h = s + e;
+    return df{h, e - (h - s)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return fast2sum(s, e + (a.lo + b.lo));
+}
+__device__ __forceinline__ df df_add_f(df a, float b) {
+    float s, e;
+    two_sum(a.hi, b, s, e);
+    return fast2sum(s, e + a.lo);
+}
+// a / n for a small positive integer n: the remainder a.hi - q n is exact with an FMA.
+__device__ __forceinline__ df df_div_i(df a, int n) {
+    const float fn = float(n);
+    const float q = a.hi / fn;
+    const float r = fmaf(-q, fn, a.hi) + a.lo;
+    return fast2sum(q, r / fn);
+}
+
+// Deferred mean of variable v: sum of its deg removed masses (rank order) / deg, in df.
+__device__ __forceinline__ df pend_of(const float* __restrict__ acc, uint32_t v, int deg) {
+    const float4* p = reinterpret_cast<const float4*>(acc + size_t(v) * kAccStride);
+    const float4 a = __ldg(p);
+    df s = df_add_f(df{a.x, 0.0f}, a.y);
+    if (deg > 2) s = df_add_f(s, a.z);
+    if (deg > 3) s = df_add_f(s, a.w);
+    if (deg > 4) {
+        const float4 b = __ldg(p + 1);
+        s = df_add_f(s, b.x);
+        if (deg > 5) s = df_add_f(s, b.y);
+        if (deg > 6) s = df_add_f(s, b.z);
+    }
+    return df_div_i(s, deg);
+}
+
+__device__ __forceinline__ uint64_t shl(uint64_t x, int k) { return k >= 0 ? (x << k) : (x >> (-k)); }
+__device__ __forceinline__ uint64_t low_mask(int n) { return n >= 64 ? ~0ull : ((1ull << n) - 1ull); }
+
+// ---------------------------------------------------------------------------------------
+// Inputs of one layer of one lane, loaded ahead of their use. A lane's layers form a
+// sequential recurrence only through the node costs it keeps in registers; every load
+// (variable, descriptor, lambda, the averaging sector, the other direction's node costs) is
+// independent of it, so the kernels keep a ring of kDepth layers in flight: descriptors are
+// fetched 2 * kDepth layers ahead, the loads that need the variable id kDepth layers ahead.
+template <int W>
+struct Layer {
+    uint32_t v, desc;
+    float lam, lo;
+    float4 acc;   // acc_in[v * 8 + 0..3]
+    float acc4;   // acc_in[v * 8 + 4] (variables in five BDDs)
+    uint8_t st;
+    float nb[W];  // forward: B of the next layer; backward: F of this layer
+};
+
+template <int W>
+__host__ __device__ constexpr int depth() { return W <= 8 ? 4 : 2; }
+
+__device__ __forceinline__ void load_head(const KArgs& a, int64_t si, bool ok, uint32_t& v, uint32_t& d) {
+    v = ok ? __ldg(a.var + si) : kNoVar;
+    d = ok ? __ldg(a.desc + si) : 0u;
+}
+
+// NODES: 0 none, 1 = B of layer l + 1 (count wn), 2 = F of layer l (count w)
+template <int W, bool ROUND, int NODES>
+__device__ __forceinline__ void load_body(const KArgs& a, int64_t si, const float* node_row, uint32_t v, uint32_t dsc,
+                                          Layer<W>& L) {
+    L.v = v;
+    L.desc = dsc;
+    if (v == kNoVar) return;
+    L.lam = a.lam[si];
+    L.lo = a.lam_lo[si];
+    const float* ap = a.acc_in + size_t(v) * kAccStride;
+    L.acc = __ldg(reinterpret_cast<const float4*>(ap));
+    const int deg = int((dsc >> 25) & 7u);
+    L.acc4 = deg > 4 ? __ldg(ap + 4) : 0.0f;
+    L.st = ROUND ? __ldg(a.state + v) : kFree;
+    if (NODES) {
+        const int n = NODES == 1 ? int((dsc >> 6) & 63u) + 1 : int(dsc & 63u) + 1;
+#pragma unroll
+        for (int s = 0; s < W; ++s) L.nb[s] = s < n ? __ldg(node_row + s * 32) : BIG;
+    }
+}
+
+template <int W>
+__device__ __forceinline__ df pend_layer(const Layer<W>& L, int deg) {
+    df s = df_add_f(df{L.acc.x, 0.0f}, L.acc.y);
+    if (deg > 2) s = df_add_f(s, L.acc.z);
+    if (deg > 3) s = df_add_f(s, L.acc.w);
+    if (deg > 4) s = df_add_f(s, L.acc4);
+    return df_div_i(s, deg);
+}
+
+// ---------------------------------------------------------------------------------------
+// Forward half-pass with min-marginal averaging (and the plain forward min-sum variants).
+//   MODE 0: MMA update, store F.       MODE 1: MMA update under fixings, store F.
+//   MODE 2: lower bound (no store).    MODE 3: plain min-sum under fixings, store F.
+template <int W, int MODE>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward(KArgs a) {
+    constexpr bool kUpdate = MODE <= 1;
+    constexpr bool kRound = MODE == 1 || MODE == 3;
+    constexpr bool kStoreF = MODE != 2;
+    constexpr int P = depth<W>();
+    const int lane = threadIdx.x & 31;
+    const int tile = a.tile0 + int(blockIdx.x) * kWarpsPerBlock + int(threadIdx.x >> 5);
+    if (tile >= a.tile_end) return;
+    const TileInfo ti = a.tiles[tile];
+    const int64_t sb = ti.slot_base + lane;
+    const float* Bl = a.B + ti.node_base + lane;  // B of layer l at Bl + l * W * 32
+    float* Fl = a.F + ti.node_base + lane;
+    const int L = ti.L;
+    float f[W];
+#pragma unroll
+    for (int s = 0; s < W; ++s) f[s] = s == 0 ? 0.0f : BIG;
+    Layer<W> ring[P];
+    uint32_t hv[P], hd[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        uint32_t v, d;
+        load_head(a, sb + int64_t(k) * 32, k < L, v, d);
+        load_body<W, kRound, kUpdate ? 1 : 0>(a, sb + int64_t(k) * 32, Bl + int64_t(k + 1) * W * 32, v, d, ring[k]);
+        load_head(a, sb + int64_t(k + P) * 32, k + P < L, hv[k], hd[k]);
+    }
+    for (int l0 = 0; l0 < L; l0 += P) {
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            const int l = l0 + k;
+            if (ring[k].v == kNoVar) goto done;
+            // issue the loads of layer l + P and the descriptor of layer l + 2P first
+            Layer<W> nxt;
+            load_body<W, kRound, kUpdate ? 1 : 0>(a, sb + int64_t(l + P) * 32, Bl + int64_t(l + P + 1) * W * 32, hv[k],
+                                                  hd[k], nxt);
+            uint32_t nv, nd;
+            load_head(a, sb + int64_t(l + 2 * P) * 32, l + 2 * P < L, nv, nd);
+            const Layer<W>& c = ring[k];
+            const int64_t si = sb + int64_t(l) * 32;
+            const Desc d = decode(c.desc);
+            const df p = pend_layer(c, d.deg);
+            df Lm{c.lam, c.lo};
+            const bool al0 = c.st != kFix1, al1 = c.st != kFix0;
+            float lm = Lm.hi;
+            if (kStoreF) {
+                float* Fr = Fl + int64_t(l) * W * 32;
+#pragma unroll
+                for (int s = 0; s < W; ++s)
+                    if (s < d.w) Fr[s * 32] = f[s];
+            }
+            if (kUpdate) {
+                float removed = 0.0f;
+                if (c.st == kFree) {
+                    Lm = df_add(Lm, p);
+                    float m0 = BIG, m1 = BIG;
+#pragma unroll
+                    for (int s = 0; s < W; ++s) m0 = fminf(m0, f[s] + at_shift(c.nb, s, d.d0));
+                    if (d.one) {
+                        m1 = f[0] + at_dyn(c.nb, d.d1);
+                    } else {
+#pragma unroll
+                        for (int s = 0; s < W; ++s) m1 = fminf(m1, f[s] + at_shift(c.nb, s, d.d1));
+                    }
+                    const float M = (m1 + Lm.hi) - m0;
+                    removed = a.omega * M;
+                    Lm = df_add_f(Lm, -removed);
+                    a.lam[si] = Lm.hi;
+                    a.lam_lo[si] = Lm.lo;
+                    lm = Lm.hi;
+                }
+                a.acc_out[size_t(c.v) * kAccStride + d.rank] = removed;
+            } else {
+                lm = df_add(Lm, p).hi;
+            }
+            float fn[W];
+#pragma unroll
+            for (int s = 0; s < W; ++s) {
+                float v0 = al0 ? at_shift(f, s, -d.d0) : BIG;
+                float v1 = BIG;
+                if (al1) v1 = (d.one ? (s == d.d1 ? f[0] : BIG) : at_shift(f, s, -d.d1)) + lm;
+                fn[s] = s < d.wn ? fminf(v0, v1) : BIG;
+            }
+#pragma unroll
+            for (int s = 0; s < W; ++s) f[s] = fn[s];
+            ring[k] = nxt;
+            hv[k] = nv;
+            hd[k] = nd;
+        }
+    }
+done:
+    if (MODE == 2) {
+        double x = double(f[0]);  // cost of the cheapest root -> TOP path (0 for an empty lane)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) a.tile_sum[tile] = x;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Backward half-pass with min-marginal averaging (and plain backward variants).
+//   MODE 0: MMA update, store B.                 MODE 1: MMA update under fixings, store B.
+//   MODE 2: min-marginals under fixings (out).   MODE 3: plain min-sum under fixings, store B.
+template <int W, int MODE>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_backward(KArgs a) {
+    constexpr bool kUpdate = MODE <= 1;
+    constexpr bool kRound = MODE >= 1;
+    constexpr bool kStoreB = MODE != 2;
+    constexpr bool kNeedF = MODE != 3;
+    constexpr int P = depth<W>();
+    const int lane = threadIdx.x & 31;
+    const int tile = a.tile0 + int(blockIdx.x) * kWarpsPerBlock + int(threadIdx.x >> 5);
+    if (tile >= a.tile_end) return;
+    const TileInfo ti = a.tiles[tile];
+    const int64_t sb = ti.slot_base + lane;
+    const float* Fl = a.F + ti.node_base + lane;
+    float* Bl = a.B + ti.node_base + lane;
+    const int L = ti.L;
+    float bn[W];
+#pragma unroll
+    for (int s = 0; s < W; ++s) bn[s] = s == 0 ? 0.0f : BIG;
+    Layer<W> ring[P];
+    uint32_t hv[P], hd[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        const int l = L - 1 - k;
+        uint32_t v, d;
+        load_head(a, sb + int64_t(l) * 32, l >= 0, v, d);
+        load_body<W, kRound, kNeedF ? 2 : 0>(a, sb + int64_t(l) * 32, Fl + int64_t(l) * W * 32, v, d, ring[k]);
+        load_head(a, sb + int64_t(l - P) * 32, l - P >= 0, hv[k], hd[k]);
+    }
+    for (int l0 = L - 1; l0 >= 0; l0 -= P) {
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            const int l = l0 - k;
+            if (l < 0) goto done;
+            Layer<W> nxt;
+            load_body<W, kRound, kNeedF ? 2 : 0>(a, sb + int64_t(l - P) * 32, Fl + int64_t(l - P) * W * 32, hv[k], hd[k],
+                                                 nxt);
+            uint32_t nv, nd;
+            load_head(a, sb + int64_t(l - 2 * P) * 32, l - 2 * P >= 0, nv, nd);
+            const Layer<W>& c = ring[k];
+            if (c.v != kNoVar) {
+                const int64_t si = sb + int64_t(l) * 32;
+                const Desc d = decode(c.desc);
+                const df p = pend_layer(c, d.deg);
+                df Lm{c.lam, c.lo};
+                const bool al0 = c.st != kFix1, al1 = c.st != kFix0;
+                float lm = Lm.hi;
+                const float b1 = d.one ? at_dyn(bn, d.d1) : BIG;  // target of node 0's 1-arc (one-hot chains)
+                if (kNeedF) {
+                    float m0 = BIG, m1 = BIG;
+#pragma unroll
+                    for (int s = 0; s < W; ++s) m0 = fminf(m0, c.nb[s] + (al0 ? at_shift(bn, s, d.d0) : BIG));
+                    if (al1) {
+                        if (d.one) {
+                            m1 = c.nb[0] + b1;
+                        } else {
+#pragma unroll
+                            for (int s = 0; s < W; ++s) m1 = fminf(m1, c.nb[s] + at_shift(bn, s, d.d1));
+                        }
+                    }
+                    if (kUpdate) {
+                        float removed = 0.0f;
+                        if (c.st == kFree) {
+                            Lm = df_add(Lm, p);
+                            const float M = (m1 + Lm.hi) - m0;
+                            removed = a.omega * M;
+                            Lm = df_add_f(Lm, -removed);
+                            a.lam[si] = Lm.hi;
+                            a.lam_lo[si] = Lm.lo;
+                            lm = Lm.hi;
+                        }
+                        a.acc_out[size_t(c.v) * kAccStride + d.rank] = removed;
+                    } else {
+                        lm = df_add(Lm, p).hi;
+                        const float M = (m1 + lm) - m0;
+                        a.mm_slot[si] = M;
+                        a.mm_var[size_t(c.v) * kAccStride + d.rank] = M;
+                    }
+                } else {
+                    lm = df_add(Lm, p).hi;
+                }
+                float bc[W];
+#pragma unroll
+                for (int s = 0; s < W; ++s) {
+                    float v0 = al0 ? at_shift(bn, s, d.d0) : BIG;
+                    float v1 = BIG;
+                    if (al1) v1 = (d.one ? (s == 0 ? b1 : BIG) : at_shift(bn, s, d.d1)) + lm;
+                    bc[s] = s < d.w ? fminf(v0, v1) : BIG;
+                }
+                if (kStoreB) {
+                    float* Br = Bl + int64_t(l) * W * 32;
+#pragma unroll
+                    for (int s = 0; s < W; ++s)
+                        if (s < d.w) Br[s * 32] = bc[s];
+                }
+#pragma unroll
+                for (int s = 0; s < W; ++s) bn[s] = bc[s];
+            }
+            ring[k] = nxt;
+            hv[k] = nv;
+            hd[k] = nd;
+        }
+    }
+done:
+    return;
+}
+
+// ---------------------------------------------------------------------------------------
+// Value supports under fixings: which values of each slot's variable lie on some
+// root -> TOP path of its segment that respects the fixings (bit-parallel over nodes).
+template <int W>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_supports(KArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int tile = a.tile0 + int(blockIdx.x) * kWarpsPerBlock + int(threadIdx.x >> 5);
+    if (tile >= a.tile_end) return;
+    const TileInfo ti = a.tiles[tile];
+    const int64_t sb = ti.slot_base + lane;
+    uint64_t rf = 1;  // nodes of the current layer reachable from the root
+    int Ll = 0;
+    for (int l = 0; l < ti.L; ++l) {
+        const int64_t si = sb + int64_t(l) * 32;
+        const uint32_t v = __ldg(a.var + si);
+        if (v == kNoVar) break;
+        const Desc d = decode(__ldg(a.desc + si));
+        const uint8_t st = __ldg(a.state + v);
+        a.reach[si] = uint32_t(rf);
+        uint64_t n0 = st != kFix1 ? shl(rf, d.d0) : 0;
+        uint64_t n1 = 0;
+        if (st != kFix0) n1 = d.one ? ((rf & 1ull) << d.d1) : shl(rf, d.d1);
+        rf = (n0 | n1) & low_mask(d.wn);
+        Ll = l + 1;
+    }
+    uint64_t rb = 1;  // nodes of the next layer that reach TOP
+    for (int l = Ll - 1; l >= 0; --l) {
+        const int64_t si = sb + int64_t(l) * 32;
+        const uint32_t v = __ldg(a.var + si);
+        const Desc d = decode(__ldg(a.desc + si));
+        const uint8_t st = __ldg(a.state + v);
+        const uint64_t rfl = a.reach[si];
+        const uint64_t ok0 = st != kFix1 ? (shl(rb, -d.d0) & low_mask(d.w)) : 0;
+        uint64_t ok1 = 0;
+        if (st != kFix0) ok1 = d.one ? ((rb >> d.d1) & 1ull) : (shl(rb, -d.d1) & low_mask(d.w));
+        const uint8_t sup = uint8_t(((rfl & ok0) ? 1 : 0) | ((rfl & ok1) ? 2 : 0));
+        a.sup_var[size_t(v) * kAccStride + d.rank] = sup;
+        rb = ok0 | ok1;
+    }
+}
+
+template <int W>
+cudaError_t launch_w(Pass pass, const KArgs& a, cudaStream_t s) {
+    const int n = a.tile_end - a.tile0;
+    if (n <= 0) return cudaSuccess;
+    const dim3 grid((n + kWarpsPerBlock - 1) / kWarpsPerBlock), block(kWarpsPerBlock * 32);
+    switch (pass) {
+        case Pass::FwdMMA: k_forward<W, 0><<<grid, block, 0, s>>>(a); break;
+        case Pass::FwdMMARound: k_forward<W, 1><<<grid, block, 0, s>>>(a); break;
+        case Pass::Lb: k_forward<W, 2><<<grid, block, 0, s>>>(a); break;
+        case Pass::FwdMM: k_forward<W, 3><<<grid, block, 0, s>>>(a); break;
+        case Pass::BwdMMA: k_backward<W, 0><<<grid, block, 0, s>>>(a); break;
+        case Pass::BwdMMARound: k_backward<W, 1><<<grid, block, 0, s>>>(a); break;
+        case Pass::BwdMM: k_backward<W, 2><<<grid, block, 0, s>>>(a); break;
+        case Pass::BwdReset: k_backward<W, 3><<<grid, block, 0, s>>>(a); break;
+        case Pass::Supports: k_supports<W><<<grid, block, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+__global__ void k_sum_tiles(const double* __restrict__ x, int64_t n, double add, double* out) {
+    __shared__ double sh[1024];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (int(threadIdx.x) < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0] + add;
+}
+
+__global__ void k_gather(const float* __restrict__ src, const int64_t* __restrict__ pos, int64_t n, float* dst) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        dst[i] = src[pos[i]];
+}
+
+__global__ void k_scatter(const float* __restrict__ src, const int64_t* __restrict__ pos, int64_t n, float* dst) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        dst[pos[i]] = src[i];
+}
+
+__global__ void k_pend(const float* __restrict__ acc, const uint8_t* __restrict__ deg, int64_t n, float* pend) {
+    for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x)
+        pend[v] = deg[v] ? pend_of(acc, uint32_t(v), deg[v]).hi : 0.0f;
+}
+
+__global__ void k_set_pend(const float* __restrict__ pend, const uint8_t* __restrict__ deg, int64_t n, float* acc) {
+    for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
+        // a deferred mean p is reproduced by deg removed masses of p each
+        for (int r = 0; r < kAccStride; ++r) acc[v * kAccStride + r] = r < deg[v] ? pend[v] : 0.0f;
+    }
+}
+
+__global__ void k_flush(const uint32_t* __restrict__ var, const uint32_t* __restrict__ desc, int64_t n,
+                        const float* __restrict__ acc, float* lam, float* lam_lo) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const uint32_t v = var[i];
+        if (v == kNoVar) continue;
+        const df L = df_add(df{lam[i], lam_lo[i]}, pend_of(acc, v, decode(desc[i]).deg));
+        lam[i] = L.hi;
+        lam_lo[i] = L.lo;
+    }
+}
+
+__global__ void k_decide(const float* __restrict__ mm_var, const uint8_t* __restrict__ deg,
+                         const uint8_t* __restrict__ state, int64_t n, float tau, uint8_t* trial) {
+    for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
+        uint8_t st = state[v];
+        if (st == kFree && deg[v] > 0) {
+            bool pos = true, neg = true;
+            for (int r = 0; r < deg[v]; ++r) {
+                const float M = mm_var[v * kAccStride + r];
+                pos = pos && (M > tau);
+                neg = neg && (M < -tau);
+            }
+            st = pos ? kFix0 : (neg ? kFix1 : kFree);
+        }
+        trial[v] = st;
+    }
+}
+
+// counters[0]: newly forced variables, counters[1]: conflicts, counters[2]: free variables left
+__global__ void k_apply(const uint8_t* __restrict__ sup, const uint8_t* __restrict__ deg, int64_t n, uint8_t* state,
+                        int* counters) {
+    for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
+        const int dg = deg[v];
+        if (dg == 0) continue;
+        bool can0 = true, can1 = true;
+        for (int r = 0; r < dg; ++r) {
+            const uint8_t s = sup[v * kAccStride + r];
+            can0 = can0 && (s & 1);
+            can1 = can1 && (s & 2);
+        }
+        const uint8_t st = state[v];
+        if ((st == kFix0 && !can0) || (st == kFix1 && !can1) || (st == kFree && !can0 && !can1)) {
+            atomicAdd(counters + 1, 1);
+        } else if (st == kFree) {
+            if (!can0) { state[v] = kFix1; atomicAdd(counters, 1); }
+            else if (!can1) { state[v] = kFix0; atomicAdd(counters, 1); }
+            else atomicAdd(counters + 2, 1);
+        }
+    }
+}
+
+__global__ void k_perturb(const uint32_t* __restrict__ var, const uint32_t* __restrict__ desc, int64_t n,
+                          const float* __restrict__ mm_var, const uint8_t* __restrict__ state, float delta, float* lam,
+                          float* lam_lo) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const uint32_t v = var[i];
+        if (v == kNoVar || state[v] != kFree) continue;
+        const int dg = decode(desc[i]).deg;
+        float s = 0.0f;
+        for (int r = 0; r < dg; ++r) s += mm_var[size_t(v) * kAccStride + r];
+        const df L = df_add_f(df{lam[i], lam_lo[i]}, s >= 0.0f ? delta : -delta);
+        lam[i] = L.hi;
+        lam_lo[i] = L.lo;
+    }
+}
+
+// ---- feature distances: d[m, n] = mean_k (FX[m,k] - FY[n,k])^2, 64 x 64 tiles, 4 x 4 per thread
+constexpr int kPT = 64, kPK = 32;
+__global__ void __launch_bounds__(256) k_pair_costs(const float* __restrict__ FX, const float* __restrict__ FY, int nvx,
+                                                    int nvy, int dim, float* __restrict__ d) {
+    __shared__ float sx[kPK][kPT + 1];
+    __shared__ float sy[kPK][kPT + 1];
+    const int m0 = blockIdx.y * kPT, n0 = blockIdx.x * kPT;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < dim; k0 += kPK) {
+        for (int i = threadIdx.x; i < kPT * kPK; i += 256) {
+            const int r = i / kPK, c = i % kPK;
+            const int m = m0 + r, n = n0 + r, k = k0 + c;
+            sx[c][r] = (m < nvx && k < dim) ? FX[size_t(m) * dim + k] : 0.0f;
+            sy[c][r] = (n < nvy && k < dim) ? FY[size_t(n) * dim + k] : 0.0f;
+        }
+        __syncthreads();
+        const int kk = min(kPK, dim - k0);
+        for (int c = 0; c < kk; ++c) {
+            float xv[4], yv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { xv[i] = sx[c][ty * 4 + i]; yv[i] = sy[c][tx * 4 + i]; }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float t = xv[i] - yv[j];
+                    acc[i][j] = fmaf(t, t, acc[i][j]);
+                }
+        }
+        __syncthreads();
+    }
+    const float inv = 1.0f / float(dim);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + ty * 4 + i, n = n0 + tx * 4 + j;
+            if (m < nvx && n < nvy) d[size_t(m) * nvy + n] = acc[i][j] * inv;
+        }
+}
+
+__global__ void k_transpose(const float* __restrict__ src, int rows, int cols, float* __restrict__ dst) {
+    __shared__ float t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) t[i][threadIdx.x] = src[size_t(r) * cols + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) dst[size_t(c) * rows + r] = t[threadIdx.x][i];
+    }
+}
+
+// k smallest entries of every row (ties to the lower column), one warp per row: k rounds of
+// a warp-wide arg-min over the entries ordered after the previous pick.
+__global__ void k_topk_rows(const float* __restrict__ d, int rows, int cols, int k, int32_t* __restrict__ idx) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    const float* r = d + size_t(row) * cols;
+    float pv = -FLT_MAX;
+    int pi = -1;
+    for (int t = 0; t < k && t < cols; ++t) {
+        float bv = FLT_MAX;
+        int bi = INT32_MAX;
+        for (int c = lane; c < cols; c += 32) {
+            const float x = r[c];
+            const bool after = (x > pv) || (x == pv && c > pi);
+            if (after && ((x < bv) || (x == bv && c < bi))) { bv = x; bi = c; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if ((ov < bv) || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        }
+        if (lane == 0) idx[size_t(row) * k + t] = bi;
+        pv = bv;
+        pi = bi;
+    }
+}
+
+// allowed[m, n] = 1 for every n in the closed 1-ring of a pick of row m (transposed: the
+// rows are Y vertices n and the ring is on X).
+__global__ void k_dilate(const int32_t* __restrict__ topk, int rows, int k, const int32_t* __restrict__ ring_ptr,
+                         const int32_t* __restrict__ ring, int nvy, bool transposed, uint8_t* allowed) {
+    const int row = blockIdx.x;
+    if (row >= rows) return;
+    for (int t = threadIdx.y; t < k; t += blockDim.y) {
+        const int c = topk[size_t(row) * k + t];
+        for (int j = ring_ptr[c] + threadIdx.x; j < ring_ptr[c + 1]; j += blockDim.x) {
+            const int o = ring[j];
+            if (!transposed) allowed[size_t(row) * nvy + o] = 1;
+            else allowed[size_t(o) * nvy + row] = 1;
+        }
+    }
+}
+
+inline int grid_for(int64_t n, int block) {
+    const int64_t g = (n + block - 1) / block;
+    return int(g < 1 ? 1 : (g > 152 * 64 ? 152 * 64 : g));
+}
+
+}  // namespace
+
+cudaError_t launch_pass(Pass pass, int W, const KArgs& a, cudaStream_t s) {
+    switch (W) {
+        case 2: return launch_w<2>(pass, a, s);
+        case 4: return launch_w<4>(pass, a, s);
+        case 8: return launch_w<8>(pass, a, s);
+        case 16: return launch_w<16>(pass, a, s);
+        case 32: return launch_w<32>(pass, a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_sum_tiles(const double* tile_sum, int64_t n, double add, double* out, cudaStream_t s) {
+    k_sum_tiles<<<1, 1024, 0, s>>>(tile_sum, n, add, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_gather_f32(const float* src, const int64_t* pos, int64_t n, float* dst, cudaStream_t s) {
+    if (n > 0) k_gather<<<grid_for(n, 256), 256, 0, s>>>(src, pos, n, dst);
+    return cudaGetLastError();
+}
+cudaError_t launch_scatter_f32(const float* src, const int64_t* pos, int64_t n, float* dst, cudaStream_t s) {
+    if (n > 0) k_scatter<<<grid_for(n, 256), 256, 0, s>>>(src, pos, n, dst);
+    return cudaGetLastError();
+}
+cudaError_t launch_pend(const float* acc, const uint8_t* deg, int64_t n, float* pend, cudaStream_t s) {
+    if (n > 0) k_pend<<<grid_for(n, 256), 256, 0, s>>>(acc, deg, n, pend);
+    return cudaGetLastError();
+}
+cudaError_t launch_set_pend(const float* pend, const uint8_t* deg, int64_t n, float* acc, cudaStream_t s) {
+    if (n > 0) k_set_pend<<<grid_for(n, 256), 256, 0, s>>>(pend, deg, n, acc);
+    return cudaGetLastError();
+}
+cudaError_t launch_flush(const uint32_t* var, const uint32_t* desc, int64_t n, const float* acc, float* lam,
+                         float* lam_lo, cudaStream_t s) {
+    if (n > 0) k_flush<<<grid_for(n, 256), 256, 0, s>>>(var, desc, n, acc, lam, lam_lo);
+    return cudaGetLastError();
+}
+cudaError_t launch_decide(const float* mm_var, const uint8_t* deg, const uint8_t* state, int64_t n, float tau,
+                          uint8_t* trial, cudaStream_t s) {
+    if (n > 0) k_decide<<<grid_for(n, 256), 256, 0, s>>>(mm_var, deg, state, n, tau, trial);
+    return cudaGetLastError();
+}
+cudaError_t launch_apply(const uint8_t* sup_var, const uint8_t* deg, int64_t n, uint8_t* state, int* counters,
+                         cudaStream_t s) {
+    if (n > 0) k_apply<<<grid_for(n, 256), 256, 0, s>>>(sup_var, deg, n, state, counters);
+    return cudaGetLastError();
+}
+cudaError_t launch_perturb(const uint32_t* var, const uint32_t* desc, int64_t n, const float* mm_var,
+                           const uint8_t* state, float delta, float* lam, float* lam_lo, cudaStream_t s) {
+    if (n > 0) k_perturb<<<grid_for(n, 256), 256, 0, s>>>(var, desc, n, mm_var, state, delta, lam, lam_lo);
+    return cudaGetLastError();
+}
+cudaError_t launch_pair_costs(const float* FX, const float* FY, int nvx, int nvy, int dim, float* d, cudaStream_t s) {
+    const dim3 grid((nvy + kPT - 1) / kPT, (nvx + kPT - 1) / kPT);
+    k_pair_costs<<<grid, 256, 0, s>>>(FX, FY, nvx, nvy, dim, d);
+    return cudaGetLastError();
+}
+cudaError_t launch_transpose(const float* src, int rows, int cols, float* dst, cudaStream_t s) {
+    const dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+    k_transpose<<<grid, block, 0, s>>>(src, rows, cols, dst);
+    return cudaGetLastError();
+}
+cudaError_t launch_topk_rows(const float* d, int rows, int cols, int k, int32_t* idx, cudaStream_t s) {
+    k_topk_rows<<<(rows + 7) / 8, 256, 0, s>>>(d, rows, cols, k, idx);
+    return cudaGetLastError();
+}
+cudaError_t launch_dilate(const int32_t* topk, int rows, int k, const int32_t* ring_ptr, const int32_t* ring, int nvy,
+                          bool transposed, uint8_t* allowed, cudaStream_t s) {
+    k_dilate<<<rows, dim3(8, 8), 0, s>>>(topk, rows, k, ring_ptr, ring, nvy, transposed, allowed);
+    return cudaGetLastError();
+}
+
+}  // namespace disco

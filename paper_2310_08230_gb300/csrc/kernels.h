@@ -1,0 +1,80 @@
+// Device store layout and kernel launchers of the dual / primal hot path.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace disco {
+
+// A warp tile: 32 BDD segments (one per lane) of one width class.
+//   slot (layer l, lane)      at slot_base + l * 32 + lane              (var, desc, lambda)
+//   node (layer l, s, lane)   at node_base + (l * W + s) * 32 + lane    (F, B)
+// Layers 0..L-1 hold variables; layer L is the terminal (B = 0 at s = 0). Lanes with fewer
+// layers, or no segment, carry var = kNoVar from their end on.
+struct TileInfo {
+    int64_t slot_base;
+    int64_t node_base;
+    int32_t L;
+    int32_t W;
+};
+
+constexpr uint32_t kNoVar = 0xFFFFFFFFu;
+constexpr int kAccStride = 8;  // floats per variable in the averaging tables
+enum : uint8_t { kFree = 0, kFix0 = 1, kFix1 = 2 };
+
+struct KArgs {
+    const TileInfo* tiles;
+    int32_t tile0, tile_end;         // tiles of one width class
+    const uint32_t* var;
+    const uint32_t* desc;
+    float* lam;                      // dual variables, high part (the FP32 value used by the passes)
+    float* lam_lo;                   // low part: lambda = lam + lam_lo (double-float)
+    float* F;
+    float* B;
+    const float* acc_in;             // mass removed by the previous half-pass (kAccStride per var)
+    float* acc_out;                  // mass removed by this half-pass
+    const uint8_t* state;            // per variable, rounding only
+    float omega;
+    float* mm_slot;                  // per slot (tile layout)
+    float* mm_var;                   // kAccStride per variable
+    double* tile_sum;                // per tile
+    uint32_t* reach;                 // per slot (tile layout)
+    uint8_t* sup_var;                // kAccStride per variable
+};
+
+enum class Pass {
+    FwdMMA,      // forward half-pass with updates, stores F
+    BwdMMA,      // backward half-pass with updates, stores B
+    FwdMMARound, // same, fixed variables masked and not updated
+    BwdMMARound,
+    Lb,          // forward min-sum on lambda + pend, per-tile sum of BDD minima
+    FwdMM,       // forward min-sum on lambda + pend (fixings masked), stores F
+    BwdMM,       // backward min-sum, writes min-marginals
+    BwdReset,    // backward min-sum on lambda + pend (fixings masked), stores B
+    Supports     // reachability under fixings, writes per-slot value supports
+};
+
+// Launches `pass` over the tiles [a.tile0, a.tile_end) of width class W (2, 4, 8, 16, 32).
+cudaError_t launch_pass(Pass pass, int W, const KArgs& a, cudaStream_t s);
+
+cudaError_t launch_sum_tiles(const double* tile_sum, int64_t n, double add, double* out, cudaStream_t s);
+cudaError_t launch_gather_f32(const float* src, const int64_t* pos, int64_t n, float* dst, cudaStream_t s);
+cudaError_t launch_scatter_f32(const float* src, const int64_t* pos, int64_t n, float* dst, cudaStream_t s);
+cudaError_t launch_pend(const float* acc, const uint8_t* deg, int64_t n, float* pend, cudaStream_t s);
+cudaError_t launch_set_pend(const float* pend, const uint8_t* deg, int64_t n, float* acc, cudaStream_t s);
+cudaError_t launch_flush(const uint32_t* var, const uint32_t* desc, int64_t nslots, const float* acc, float* lam,
+                         float* lam_lo, cudaStream_t s);
+cudaError_t launch_decide(const float* mm_var, const uint8_t* deg, const uint8_t* state, int64_t n, float tau,
+                          uint8_t* trial, cudaStream_t s);
+cudaError_t launch_apply(const uint8_t* sup_var, const uint8_t* deg, int64_t n, uint8_t* state, int* counters,
+                         cudaStream_t s);
+cudaError_t launch_perturb(const uint32_t* var, const uint32_t* desc, int64_t nslots, const float* mm_var,
+                           const uint8_t* state, float delta, float* lam, float* lam_lo, cudaStream_t s);
+cudaError_t launch_pair_costs(const float* FX, const float* FY, int nvx, int nvy, int dim, float* d, cudaStream_t s);
+cudaError_t launch_transpose(const float* src, int rows, int cols, float* dst, cudaStream_t s);
+cudaError_t launch_topk_rows(const float* d, int rows, int cols, int k, int32_t* idx, cudaStream_t s);
+cudaError_t launch_dilate(const int32_t* topk, int rows, int k, const int32_t* ring_ptr, const int32_t* ring,
+                          int nvy, bool transposed, uint8_t* allowed, cudaStream_t s);
+
+}  // namespace disco

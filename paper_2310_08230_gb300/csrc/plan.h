@@ -1,0 +1,74 @@
+// Host-side compilation of ILP (P) into BDD segments ("the plan"), consumed by the device
+// store in disco.cu. See host_build.cpp for the passages each step follows.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace disco {
+
+// Widest BDD layer the device kernels accept (node states held in registers).
+constexpr int kMaxWidth = 32;
+
+// Per-slot layer descriptor (uint32):
+//   bits  0..5   w     nodes in this layer (1..32)
+//   bits  6..11  wn    nodes in the next layer (1..32); the terminal layer has 1 node
+//   bits 12..14  d0+2  0-arc: node s goes to node s + d0 of the next layer
+//   bits 15..20  d1+2  1-arc: node s goes to node s + d1 (d1 in [-2, 32])
+//   bit  21      one   the 1-arc leaves only node 0 (auxiliary chains of a split)
+//   bits 22..24  rank  position of this slot among its variable's slots
+//   bits 25..27  deg   number of slots of the variable (|J_i|, 2..5)
+// An arc whose target index falls outside [0, wn) leads to the false terminal.
+inline uint32_t pack_desc(int w, int wn, int d0, int d1, bool one, int rank, int deg) {
+    return uint32_t(w - 1) | (uint32_t(wn - 1) << 6) | (uint32_t(d0 + 2) << 12) |
+           (uint32_t(d1 + 2) << 15) | (uint32_t(one ? 1 : 0) << 21) | (uint32_t(rank) << 22) |
+           (uint32_t(deg) << 25);
+}
+
+struct Segment {
+    int64_t row;        // row of (P)
+    int32_t index;      // segment index within the row
+    int64_t first_slot; // canonical index of its first layer
+    int32_t n_layers;
+    int32_t max_width;
+};
+
+struct Plan {
+    // ---- problem (P)
+    int32_t nvx = 0, nvy = 0;
+    int64_t nvars = 0, nrows = 0, n_closed = 0, n_projx = 0, n_projy = 0;
+    std::vector<int32_t> vm, vn;         // 3 per variable: X / Y vertex of each corner
+    std::vector<double> cost;            // normalised c_p per variable
+    std::vector<int64_t> row_ptr;        // rows: closedness, X projection, Y projection
+    std::vector<int32_t> row_var;
+    std::vector<int8_t> row_coef;
+    std::vector<int32_t> rhs;
+    // ---- presolve
+    std::vector<int8_t> fixed;           // per variable: -1 free, 0 / 1 fixed
+    double constant = 0.0;               // sum of c over variables fixed to 1
+    // ---- internal variables: [0, n_free) free variables in ascending id, then auxiliaries
+    int64_t n_free = 0, n_aux = 0;
+    std::vector<int32_t> free_orig;      // internal id -> variable id (free ones)
+    std::vector<uint8_t> deg;            // slots per internal variable
+    // ---- canonical slots: segments by (row, index), layers in order
+    std::vector<int32_t> slot_var;       // internal variable id
+    std::vector<uint32_t> slot_desc;
+    std::vector<float> slot_lam0;        // lambda^0 = c / |J| (high part), 0 for auxiliaries
+    std::vector<float> slot_lam0_lo;     // low part: c / |J| - slot_lam0
+    std::vector<Segment> segs;
+    int64_t n_nodes = 0;
+    int32_t max_layers = 0, max_width = 0;
+    double build_ms = 0.0;
+};
+
+struct MeshIn {
+    int32_t nv, nt;
+    const int32_t* T;
+};
+
+// Returns 0 or a negative DISCO_ERR_* code (err receives a message).
+int build_plan(const MeshIn& X, const MeshIn& Y, const float* d, const uint8_t* allowed,
+               int split_chunk, int threads, Plan* out, std::string* err);
+
+}  // namespace disco

@@ -1,0 +1,199 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances (FP32 device arithmetic on costs normalised to [0, 1]): lower bound 1e-5
+relative after a fixed iteration count, min-marginals 1e-4 absolute, primal feasible
+exactly with cost within 1e-4 relative of the oracle's (ties excepted), pair costs 1e-5
+relative."""
+import numpy as np
+import pytest
+
+from oracle import bdd as B
+from oracle import primal as PR
+from oracle import problem as P
+from oracle import solver as S
+from synth import instances as I
+
+pytestmark = pytest.mark.gpu
+
+LB_RTOL = 1e-5
+MM_ATOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_08230_gb300.build import build
+
+    build()
+    return torch
+
+
+_cache = {}
+
+
+def _oracle(which, chunk):
+    key = (which, chunk)
+    if key not in _cache:
+        inst = getattr(I, which)()
+        prob, d, allowed = P.make_problem(inst)
+        fixed, const = P.presolve(prob)
+        dec = B.decompose(prob, fixed, const, chunk)
+        _cache[key] = (inst, prob, d, allowed, fixed, dec)
+    return _cache[key]
+
+
+def _solver(inst, d, allowed, **kw):
+    from paper_2310_08230_gb300.api import Solver
+
+    return Solver(inst.X.T, inst.Y.T, np.asarray(d, np.float32), None if inst.topk is None else allowed, **kw)
+
+
+def test_pair_costs_match_oracle(torch):
+    from paper_2310_08230_gb300.api import pair_costs
+
+    for which in ("config1", "config2"):
+        inst = getattr(I, which)()
+        d_ref = P.pair_distance(inst.FX, inst.FY)
+        d = pair_costs(torch.from_numpy(inst.FX).cuda(), torch.from_numpy(inst.FY).cuda())
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(d.cpu().numpy(), d_ref, rtol=1e-5, atol=1e-7)
+
+
+def test_pair_costs_ragged_tiles(torch):
+    """Sizes that are not multiples of the 64 x 64 tile or the 32-wide k chunk."""
+    from paper_2310_08230_gb300.api import pair_costs
+
+    rng = np.random.Generator(np.random.PCG64(7))
+    for nx, ny, D in ((1, 1, 1), (65, 3, 33), (130, 97, 70)):
+        FX = rng.standard_normal((nx, D)).astype(np.float32)
+        FY = rng.standard_normal((ny, D)).astype(np.float32)
+        d = pair_costs(torch.from_numpy(FX).cuda(), torch.from_numpy(FY).cuda()).cpu().numpy()
+        np.testing.assert_allclose(d, P.pair_distance(FX, FY), rtol=1e-5, atol=1e-7)
+
+
+def test_candidates_match_oracle(torch):
+    from paper_2310_08230_gb300.api import candidates
+
+    for which in ("config2",):
+        inst = getattr(I, which)()
+        d_ref = P.pair_distance(inst.FX, inst.FY)
+        # both sides rank the same FP32 distances: take the decision in one precision
+        d32 = d_ref.astype(np.float32)
+        ref = P.candidate_pairs(d32.astype(np.float64), inst.topk, inst.X.T, inst.Y.T)
+        got = candidates(torch.from_numpy(d32).cuda(), inst.topk, inst.X.T, inst.Y.T).cpu().numpy().astype(bool)
+        assert np.array_equal(got, ref)
+        assert np.all(got[np.arange(inst.X.nv), inst.perm])
+
+
+@pytest.mark.parametrize("which,chunk,iters", [("tet", 0, 0), ("tet", 0, 50), ("tet", 5, 50), ("config1", 0, 0),
+                                               ("config1", 0, 200), ("config1", 8, 200), ("config2", 0, 0),
+                                               ("config2", 0, 500)])
+def test_lower_bound_parity(torch, which, chunk, iters):
+    inst, prob, d, allowed, fixed, dec = _oracle(which, chunk)
+    o = S.DualOracle(dec)
+    o.iterate(iters)
+    s = _solver(inst, d, allowed, split_chunk=chunk)
+    s.dual(iters)
+    lb = s.lower_bound()
+    ref = o.lower_bound()
+    assert abs(lb - ref) <= LB_RTOL * max(abs(ref), 1e-3), (lb, ref)
+    info = s.info()
+    assert info["nslots"] == dec.n_layers and info["nnodes"] == dec.n_nodes
+    s.close()
+
+
+@pytest.mark.parametrize("which,chunk,iters", [("tet", 0, 30), ("config1", 0, 100), ("config1", 8, 60),
+                                               ("config2", 0, 100)])
+def test_min_marginal_parity(torch, which, chunk, iters):
+    inst, prob, d, allowed, fixed, dec = _oracle(which, chunk)
+    o = S.DualOracle(dec)
+    o.iterate(iters)
+    s = _solver(inst, d, allowed, split_chunk=chunk)
+    s.dual(iters)
+    mm = s.min_marginals()
+    ref = o.min_marginals()
+    np.testing.assert_allclose(mm, ref, atol=MM_ATOL, rtol=0)
+    s.close()
+
+
+def test_state_roundtrip_and_dual_feasibility(torch):
+    inst, prob, d, allowed, fixed, dec = _oracle("config1", 0)
+    s = _solver(inst, d, allowed)
+    s.dual(37)
+    lam, pend = s.get_state()
+    # sum_j lambda^j_i + |J_i| pend_i = c_i (Eq. D feasibility), in FP32
+    free = np.nonzero(fixed < 0)[0]
+    lv = dec.layer_var
+    tot = np.bincount(lv, weights=lam.astype(np.float64), minlength=dec.nvars_total)
+    resid = tot[free] + dec.deg[free] * pend[: len(free)].astype(np.float64) - prob.cost[free]
+    assert np.abs(resid).max() < 1e-5
+    lb1 = s.lower_bound()
+    s2 = _solver(inst, d, allowed)
+    s2.set_state(lam, pend)
+    assert s2.lower_bound() == pytest.approx(lb1, rel=1e-6)
+    s.dual(5)
+    s2.dual(5)
+    assert s2.lower_bound() == pytest.approx(s.lower_bound(), rel=1e-6)
+    s.close()
+    s2.close()
+
+
+def test_bound_is_monotone_and_below_primal(torch):
+    inst, prob, d, allowed, fixed, dec = _oracle("config2", 0)
+    s = _solver(inst, d, allowed)
+    prev = s.lower_bound()
+    for _ in range(10):
+        s.dual(10)
+        lb = s.lower_bound()
+        assert lb >= prev - 1e-6 * abs(lb)
+        prev = lb
+    x, cost, ok = s.primal()
+    assert ok
+    assert not np.any(prob.residual(x))
+    assert prev <= cost + 1e-6 * abs(cost)
+    s.close()
+
+
+@pytest.mark.parametrize("which,iters", [("tet", 50), ("config1", 200), ("config2", 500)])
+def test_primal_parity(torch, which, iters):
+    inst, prob, d, allowed, fixed, dec = _oracle(which, 0)
+    o = S.DualOracle(dec)
+    o.iterate(iters)
+    ref = PR.round_primal(o, prob, fixed)
+    s = _solver(inst, d, allowed)
+    s.dual(iters)
+    x, cost, ok = s.primal()
+    assert ok and ref.ok
+    assert not np.any(prob.residual(x))  # integer-exact feasibility
+    # the library's c comes from FP32 pair costs; the oracle's from FP64 features
+    assert cost == pytest.approx(float(prob.cost @ x), rel=1e-6)
+    assert abs(cost - ref.cost) <= 1e-4 * abs(ref.cost)
+    s.close()
+
+
+def test_converge_stops_on_relative_change(torch):
+    inst, prob, d, allowed, fixed, dec = _oracle("config2", 0)
+    s = _solver(inst, d, allowed, lb_every=20, conv_rel_tol=1e-6)
+    n, lb, ok = s.converge(5000)
+    assert ok and n % 20 == 0 and n > 0
+    s.dual(20)
+    assert abs(s.lower_bound() - lb) < 1e-5 * abs(lb)
+    s.close()
+
+
+def test_errors_are_codes_not_crashes(torch):
+    from paper_2310_08230_gb300 import _lib as L
+
+    inst, prob, d, allowed, fixed, dec = _oracle("tet", 0)
+    s = _solver(inst, d, allowed)
+    small = np.zeros(3, np.float32)
+    rc = L.lib().disco_min_marginals(s.h, small.ctypes.data, 3)
+    assert rc == L.DISCO_ERR_INVALID_ARG
+    rc = L.lib().disco_dual(s.h, -1)
+    assert rc == L.DISCO_ERR_INVALID_ARG
+    s.dual(3)
+    assert np.isfinite(s.lower_bound())
+    s.close()

@@ -1,0 +1,115 @@
+"""CPU checks of the C ABI library without a GPU: it loads, exports every symbol that
+include/disco.h declares, and its host compiler (disco_compile_host) builds the same
+problem, presolve and BDD segments as the independently written oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import bdd as B
+from oracle import problem as P
+from synth import instances as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2310_08230_gb300 import _lib
+    from paper_2310_08230_gb300.build import build
+
+    build()
+    return _lib
+
+
+def test_library_exports_every_declared_symbol(L):
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(disco_[a-z_0-9]+)\s*\(", src, re.M))
+    assert len(names) >= 15
+    lib = L.lib()
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+        assert n in L.SIGNATURES, n
+
+
+def test_struct_layouts_match_header(L):
+    assert ctypes.sizeof(L.disco_opts) == 96
+    assert ctypes.sizeof(L.disco_info_t) == 160
+    assert ctypes.sizeof(L.disco_mesh) == 24
+
+
+def _compile(L, inst, allowed, d, chunk):
+    mx = L.disco_mesh(inst.X.nv, inst.X.nt, None, inst.X.T.ctypes.data)
+    my = L.disco_mesh(inst.Y.nv, inst.Y.nt, None, inst.Y.T.ctypes.data)
+    info = L.disco_info_t()
+    d32 = np.ascontiguousarray(d, np.float32)
+    a8 = None if allowed is None else np.ascontiguousarray(allowed, np.uint8)
+    args = (ctypes.byref(mx), ctypes.byref(my), d32.ctypes.data, None if a8 is None else a8.ctypes.data, chunk,
+            ctypes.byref(info))
+    L.check(L.lib().disco_compile_host(*args, None, None, 0, None, 0), "compile")
+    sv = np.empty(info.nslots, np.int32)
+    sw = np.empty(info.nslots, np.int32)
+    fx = np.empty(info.nvars, np.int8)
+    L.check(L.lib().disco_compile_host(*args, sv.ctypes.data, sw.ctypes.data, sv.shape[0], fx.ctypes.data,
+                                       fx.shape[0]), "compile")
+    return info, sv, sw, fx
+
+
+@pytest.mark.parametrize("which,chunk", [("tet", 0), ("tet", 5), ("config1", 0), ("config1", 7), ("config2", 0),
+                                         ("config2", 16)])
+def test_host_compiler_matches_oracle(L, which, chunk):
+    inst = getattr(I, which)()
+    prob, d, allowed = P.make_problem(inst)
+    fixed, const = P.presolve(prob)
+    dec = B.decompose(prob, fixed, const, chunk)
+    info, sv, sw, fx = _compile(L, inst, None if inst.topk is None else allowed, d, chunk)
+    assert info.nvars == prob.nvars
+    assert info.nrows == prob.nrows
+    assert np.array_equal(fx, fixed)
+    assert info.nvars_free == int((fixed < 0).sum())
+    assert info.nvars_aux == dec.nvars_total - dec.nvars
+    assert info.nbdds == dec.nb
+    assert np.array_equal(sv, dec.layer_var)
+    assert np.array_equal(sw, np.diff(dec.layer_node_ptr))
+    assert info.nnodes == dec.n_nodes
+    assert info.constant == pytest.approx(const, abs=1e-6)
+
+
+def test_host_compiler_errors(L):
+    inst = I.config1()
+    d = np.ones((inst.X.nv, inst.Y.nv), np.float32)
+    info = L.disco_info_t()
+    mx = L.disco_mesh(inst.X.nv, inst.X.nt, None, inst.X.T.ctypes.data)
+    # genus mismatch: torus vs icosahedron
+    from synth import meshes as M
+    t = M.torus(3, 4)
+    mt = L.disco_mesh(t.nv, t.nt, None, t.T.ctypes.data)
+    dt = np.ones((inst.X.nv, t.nv), np.float32)
+    rc = L.lib().disco_compile_host(ctypes.byref(mx), ctypes.byref(mt), dt.ctypes.data, None, 0, ctypes.byref(info),
+                                    None, None, 0, None, 0)
+    assert rc == L.DISCO_ERR_GENUS_MISMATCH
+    # flipped triangle
+    T = inst.Y.T.copy()
+    T[0] = T[0][[0, 2, 1]]
+    my = L.disco_mesh(inst.Y.nv, inst.Y.nt, None, T.ctypes.data)
+    rc = L.lib().disco_compile_host(ctypes.byref(mx), ctypes.byref(my), d.ctypes.data, None, 0, ctypes.byref(info),
+                                    None, None, 0, None, 0)
+    assert rc == L.DISCO_ERR_NONMANIFOLD
+    # negative / NaN costs
+    bad = d.copy()
+    bad[0, 0] = np.nan
+    my = L.disco_mesh(inst.Y.nv, inst.Y.nt, None, inst.Y.T.ctypes.data)
+    rc = L.lib().disco_compile_host(ctypes.byref(mx), ctypes.byref(my), bad.ctypes.data, None, 0, ctypes.byref(info),
+                                    None, None, 0, None, 0)
+    assert rc == L.DISCO_ERR_INVALID_ARG
+    # a candidate mask that leaves a triangle without any element
+    allowed = np.zeros((inst.X.nv, inst.Y.nv), np.uint8)
+    rc = L.lib().disco_compile_host(ctypes.byref(mx), ctypes.byref(my), d.ctypes.data, allowed.ctypes.data, 0,
+                                    ctypes.byref(info), None, None, 0, None, 0)
+    assert rc == L.DISCO_ERR_INFEASIBLE
+    assert b"element" in L.lib().disco_last_error() or b"empty" in L.lib().disco_last_error()
