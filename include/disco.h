@@ -117,6 +117,22 @@ int disco_candidates(const float *d, int32_t nvx, int32_t nvy, int32_t k, const 
                      const disco_mesh *Y, uint8_t *allowed, void *stream);
 
 /*
+ * disco_candidates without any allocation. The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate memory while they run (a fixed device
+ * budget owned by another allocator, latency-critical loops that cannot afford an
+ * allocation's synchronisation). Same inputs and output as disco_candidates; every
+ * temporary lives in one fixed library-owned device array of 3.75 MiB that each device
+ * loading the library holds until the process exits. Limits: at most 16384 vertices and
+ * 32768 triangles per mesh, 1 <= k <= 32 (and k <= both vertex counts); larger sizes return
+ * DISCO_ERR_INVALID_ARG before any GPU work. The first call on a device resolves the
+ * array's address (make it before any stream capture). All calls on a device share the
+ * array: calls whose GPU work overlaps race and must be serialised by the caller. Each call
+ * clears what it needs and synchronises `stream` before returning.
+ */
+int disco_candidates_noalloc(const float *d, int32_t nvx, int32_t nvy, int32_t k, const disco_mesh *X,
+                             const disco_mesh *Y, uint8_t *allowed, void *stream);
+
+/*
  * Builds the problem and the device BDD store (host compiler + one upload):
  * product space restricted to `allowed` (nvx*nvy uint8, host or device; NULL = full
  * product space), costs c_p = mean of the three pair costs d (nvx*nvy float, host or

@@ -52,6 +52,8 @@ SIGNATURES = {
     "disco_default_opts": (ctypes.c_int, [ctypes.POINTER(disco_opts)]),
     "disco_pair_costs": (ctypes.c_int, [P, P, I32, I32, I32, P, P]),
     "disco_candidates": (ctypes.c_int, [P, I32, I32, I32, ctypes.POINTER(disco_mesh), ctypes.POINTER(disco_mesh), P, P]),
+    "disco_candidates_noalloc": (ctypes.c_int, [P, I32, I32, I32, ctypes.POINTER(disco_mesh),
+                                                ctypes.POINTER(disco_mesh), P, P]),
     "disco_build": (ctypes.c_int, [ctypes.POINTER(disco_mesh), ctypes.POINTER(disco_mesh), P, P,
                                    ctypes.POINTER(disco_opts), ctypes.POINTER(ctypes.c_void_p)]),
     "disco_compile_host": (ctypes.c_int, [ctypes.POINTER(disco_mesh), ctypes.POINTER(disco_mesh), P, P, I32,
