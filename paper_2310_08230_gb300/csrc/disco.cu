@@ -176,23 +176,43 @@ int upload(disco_handle* h) {
     });
     std::vector<TileInfo> tiles;
     std::vector<std::vector<int64_t>> tile_segs;
-    h->classes.clear();
-    int64_t slot_base = 0, node_base = 0;
     for (int64_t i = 0; i < nseg;) {
         const int W = width_class(P.segs[order[i]].max_width);
-        WidthClass wc{W, int(tiles.size()), 0};
-        while (i < nseg && width_class(P.segs[order[i]].max_width) == W) {
-            std::vector<int64_t> ts;
-            for (int k = 0; k < 32 && i < nseg && width_class(P.segs[order[i]].max_width) == W; ++k, ++i) ts.push_back(order[i]);
-            int L = 0;
-            for (int64_t sg : ts) L = std::max(L, P.segs[sg].n_layers);
-            tiles.push_back(TileInfo{slot_base, node_base, L, W});
-            tile_segs.push_back(ts);
-            slot_base += int64_t(L) * 32;
-            node_base += int64_t(L + 1) * W * 32;
+        std::vector<int64_t> ts;
+        for (int k = 0; k < 32 && i < nseg && width_class(P.segs[order[i]].max_width) == W; ++k, ++i) ts.push_back(order[i]);
+        int L = 0;
+        for (int64_t sg : ts) L = std::max(L, P.segs[sg].n_layers);
+        tiles.push_back(TileInfo{0, 0, L, W});
+        tile_segs.push_back(ts);
+    }
+    // classes 2, 4, 8 share one launch, longest tiles first; 16 and 32 launch on their own
+    std::vector<size_t> tord(tiles.size());
+    std::iota(tord.begin(), tord.end(), size_t(0));
+    std::stable_sort(tord.begin(), tord.end(), [&](size_t a, size_t b) {
+        const int ga = tiles[a].W <= 8 ? 0 : tiles[a].W, gb = tiles[b].W <= 8 ? 0 : tiles[b].W;
+        if (ga != gb) return ga < gb;
+        return tiles[a].L > tiles[b].L;
+    });
+    {
+        std::vector<TileInfo> t2;
+        std::vector<std::vector<int64_t>> s2;
+        for (size_t k : tord) {
+            t2.push_back(tiles[k]);
+            s2.push_back(tile_segs[k]);
         }
-        wc.tile_end = int(tiles.size());
-        h->classes.push_back(wc);
+        tiles.swap(t2);
+        tile_segs.swap(s2);
+    }
+    h->classes.clear();
+    int64_t slot_base = 0, node_base = 0;
+    for (size_t t = 0; t < tiles.size(); ++t) {
+        const int group = tiles[t].W <= 8 ? 0 : tiles[t].W;
+        if (h->classes.empty() || h->classes.back().W != group) h->classes.push_back(WidthClass{group, int(t), int(t)});
+        h->classes.back().tile_end = int(t) + 1;
+        tiles[t].slot_base = slot_base;
+        tiles[t].node_base = node_base;
+        slot_base += int64_t(tiles[t].L) * 32;
+        node_base += int64_t(tiles[t].L + 1) * tiles[t].W * 32;
     }
     h->ntiles = int64_t(tiles.size());
     h->nslots_tile = slot_base;

@@ -23,11 +23,15 @@
 // sigma in [max(-Q_pre, r - P_suf), min(P_pre, r + Q_suf)] (P / Q: counts of +1 / -1
 // coefficients before / from layer l). Node s of a layer stands for sigma = lo + s.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <memory>
 #include <cstring>
 #include <numeric>
+#include <string>
 #include <thread>
 #include <utility>
+#include <vector>
 
 #include "../../include/disco.h"
 #include "plan.h"
@@ -38,13 +42,37 @@ namespace {
 // vertex sequence of a degenerate triangle over an edge (a < b): 0 -> a, 1 -> b
 const int kEdgePattern[6][3] = {{0, 0, 1}, {0, 1, 0}, {1, 0, 0}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
 
+// Compressed incidence list: the items of vertex v are item[ptr[v] .. ptr[v+1]).
+template <class T>
+struct Csr {
+    std::vector<int32_t> ptr;
+    std::vector<T> item;
+    template <class F>
+    void for_each(int v, F f) const {
+        for (int32_t i = ptr[v]; i < ptr[v + 1]; ++i) f(item[i]);
+    }
+};
+
 struct MeshTopo {
     int nv = 0, nt = 0;
     const int32_t* T = nullptr;
-    std::vector<std::pair<int, int>> edges;     // sorted unique (a < b)
-    std::vector<std::vector<std::pair<int, int>>> tri_at;  // vertex -> (triangle, corner)
-    std::vector<std::vector<int>> edge_at;      // vertex -> incident edges
+    std::vector<std::pair<int, int>> edges;  // sorted unique (a < b)
+    Csr<std::pair<int, int>> tri_at;         // vertex -> (triangle, corner), ascending triangle
+    Csr<int32_t> tri_at0;                    // vertex -> triangles having it as corner 0
+    Csr<int32_t> edge_at;                    // vertex -> incident edges, ascending
 };
+
+template <class T, class Fill>
+Csr<T> make_csr(int nv, int64_t nitems, Fill fill) {
+    Csr<T> c;
+    c.ptr.assign(size_t(nv) + 1, 0);
+    fill([&](int v, const T&) { ++c.ptr[v + 1]; });
+    for (int v = 0; v < nv; ++v) c.ptr[v + 1] += c.ptr[v];
+    c.item.resize(size_t(nitems));
+    std::vector<int32_t> pos(c.ptr.begin(), c.ptr.end() - 1);
+    fill([&](int v, const T& x) { c.item[pos[v]++] = x; });
+    return c;
+}
 
 int topo(const MeshIn& m, MeshTopo* t, int* chi, std::string* err) {
     if (m.nv <= 0 || m.nt <= 0 || !m.T) { *err = "empty mesh"; return DISCO_ERR_INVALID_ARG; }
@@ -74,21 +102,27 @@ int topo(const MeshIn& m, MeshTopo* t, int* chi, std::string* err) {
     for (int v = 0; v < m.nv; ++v)
         if (!used[v]) { *err = "isolated vertex"; return DISCO_ERR_NONMANIFOLD; }
     *chi = m.nv - int(t->edges.size()) + m.nt;
-    t->tri_at.assign(m.nv, {});
-    for (int f = 0; f < m.nt; ++f)
-        for (int k = 0; k < 3; ++k) t->tri_at[m.T[3 * f + k]].emplace_back(f, k);
-    t->edge_at.assign(m.nv, {});
-    for (int e = 0; e < int(t->edges.size()); ++e) {
-        t->edge_at[t->edges[e].first].push_back(e);
-        t->edge_at[t->edges[e].second].push_back(e);
-    }
+    t->tri_at = make_csr<std::pair<int, int>>(m.nv, 3 * int64_t(m.nt), [&](auto add) {
+        for (int f = 0; f < m.nt; ++f)
+            for (int k = 0; k < 3; ++k) add(m.T[3 * f + k], std::pair<int, int>(f, k));
+    });
+    t->tri_at0 = make_csr<int32_t>(m.nv, m.nt, [&](auto add) {
+        for (int f = 0; f < m.nt; ++f) add(m.T[3 * f], int32_t(f));
+    });
+    const int ne = int(t->edges.size());
+    t->edge_at = make_csr<int32_t>(m.nv, 2 * int64_t(ne), [&](auto add) {
+        for (int e = 0; e < ne; ++e) {
+            add(t->edges[e].first, int32_t(e));
+            add(t->edges[e].second, int32_t(e));
+        }
+    });
     return DISCO_OK;
 }
 
 struct Elems {  // matching elements, structure of arrays
-    std::vector<int32_t> m, n;  // 3 per element
-    std::vector<uint8_t> type;
-    std::vector<int32_t> xe, ye;
+    pod_vector<int32_t> m, n;  // 3 per element
+    pod_vector<uint8_t> type;
+    pod_vector<int32_t> xe, ye;
     void push(int m0, int m1, int m2, int n0, int n1, int n2, int ty, int x, int y) {
         m.push_back(m0); m.push_back(m1); m.push_back(m2);
         n.push_back(n0); n.push_back(n1); n.push_back(n2);
@@ -106,27 +140,58 @@ struct Elems {  // matching elements, structure of arrays
     size_t size() const { return type.size(); }
 };
 
+// Candidate pairs: a bit row per X vertex (cache resident) and the allowed Y vertices of
+// every X vertex in ascending order.
 struct Allowed {
-    const uint8_t* mask;  // nullptr: every pair
-    int nvx, nvy;
-    std::vector<std::vector<int>> row;  // m -> allowed n, ascending
-    bool operator()(int a, int b) const { return !mask || mask[size_t(a) * nvy + b]; }
+    bool full = true;
+    int words = 0;
+    std::vector<uint64_t> bits;
+    Csr<int32_t> row;
+    bool operator()(int a, int b) const {
+        return full || ((bits[size_t(a) * words + (b >> 6)] >> (b & 63)) & 1u);
+    }
 };
 
 // Runs body(lo, hi, out) over [0, n) in contiguous chunks on up to `threads` threads and
 // concatenates the per-chunk outputs in order (the result does not depend on threads).
 template <class F>
 void chunked(int n, int threads, Elems* out, F body) {
-    int nch = std::max(1, std::min(threads, n / 64 + 1));
+    int nch = std::max(1, std::min(threads * 4, n / 16 + 1));
     std::vector<Elems> parts(nch);
-    std::vector<std::thread> pool;
-    for (int c = 0; c < nch; ++c) {
-        int lo = int(int64_t(n) * c / nch), hi = int(int64_t(n) * (c + 1) / nch);
-        if (nch == 1) body(lo, hi, &parts[c]);
-        else pool.emplace_back([&, lo, hi, c] { body(lo, hi, &parts[c]); });
-    }
-    for (auto& th : pool) th.join();
-    for (auto& p : parts) out->append(p);
+    std::atomic<int> next{0};
+    auto run = [&](auto&& job, int njobs) {
+        next = 0;
+        std::vector<std::thread> pool;
+        auto worker = [&] {
+            for (int c; (c = next.fetch_add(1)) < njobs;) job(c);
+        };
+        for (int t = 1; t < std::min(threads, njobs); ++t) pool.emplace_back(worker);
+        worker();
+        for (auto& th : pool) th.join();
+    };
+    run([&](int c) {
+        const int lo = int(int64_t(n) * c / nch), hi = int(int64_t(n) * (c + 1) / nch);
+        body(lo, hi, &parts[c]);
+    }, nch);
+    // concatenate in chunk order, copying the parts in parallel
+    std::vector<size_t> off(nch + 1, out->size());
+    for (int c = 0; c < nch; ++c) off[c + 1] = off[c] + parts[c].size();
+    const size_t total = off[nch];
+    out->m.resize(3 * total);
+    out->n.resize(3 * total);
+    out->type.resize(total);
+    out->xe.resize(total);
+    out->ye.resize(total);
+    run([&](int c) {
+        const Elems& p = parts[c];
+        const size_t o = off[c];
+        std::copy(p.m.begin(), p.m.end(), out->m.begin() + 3 * o);
+        std::copy(p.n.begin(), p.n.end(), out->n.begin() + 3 * o);
+        std::copy(p.type.begin(), p.type.end(), out->type.begin() + o);
+        std::copy(p.xe.begin(), p.xe.end(), out->xe.begin() + o);
+        std::copy(p.ye.begin(), p.ye.end(), out->ye.begin() + o);
+        Elems().m.swap(parts[c].m);
+    }, nch);
 }
 
 void enumerate(const MeshTopo& X, const MeshTopo& Y, const Allowed& A, int threads, Elems* out) {
@@ -138,9 +203,12 @@ void enumerate(const MeshTopo& X, const MeshTopo& Y, const Allowed& A, int threa
         for (int t = lo; t < hi; ++t) {
             int m0 = TX[3 * t], m1 = TX[3 * t + 1], m2 = TX[3 * t + 2];
             cand.clear();
-            for (int n0 : A.row[m0])
-                for (auto [s, r] : Y.tri_at[n0])
+            A.row.for_each(m0, [&](int n0) {
+                Y.tri_at.for_each(n0, [&](std::pair<int, int> sr) {
+                    const int s = sr.first, r = sr.second;
                     if (A(m1, TY[3 * s + (r + 1) % 3]) && A(m2, TY[3 * s + (r + 2) % 3])) cand.push_back(int64_t(s) * 3 + r);
+                });
+            });
             std::sort(cand.begin(), cand.end());
             for (int64_t c : cand) {
                 int s = int(c / 3), r = int(c % 3);
@@ -154,13 +222,15 @@ void enumerate(const MeshTopo& X, const MeshTopo& Y, const Allowed& A, int threa
         for (int t = lo; t < hi; ++t) {
             int m[3] = {TX[3 * t], TX[3 * t + 1], TX[3 * t + 2]};
             cand.clear();
-            for (int n0 : A.row[m[0]])
-                for (int e : Y.edge_at[n0]) {
-                    int ab[2] = {Y.edges[e].first, Y.edges[e].second};
+            A.row.for_each(m[0], [&](int n0) {
+                Y.edge_at.for_each(n0, [&](int e) {
+                    const int ab[2] = {Y.edges[e].first, Y.edges[e].second};
+                    const int role = ab[0] == n0 ? 0 : 1;  // patterns whose first corner is n0
                     for (int p = 0; p < 6; ++p)
-                        if (ab[kEdgePattern[p][0]] == n0 && A(m[1], ab[kEdgePattern[p][1]]) && A(m[2], ab[kEdgePattern[p][2]]))
+                        if (kEdgePattern[p][0] == role && A(m[1], ab[kEdgePattern[p][1]]) && A(m[2], ab[kEdgePattern[p][2]]))
                             cand.push_back(int64_t(e) * 6 + p);
-                }
+                });
+            });
             std::sort(cand.begin(), cand.end());
             for (int64_t c : cand) {
                 int e = int(c / 6), p = int(c % 6);
@@ -177,9 +247,11 @@ void enumerate(const MeshTopo& X, const MeshTopo& Y, const Allowed& A, int threa
             cand.clear();
             for (int p = 0; p < 6; ++p) {
                 int x0 = ab[kEdgePattern[p][0]], x1 = ab[kEdgePattern[p][1]], x2 = ab[kEdgePattern[p][2]];
-                for (int n0 : A.row[x0])
-                    for (auto [s, r] : Y.tri_at[n0])
-                        if (r == 0 && A(x1, TY[3 * s + 1]) && A(x2, TY[3 * s + 2])) cand.push_back(int64_t(s) * 6 + p);
+                A.row.for_each(x0, [&](int n0) {
+                    Y.tri_at0.for_each(n0, [&](int s) {
+                        if (A(x1, TY[3 * s + 1]) && A(x2, TY[3 * s + 2])) cand.push_back(int64_t(s) * 6 + p);
+                    });
+                });
             }
             std::sort(cand.begin(), cand.end());
             for (int64_t c : cand) {
@@ -193,8 +265,9 @@ void enumerate(const MeshTopo& X, const MeshTopo& Y, const Allowed& A, int threa
     chunked(X.nt, threads, out, [&](int lo, int hi, Elems* o) {
         for (int t = lo; t < hi; ++t) {
             int m0 = TX[3 * t], m1 = TX[3 * t + 1], m2 = TX[3 * t + 2];
-            for (int n : A.row[m0])
+            A.row.for_each(m0, [&](int n) {
                 if (A(m1, n) && A(m2, n)) o->push(m0, m1, m2, n, n, n, 3, t, n);
+            });
         }
     });
     // type 4: X vertex m, Y triangle s
@@ -202,35 +275,56 @@ void enumerate(const MeshTopo& X, const MeshTopo& Y, const Allowed& A, int threa
         std::vector<int> cand;
         for (int mv = lo; mv < hi; ++mv) {
             cand.clear();
-            for (int n0 : A.row[mv])
-                for (auto [s, r] : Y.tri_at[n0])
-                    if (r == 0 && A(mv, TY[3 * s + 1]) && A(mv, TY[3 * s + 2])) cand.push_back(s);
+            A.row.for_each(mv, [&](int n0) {
+                Y.tri_at0.for_each(n0, [&](int s) {
+                    if (A(mv, TY[3 * s + 1]) && A(mv, TY[3 * s + 2])) cand.push_back(s);
+                });
+            });
             std::sort(cand.begin(), cand.end());
             for (int s : cand) o->push(mv, mv, mv, TY[3 * s], TY[3 * s + 1], TY[3 * s + 2], 4, mv, s);
         }
     });
 }
 
-// Stable LSD radix sort of (key, payload) by key.
-void radix_sort(std::vector<uint64_t>& key, std::vector<uint32_t>& val) {
-    size_t n = key.size();
-    uint64_t mx = 0;
-    for (uint64_t k : key) mx = std::max(mx, k);
-    std::vector<uint64_t> k2(n);
-    std::vector<uint32_t> v2(n);
-    for (int shift = 0; shift < 64 && (mx >> shift); shift += 16) {
-        std::vector<size_t> cnt(65537, 0);
-        for (size_t i = 0; i < n; ++i) ++cnt[((key[i] >> shift) & 0xFFFF) + 1];
-        for (int b = 0; b < 65536; ++b) cnt[b + 1] += cnt[b];
-        for (size_t i = 0; i < n; ++i) {
-            size_t p = cnt[(key[i] >> shift) & 0xFFFF]++;
-            k2[p] = key[i];
-            v2[p] = val[i];
-        }
-        key.swap(k2);
-        val.swap(v2);
+// Runs body(chunk, lo, hi) over [0, n) split into `nch` contiguous chunks on threads.
+template <class F>
+void parallel_chunks(int64_t n, int nch, F body) {
+    if (nch <= 1 || n < 2) {
+        body(0, int64_t(0), n);
+        return;
     }
+    std::vector<std::thread> pool;
+    for (int c = 0; c < nch; ++c) {
+        const int64_t lo = n * c / nch, hi = n * (c + 1) / nch;
+        pool.emplace_back([&body, c, lo, hi] { body(c, lo, hi); });
+    }
+    for (auto& th : pool) th.join();
 }
+
+// One boundary edge of one element: its smaller product vertex (m, n) is implied by the
+// bucket (m) and `lo_n`; `hi` is the larger product vertex m' * nvy + n'; `id` packs the
+// entry 3 * element + corner and the direction bit.
+struct EdgeEntry {
+    uint32_t lo_n;
+    uint32_t hi;
+    uint32_t id;
+    bool operator<(const EdgeEntry& o) const {
+        return lo_n != o.lo_n ? lo_n < o.lo_n : (hi != o.hi ? hi < o.hi : id < o.id);
+    }
+    bool same_edge(const EdgeEntry& o) const { return lo_n == o.lo_n && hi == o.hi; }
+};
+
+// BDD segments of a contiguous range of rows, with auxiliary ids local to the range.
+struct RowChunk {
+    std::vector<int32_t> var;   // internal variable id; auxiliaries as -1 - local index
+    std::vector<int32_t> w, wn, d0, d1;
+    std::vector<uint8_t> one, rank;
+    std::vector<Segment> segs;  // first_slot local to the chunk
+    int64_t n_aux = 0, nodes = 0;
+    int max_layers = 0, max_width = 0;
+    std::string err;
+    int rc = 0;
+};
 
 }  // namespace
 
@@ -250,11 +344,35 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     P->nvy = nvy;
 
     // ---- candidate rows
-    Allowed A{mask, nvx, nvy, {}};
-    A.row.assign(nvx, {});
-    for (int m = 0; m < nvx; ++m)
-        for (int n = 0; n < nvy; ++n)
-            if (A(m, n)) A.row[m].push_back(n);
+    Allowed A;
+    A.full = mask == nullptr;
+    A.words = (nvy + 63) / 64;
+    A.row.ptr.assign(size_t(nvx) + 1, 0);
+    if (!A.full) {
+        A.bits.assign(size_t(nvx) * A.words, 0);
+        parallel_chunks(nvx, threads, [&](int, int64_t lo, int64_t hi) {
+            for (int64_t m = lo; m < hi; ++m) {
+                int32_t c = 0;
+                for (int n = 0; n < nvy; ++n)
+                    if (mask[size_t(m) * nvy + n]) {
+                        A.bits[size_t(m) * A.words + (n >> 6)] |= uint64_t(1) << (n & 63);
+                        ++c;
+                    }
+                A.row.ptr[m + 1] = c;
+            }
+        });
+    } else {
+        for (int m = 0; m < nvx; ++m) A.row.ptr[m + 1] = nvy;
+    }
+    for (int m = 0; m < nvx; ++m) A.row.ptr[m + 1] += A.row.ptr[m];
+    A.row.item.resize(size_t(A.row.ptr[nvx]));
+    parallel_chunks(nvx, threads, [&](int, int64_t lo, int64_t hi) {
+        for (int64_t m = lo; m < hi; ++m) {
+            int32_t o = A.row.ptr[m];
+            for (int n = 0; n < nvy; ++n)
+                if (A(int(m), n)) A.row.item[o++] = n;
+        }
+    });
 
     // ---- product space
     Elems E;
@@ -267,126 +385,264 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     P->vn = std::move(E.n);
 
     // ---- costs: mean of the three pair costs, normalised by the largest
+    const int nth = threads;
     P->cost.resize(nv);
-    double cmax = 0.0;
-    for (int64_t i = 0; i < nv; ++i) {
-        double c = 0.0;
-        for (int v = 0; v < 3; ++v) c += double(d[size_t(P->vm[3 * i + v]) * nvy + P->vn[3 * i + v]]);
-        c /= 3.0;
-        if (!(c >= 0.0) || c > 3.0e38) { *err = "pair costs must be finite and >= 0"; return DISCO_ERR_INVALID_ARG; }
-        P->cost[i] = c;
-        cmax = std::max(cmax, c);
+    {
+        std::vector<double> cmaxs(nth, 0.0);
+        std::vector<int> bad(nth, 0);
+        parallel_chunks(nv, nth, [&](int c, int64_t lo, int64_t hi) {
+            for (int64_t i = lo; i < hi; ++i) {
+                double x = 0.0;
+                for (int v = 0; v < 3; ++v) x += double(d[size_t(P->vm[3 * i + v]) * nvy + P->vn[3 * i + v]]);
+                x /= 3.0;
+                if (!(x >= 0.0) || x > 3.0e38) bad[c] = 1;
+                P->cost[i] = x;
+                cmaxs[c] = std::max(cmaxs[c], x);
+            }
+        });
+        for (int c = 0; c < nth; ++c)
+            if (bad[c]) { *err = "pair costs must be finite and >= 0"; return DISCO_ERR_INVALID_ARG; }
+        const double cmax = *std::max_element(cmaxs.begin(), cmaxs.end());
+        if (cmax > 0) parallel_chunks(nv, nth, [&](int, int64_t lo, int64_t hi) {
+            for (int64_t i = lo; i < hi; ++i) P->cost[i] /= cmax;
+        });
     }
-    if (cmax > 0)
-        for (double& c : P->cost) c /= cmax;
 
-    // ---- closedness rows: product edge (p, q), p < q in (m, n) order
-    const uint64_t K = uint64_t(nvx) * uint64_t(nvy);
-    std::vector<uint64_t> key(size_t(3) * nv);
-    std::vector<uint32_t> pay(size_t(3) * nv);
-    for (int64_t i = 0; i < nv; ++i)
-        for (int v = 0; v < 3; ++v) {
-            int w = (v + 1) % 3;
-            uint64_t a = uint64_t(P->vm[3 * i + v]) * nvy + P->vn[3 * i + v];
-            uint64_t b = uint64_t(P->vm[3 * i + w]) * nvy + P->vn[3 * i + w];
-            key[3 * i + v] = std::min(a, b) * K + std::max(a, b);
-            pay[3 * i + v] = uint32_t(i) * 2u + (a < b ? 0u : 1u);
+    // ---- closedness rows: product edge (p, q), p < q in (m, n) order. Entries are bucketed by
+    // the X vertex of p, each bucket sorted by (key, entry), rows are the runs of equal keys.
+    if (uint64_t(nvx) * uint64_t(nvy) >= (uint64_t(1) << 32)) { *err = "meshes too large"; return DISCO_ERR_INVALID_ARG; }
+    const int64_t ne = 3 * nv;
+    if (ne >= (int64_t(1) << 31)) { *err = "product space too large"; return DISCO_ERR_INVALID_ARG; }
+    std::unique_ptr<EdgeEntry[]> ent(new EdgeEntry[size_t(ne)]);
+    std::vector<int64_t> bstart(size_t(nvx) + 1, 0);
+    {
+        // corner v of element i and corner v+1: (m, n) pairs, ordered lexicographically
+        auto edge_of = [&](int64_t i, int v, int* lm, EdgeEntry* out) {
+            const int w = (v + 1) % 3;
+            const int ma = P->vm[3 * i + v], na = P->vn[3 * i + v];
+            const int mb = P->vm[3 * i + w], nb = P->vn[3 * i + w];
+            const bool fwd = ma < mb || (ma == mb && na < nb);
+            *lm = fwd ? ma : mb;
+            out->lo_n = uint32_t(fwd ? na : nb);
+            out->hi = fwd ? uint32_t(mb) * uint32_t(nvy) + uint32_t(nb) : uint32_t(ma) * uint32_t(nvy) + uint32_t(na);
+            out->id = uint32_t(3 * i + v) * 2u + (fwd ? 0u : 1u);
+        };
+        std::vector<std::vector<int64_t>> cnt(nth, std::vector<int64_t>(size_t(nvx), 0));
+        parallel_chunks(nv, nth, [&](int c, int64_t lo, int64_t hi) {
+            for (int64_t i = lo; i < hi; ++i)
+                for (int v = 0; v < 3; ++v) {
+                    int lm;
+                    EdgeEntry x;
+                    edge_of(i, v, &lm, &x);
+                    ++cnt[c][lm];
+                }
+        });
+        // bucket offsets per (bucket, chunk) in chunk order: entries keep their id order per bucket
+        std::vector<std::vector<int64_t>> off(nth, std::vector<int64_t>(size_t(nvx), 0));
+        int64_t run = 0;
+        for (int m = 0; m < nvx; ++m) {
+            bstart[m] = run;
+            for (int c = 0; c < nth; ++c) {
+                off[c][m] = run;
+                run += cnt[c][m];
+            }
         }
-    radix_sort(key, pay);
-    P->row_ptr.clear();
-    P->row_var.resize(key.size());
-    P->row_coef.resize(key.size());
-    for (size_t e = 0; e < key.size(); ++e) {
-        if (e == 0 || key[e] != key[e - 1]) P->row_ptr.push_back(int64_t(e));
-        P->row_var[e] = int32_t(pay[e] >> 1);
-        P->row_coef[e] = (pay[e] & 1u) ? -1 : 1;
+        bstart[nvx] = run;
+        parallel_chunks(nv, nth, [&](int c, int64_t lo, int64_t hi) {
+            for (int64_t i = lo; i < hi; ++i)
+                for (int v = 0; v < 3; ++v) {
+                    int lm;
+                    EdgeEntry x;
+                    edge_of(i, v, &lm, &x);
+                    ent[off[c][lm]++] = x;
+                }
+        });
     }
-    P->n_closed = int64_t(P->row_ptr.size());
-    P->rhs.assign(size_t(P->n_closed), 0);
-    key.clear(); key.shrink_to_fit();
-    pay.clear(); pay.shrink_to_fit();
+    // order each bucket by (smaller vertex, larger vertex, entry); count rows per bucket
+    std::vector<int64_t> brows(size_t(nvx) + 1, 0);
+    const bool packed = nvy < (1 << 16);
+    parallel_chunks(nth * 4, nth, [&](int, int64_t c0, int64_t c1) {
+        std::vector<uint64_t> key;
+        std::vector<EdgeEntry> tmp;
+        for (int64_t c = c0; c < c1; ++c)
+            for (int64_t m = int64_t(nvx) * c / (nth * 4); m < int64_t(nvx) * (c + 1) / (nth * 4); ++m) {
+                const int64_t b0 = bstart[m], b1 = bstart[m + 1], nb = b1 - b0;
+                if (packed && nb < (int64_t(1) << 16)) {
+                    // entries arrive in id order: (lo_n, hi, position) in one integer sorts them
+                    key.resize(size_t(nb));
+                    for (int64_t e = 0; e < nb; ++e)
+                        key[e] = (uint64_t(ent[b0 + e].lo_n) << 48) | (uint64_t(ent[b0 + e].hi) << 16) | uint64_t(e);
+                    std::sort(key.begin(), key.end());
+                    tmp.assign(ent.get() + b0, ent.get() + b1);
+                    for (int64_t e = 0; e < nb; ++e) ent[b0 + e] = tmp[key[e] & 0xFFFFu];
+                } else {
+                    std::sort(ent.get() + b0, ent.get() + b1);
+                }
+                int64_t r = 0;
+                for (int64_t e = b0; e < b1; ++e)
+                    if (e == b0 || !ent[e].same_edge(ent[e - 1])) ++r;
+                brows[m + 1] = r;
+            }
+    });
+    for (int m = 0; m < nvx; ++m) brows[m + 1] += brows[m];
+    const int64_t n_closed = brows[nvx];
+    P->n_closed = n_closed;
+    P->row_ptr.assign(size_t(n_closed), 0);
+    // projection entries: elements whose X (Y) side is a triangle; all rows are sized once
+    int64_t nproj_entries = 0;
+    for (int64_t i = 0; i < nv; ++i) nproj_entries += (E.type[i] == 0) ? 2 : 1;
+    P->row_var.resize(size_t(ne + nproj_entries));
+    P->row_coef.resize(size_t(ne + nproj_entries));
+    pod_vector<int32_t> row_ent(static_cast<size_t>(ne + nproj_entries));  // corner (0..2) or 3 + side
+    pod_vector<int64_t> elem_row(static_cast<size_t>(ne));     // element corner -> its closedness row
+    parallel_chunks(nvx, nth * 4, [&](int, int64_t lo, int64_t hi) {
+        for (int64_t m = lo; m < hi; ++m) {
+            int64_t r = brows[m] - 1;
+            for (int64_t e = bstart[m]; e < bstart[m + 1]; ++e) {
+                if (e == bstart[m] || !ent[e].same_edge(ent[e - 1])) P->row_ptr[++r] = e;
+                const uint32_t id = ent[e].id >> 1;
+                P->row_var[e] = int32_t(id / 3);
+                P->row_coef[e] = (ent[e].id & 1u) ? -1 : 1;
+                row_ent[e] = int32_t(id % 3);
+                elem_row[id] = r;
+            }
+        }
+    });
+    ent.reset();
+    P->rhs.assign(size_t(n_closed), 0);
 
-    // ---- projection rows (counting sort keeps variable order inside a row)
+    // ---- projection rows (counting sort keeps the element order inside a row)
+    std::vector<int32_t> proj_row(size_t(2) * nv, -1);  // element -> X / Y projection row
+    int64_t proj_end = ne;
     for (int side = 0; side < 2; ++side) {
-        int ntri = side == 0 ? X.nt : Y.nt;
-        std::vector<int64_t> cnt(ntri + 1, 0);
+        const int ntri = side == 0 ? X.nt : Y.nt;
         auto tri_of = [&](int64_t i) -> int {
-            int ty = E.type[i];
+            const int ty = E.type[i];
             if (side == 0) return (ty == 0 || ty == 1 || ty == 3) ? E.xe[i] : -1;
             return (ty == 0 || ty == 2 || ty == 4) ? E.ye[i] : -1;
         };
-        for (int64_t i = 0; i < nv; ++i) {
-            int t = tri_of(i);
-            if (t >= 0) ++cnt[t + 1];
+        std::vector<std::vector<int64_t>> cnt(nth, std::vector<int64_t>(size_t(ntri), 0));
+        parallel_chunks(nv, nth, [&](int c, int64_t lo, int64_t hi) {
+            for (int64_t i = lo; i < hi; ++i) {
+                const int t = tri_of(i);
+                if (t >= 0) ++cnt[c][t];
+            }
+        });
+        const int64_t base = proj_end;
+        const int64_t row0 = int64_t(P->row_ptr.size());
+        std::vector<std::vector<int64_t>> off(nth, std::vector<int64_t>(size_t(ntri), 0));
+        int64_t run = base;
+        for (int t = 0; t < ntri; ++t) {
+            int64_t tot = 0;
+            for (int c = 0; c < nth; ++c) tot += cnt[c][t];
+            if (tot == 0) { *err = "a triangle has no matching element"; return DISCO_ERR_INFEASIBLE; }
+            P->row_ptr.push_back(run);
+            for (int c = 0; c < nth; ++c) {
+                off[c][t] = run;
+                run += cnt[c][t];
+            }
         }
-        for (int t = 0; t < ntri; ++t)
-            if (cnt[t + 1] == 0) { *err = "a triangle has no matching element"; return DISCO_ERR_INFEASIBLE; }
-        for (int t = 0; t < ntri; ++t) cnt[t + 1] += cnt[t];
-        int64_t base = int64_t(P->row_var.size());
-        P->row_var.resize(size_t(base + cnt[ntri]));
-        P->row_coef.resize(size_t(base + cnt[ntri]), 1);
-        std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
-        for (int64_t i = 0; i < nv; ++i) {
-            int t = tri_of(i);
-            if (t >= 0) P->row_var[size_t(base + pos[t]++)] = int32_t(i);
-        }
-        for (int t = 0; t < ntri; ++t) P->row_ptr.push_back(base + cnt[t]);
+        proj_end = run;
+        parallel_chunks(nv, nth, [&](int c, int64_t lo, int64_t hi) {
+            for (int64_t i = lo; i < hi; ++i) {
+                const int t = tri_of(i);
+                if (t < 0) continue;
+                const int64_t pos = off[c][t]++;
+                P->row_var[size_t(pos)] = int32_t(i);
+                P->row_coef[size_t(pos)] = 1;
+                row_ent[size_t(pos)] = 3 + side;
+                proj_row[size_t(2) * i + side] = int32_t(row0 + t);
+            }
+        });
         P->rhs.resize(P->rhs.size() + size_t(ntri), 1);
         (side == 0 ? P->n_projx : P->n_projy) = ntri;
     }
     P->nrows = int64_t(P->rhs.size());
-    P->row_ptr.push_back(int64_t(P->row_var.size()));
-
-    // ---- presolve: saturated rows force all their free variables, to a fixpoint
+    if (proj_end != int64_t(P->row_var.size())) { *err = "internal: projection entry count"; return DISCO_ERR_INVALID_ARG; }
+    P->row_ptr.push_back(proj_end);
     const int64_t nr = P->nrows;
-    std::vector<int64_t> vptr(nv + 1, 0);
-    for (int32_t v : P->row_var) ++vptr[v + 1];
-    for (int64_t i = 0; i < nv; ++i) vptr[i + 1] += vptr[i];
-    std::vector<int64_t> vrow(P->row_var.size());
-    std::vector<int8_t> vcoef(P->row_var.size());
-    {
-        std::vector<int64_t> fill(vptr.begin(), vptr.end() - 1);
-        for (int64_t r = 0; r < nr; ++r)
-            for (int64_t e = P->row_ptr[r]; e < P->row_ptr[r + 1]; ++e) {
-                int64_t p = fill[P->row_var[e]]++;
-                vrow[p] = r;
-                vcoef[p] = P->row_coef[e];
-            }
-    }
-    std::vector<int32_t> res(P->rhs.begin(), P->rhs.end()), npos(nr, 0), nneg(nr, 0);
-    for (int64_t r = 0; r < nr; ++r)
-        for (int64_t e = P->row_ptr[r]; e < P->row_ptr[r + 1]; ++e) (P->row_coef[e] > 0 ? npos : nneg)[r]++;
-    P->fixed.assign(nv, -1);
-    std::vector<int64_t> queue(nr);
-    std::iota(queue.begin(), queue.end(), 0);
-    std::vector<char> inq(nr, 1);
-    size_t head = 0;
-    while (head < queue.size()) {
-        int64_t r = queue[head++];
-        inq[r] = 0;
-        if (res[r] > npos[r] || res[r] < -nneg[r]) { *err = "presolve: a row has no solution"; return DISCO_ERR_INFEASIBLE; }
-        if (npos[r] + nneg[r] == 0) continue;
-        int up;  // value forced on +1 variables (-1 variables get the opposite)
-        if (res[r] == npos[r]) up = 1;
-        else if (res[r] == -nneg[r]) up = 0;
-        else continue;
+
+    // ---- presolve: saturated rows force all their free variables, to a fixpoint. Rounds
+    // are bulk-synchronous (decide on a snapshot, apply, recount the touched rows), so the
+    // result is the unique arc-consistent closure whatever the thread count.
+    std::vector<int32_t> res(P->rhs.begin(), P->rhs.end());
+    std::vector<int32_t> npos(static_cast<size_t>(nr)), nneg(static_cast<size_t>(nr));
+    P->fixed.assign(size_t(nv), -1);
+    auto recount = [&](int64_t r) {
+        int32_t rs = P->rhs[r], np = 0, nn = 0;
         for (int64_t e = P->row_ptr[r]; e < P->row_ptr[r + 1]; ++e) {
-            int32_t v = P->row_var[e];
-            if (P->fixed[v] >= 0) continue;
-            int val = P->row_coef[e] > 0 ? up : 1 - up;
-            P->fixed[v] = int8_t(val);
-            for (int64_t q = vptr[v]; q < vptr[v + 1]; ++q) {
-                int64_t rr = vrow[q];
-                if (vcoef[q] > 0) --npos[rr]; else --nneg[rr];
-                res[rr] -= vcoef[q] * val;
-                if (!inq[rr]) { inq[rr] = 1; queue.push_back(rr); }
-            }
+            const int8_t f = P->fixed[P->row_var[e]];
+            if (f < 0) (P->row_coef[e] > 0 ? np : nn)++;
+            else rs -= P->row_coef[e] * f;
         }
+        res[r] = rs;
+        npos[r] = np;
+        nneg[r] = nn;
+    };
+    parallel_chunks(nr, nth, [&](int, int64_t lo, int64_t hi) {
+        for (int64_t r = lo; r < hi; ++r) recount(r);
+    });
+    {
+        std::vector<int64_t> frontier(static_cast<size_t>(nr));
+        std::iota(frontier.begin(), frontier.end(), int64_t(0));
+        std::vector<uint8_t> touched(static_cast<size_t>(nr), 0);
+        std::atomic<int> bad{0};
+        while (!frontier.empty() && !bad.load()) {
+            // decide on the snapshot
+            std::vector<std::vector<std::pair<int32_t, int8_t>>> prop(nth);
+            parallel_chunks(int64_t(frontier.size()), nth, [&](int c, int64_t lo, int64_t hi) {
+                for (int64_t k = lo; k < hi; ++k) {
+                    const int64_t r = frontier[k];
+                    if (res[r] > npos[r] || res[r] < -nneg[r]) { bad = 1; return; }
+                    if (npos[r] + nneg[r] == 0) continue;
+                    int up;
+                    if (res[r] == npos[r]) up = 1;
+                    else if (res[r] == -nneg[r]) up = 0;
+                    else continue;
+                    for (int64_t e = P->row_ptr[r]; e < P->row_ptr[r + 1]; ++e) {
+                        const int32_t v = P->row_var[e];
+                        if (P->fixed[v] < 0) prop[c].emplace_back(v, int8_t(P->row_coef[e] > 0 ? up : 1 - up));
+                    }
+                }
+            });
+            if (bad.load()) break;
+            // apply: first writer wins, a different value is a conflict; mark the touched rows
+            bool any = false;
+            for (auto& pc : prop) any = any || !pc.empty();
+            if (!any) break;
+            parallel_chunks(nth, nth, [&](int c, int64_t, int64_t) {
+                for (auto [v, val] : prop[c]) {
+                    int8_t expect = -1;
+                    if (__atomic_compare_exchange_n(&P->fixed[v], &expect, val, false, __ATOMIC_RELAXED,
+                                                    __ATOMIC_RELAXED)) {
+                        for (int q = 0; q < 3; ++q) touched[elem_row[3 * int64_t(v) + q]] = 1;
+                        for (int side = 0; side < 2; ++side)
+                            if (proj_row[size_t(2) * v + side] >= 0) touched[proj_row[size_t(2) * v + side]] = 1;
+                    } else if (expect != val) {
+                        bad = 1;
+                    }
+                }
+            });
+            if (bad.load()) break;
+            // the touched rows are recounted and form the next frontier
+            std::vector<std::vector<int64_t>> next(nth);
+            parallel_chunks(nr, nth, [&](int c, int64_t lo, int64_t hi) {
+                for (int64_t r = lo; r < hi; ++r)
+                    if (touched[r]) {
+                        touched[r] = 0;
+                        recount(r);
+                        next[c].push_back(r);
+                    }
+            });
+            frontier.clear();
+            for (auto& x : next) frontier.insert(frontier.end(), x.begin(), x.end());
+        }
+        if (bad.load()) { *err = "presolve: a row has no solution"; return DISCO_ERR_INFEASIBLE; }
     }
     for (int64_t r = 0; r < nr; ++r)
         if (npos[r] + nneg[r] == 0 && res[r] != 0) { *err = "presolve: violated row"; return DISCO_ERR_INFEASIBLE; }
     P->constant = 0.0;
-    std::vector<int32_t> internal(nv, -1);
+    std::vector<int32_t> internal(size_t(nv), -1);
     P->free_orig.clear();
     for (int64_t i = 0; i < nv; ++i) {
         if (P->fixed[i] == 1) P->constant += P->cost[i];
@@ -397,124 +653,160 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     }
     P->n_free = int64_t(P->free_orig.size());
 
-    // ---- BDD segments
-    P->slot_var.clear();
-    P->slot_desc.clear();
-    P->segs.clear();
-    std::vector<int32_t> fv;   // free variables of a row (internal ids)
-    std::vector<int8_t> fc;    // their coefficients
-    std::vector<int32_t> lo, wd;
-    std::vector<int32_t> slot_w, slot_wn, slot_d0, slot_d1;
-    std::vector<uint8_t> slot_one;
-    int64_t next_aux = 0;
+    // ---- BDD segments, compiled in parallel over row ranges; slot rank = which of the
+    // variable's rows this is (closedness corner 0..2, then projection rows), so it is known
+    // locally; auxiliaries get rank 0 in the left segment and 1 in the right one
+    const int nrc = std::max(1, std::min<int>(nth * 8, int(nr / 1024) + 1));
+    std::vector<RowChunk> chunks(nrc);
+    parallel_chunks(nrc, nth, [&](int, int64_t c0, int64_t c1) {
+        std::vector<int32_t> fv, lo, wd;
+        std::vector<int8_t> fc;
+        std::vector<uint8_t> fr;
+        for (int64_t c = c0; c < c1; ++c) {
+            RowChunk& C = chunks[c];
+            const int64_t r0 = nr * c / nrc, r1 = nr * (c + 1) / nrc;
+            auto add_slot = [&](int32_t var, int w, int wn, int d0, int d1, bool one, int rank) {
+                C.var.push_back(var);
+                C.w.push_back(w);
+                C.wn.push_back(wn);
+                C.d0.push_back(d0);
+                C.d1.push_back(d1);
+                C.one.push_back(one ? 1 : 0);
+                C.rank.push_back(uint8_t(rank));
+                C.nodes += w;
+            };
+            for (int64_t r = r0; r < r1 && !C.rc; ++r) {
+                fv.clear();
+                fc.clear();
+                fr.clear();
+                for (int64_t e = P->row_ptr[r]; e < P->row_ptr[r + 1]; ++e) {
+                    const int32_t v = P->row_var[e];
+                    if (P->fixed[v] >= 0) continue;
+                    fv.push_back(internal[v]);
+                    fc.push_back(P->row_coef[e]);
+                    // projection rank: 3 for the first projection row of the element, 4 for the second
+                    int rk = row_ent[e];
+                    if (rk == 4 && proj_row[size_t(2) * v] < 0) rk = 3;
+                    fr.push_back(uint8_t(rk));
+                }
+                const int n = int(fv.size());
+                if (n == 0) continue;
+                const int rr = res[r];
+                int ptot = 0, qtot = 0;
+                for (int8_t cf : fc) (cf > 0 ? ptot : qtot)++;
+                lo.assign(n + 1, 0);
+                wd.assign(n + 1, 0);
+                int ppre = 0, qpre = 0;
+                for (int l = 0; l <= n; ++l) {
+                    lo[l] = std::max(-qpre, rr - (ptot - ppre));
+                    wd[l] = std::min(ppre, rr + (qtot - qpre)) - lo[l] + 1;
+                    if (wd[l] < 1 || wd[l] > kMaxWidth) {
+                        C.err = wd[l] < 1 ? "empty BDD layer after presolve" : "BDD layer wider than 32 nodes";
+                        C.rc = wd[l] < 1 ? DISCO_ERR_INFEASIBLE : DISCO_ERR_INVALID_ARG;
+                        break;
+                    }
+                    if (l < n) (fc[l] > 0 ? ppre : qpre)++;
+                }
+                if (C.rc) break;
+                const int nseg = (split_chunk > 0 && n > split_chunk) ? (n + split_chunk - 1) / split_chunk : 1;
+                std::vector<int64_t> cut_aux(size_t(nseg) + 1, -1);  // local id of y_1 of the cut before segment s
+                for (int s = 1; s < nseg; ++s) {
+                    const int b = int(int64_t(s) * n / nseg);
+                    if (wd[b] > 1) {
+                        if (wd[b] + 1 > kMaxWidth) { C.err = "split layer too wide"; C.rc = DISCO_ERR_INVALID_ARG; break; }
+                        cut_aux[s] = C.n_aux;
+                        C.n_aux += wd[b];
+                    }
+                }
+                if (C.rc) break;
+                for (int s = 0; s < nseg; ++s) {
+                    const int b0 = int(int64_t(s) * n / nseg), b1 = int(int64_t(s + 1) * n / nseg);
+                    Segment sg{r, s, int64_t(C.var.size()), 0, 0};
+                    if (s > 0 && wd[b0] > 1) {  // prefix chain: read the one-hot y_1..y_k, enter node j
+                        const int k = wd[b0];
+                        for (int j = 1; j <= k; ++j) {
+                            const int32_t var = int32_t(-1 - (cut_aux[s] + j - 1));
+                            if (j < k) add_slot(var, j, j + 1, 0, j, true, 1);
+                            else add_slot(var, k, k, -1, k - 1, true, 1);
+                            sg.max_width = std::max(sg.max_width, j);
+                        }
+                    }
+                    for (int l = b0; l < b1; ++l) {
+                        const int d0 = lo[l] - lo[l + 1];
+                        add_slot(fv[l], wd[l], wd[l + 1], d0, d0 + fc[l], false, fr[l]);
+                        sg.max_width = std::max(sg.max_width, wd[l]);
+                    }
+                    if (s + 1 < nseg && wd[b1] > 1) {  // suffix chain: y_j = 1 iff the path leaves through node j
+                        const int k = wd[b1];
+                        for (int j = 1; j <= k; ++j) {
+                            const int32_t var = int32_t(-1 - (cut_aux[s + 1] + j - 1));
+                            const int w = j == 1 ? k : k - j + 2;
+                            add_slot(var, w, j < k ? k - j + 1 : 1, -1, k - j, true, 0);
+                            sg.max_width = std::max(sg.max_width, w);
+                        }
+                    }
+                    sg.n_layers = int32_t(int64_t(C.var.size()) - sg.first_slot);
+                    C.max_layers = std::max(C.max_layers, sg.n_layers);
+                    C.max_width = std::max(C.max_width, sg.max_width);
+                    C.segs.push_back(sg);
+                }
+            }
+        }
+    });
+    for (const RowChunk& C : chunks)
+        if (C.rc) { *err = C.err; return C.rc; }
+    // global offsets of slots, segments and auxiliaries per chunk
+    std::vector<int64_t> slot_off(nrc + 1, 0), seg_off(nrc + 1, 0), aux_off(nrc + 1, 0);
     int64_t nodes = 0;
     int max_layers = 0, max_width = 0;
-    auto add_slot = [&](int32_t var, int w, int wn, int d0, int d1, bool one) {
-        P->slot_var.push_back(var);
-        slot_w.push_back(w);
-        slot_wn.push_back(wn);
-        slot_d0.push_back(d0);
-        slot_d1.push_back(d1);
-        slot_one.push_back(one ? 1 : 0);
-        nodes += w;
-    };
-    for (int64_t r = 0; r < nr; ++r) {
-        fv.clear();
-        fc.clear();
-        for (int64_t e = P->row_ptr[r]; e < P->row_ptr[r + 1]; ++e) {
-            int32_t v = P->row_var[e];
-            if (P->fixed[v] < 0) { fv.push_back(internal[v]); fc.push_back(P->row_coef[e]); }
-        }
-        const int n = int(fv.size());
-        if (n == 0) continue;
-        const int rr = res[r];
-        int ptot = 0, qtot = 0;
-        for (int8_t c : fc) (c > 0 ? ptot : qtot)++;
-        lo.assign(n + 1, 0);
-        wd.assign(n + 1, 0);
-        int ppre = 0, qpre = 0;
-        for (int l = 0; l <= n; ++l) {
-            int lo_l = std::max(-qpre, rr - (ptot - ppre));
-            int hi_l = std::min(ppre, rr + (qtot - qpre));
-            lo[l] = lo_l;
-            wd[l] = hi_l - lo_l + 1;
-            if (wd[l] < 1 || wd[l] > kMaxWidth) {
-                *err = wd[l] < 1 ? "empty BDD layer after presolve" : "BDD layer wider than 32 nodes";
-                return wd[l] < 1 ? DISCO_ERR_INFEASIBLE : DISCO_ERR_INVALID_ARG;
-            }
-            if (l < n) (fc[l] > 0 ? ppre : qpre)++;
-        }
-        // balanced segment boundaries
-        int nseg = (split_chunk > 0 && n > split_chunk) ? (n + split_chunk - 1) / split_chunk : 1;
-        std::vector<int64_t> cut_aux(nseg + 1, -1);  // first aux id of the cut before segment s (width > 1)
-        for (int s = 1; s < nseg; ++s) {
-            int b = int(int64_t(s) * n / nseg);
-            if (wd[b] > 1) {
-                if (wd[b] + 1 > kMaxWidth) { *err = "split layer too wide"; return DISCO_ERR_INVALID_ARG; }
-                cut_aux[s] = next_aux;
-                next_aux += wd[b];
-            }
-        }
-        for (int s = 0; s < nseg; ++s) {
-            int b0 = int(int64_t(s) * n / nseg), b1 = int(int64_t(s + 1) * n / nseg);
-            Segment sg{r, s, int64_t(P->slot_var.size()), 0, 0};
-            // prefix chain: read the one-hot y_1..y_k, enter node j of layer b0
-            if (s > 0 && wd[b0] > 1) {
-                int k = wd[b0];
-                for (int j = 1; j <= k; ++j) {
-                    int32_t var = int32_t(-1 - (cut_aux[s] + j - 1));  // auxiliaries resolved below
-                    if (j < k) add_slot(var, j, j + 1, 0, j, true);
-                    else add_slot(var, k, k, -1, k - 1, true);
-                    sg.max_width = std::max(sg.max_width, j);
-                }
-            }
-            for (int l = b0; l < b1; ++l) {
-                int d0 = lo[l] - lo[l + 1];
-                add_slot(fv[l], wd[l], wd[l + 1], d0, d0 + fc[l], false);
-                sg.max_width = std::max(sg.max_width, wd[l]);
-            }
-            // suffix chain: y_j = 1 iff the path leaves through node j of layer b1
-            if (s + 1 < nseg && wd[b1] > 1) {
-                int k = wd[b1];
-                for (int j = 1; j <= k; ++j) {
-                    int32_t var = int32_t(-1 - (cut_aux[s + 1] + j - 1));
-                    int w = j == 1 ? k : k - j + 2;
-                    int wn = j < k ? k - j + 1 : 1;
-                    add_slot(var, w, wn, -1, k - j, true);
-                    sg.max_width = std::max(sg.max_width, w);
-                }
-            }
-            sg.n_layers = int32_t(int64_t(P->slot_var.size()) - sg.first_slot);
-            max_layers = std::max(max_layers, sg.n_layers);
-            max_width = std::max(max_width, sg.max_width);
-            P->segs.push_back(sg);
-        }
+    for (int c = 0; c < nrc; ++c) {
+        slot_off[c + 1] = slot_off[c] + int64_t(chunks[c].var.size());
+        seg_off[c + 1] = seg_off[c] + int64_t(chunks[c].segs.size());
+        aux_off[c + 1] = aux_off[c] + chunks[c].n_aux;
+        nodes += chunks[c].nodes;
+        max_layers = std::max(max_layers, chunks[c].max_layers);
+        max_width = std::max(max_width, chunks[c].max_width);
     }
-    P->n_aux = next_aux;
+    P->n_aux = aux_off[nrc];
     const int64_t nint = P->n_free + P->n_aux;
     if (nint >= (int64_t(1) << 31)) { *err = "too many variables"; return DISCO_ERR_INVALID_ARG; }
-    for (int32_t& v : P->slot_var)
-        if (v < 0) v = int32_t(P->n_free + (-1 - int64_t(v)));
-    // degree and rank of every slot
+    const int64_t ns = slot_off[nrc];
+    P->slot_var.resize(size_t(ns));
+    P->slot_desc.resize(size_t(ns));
+    P->slot_lam0.resize(size_t(ns));
+    P->slot_lam0_lo.resize(size_t(ns));
+    P->segs.resize(size_t(seg_off[nrc]));
     P->deg.assign(size_t(nint), 0);
-    const size_t ns = P->slot_var.size();
-    P->slot_desc.resize(ns);
-    P->slot_lam0.resize(ns);
-    P->slot_lam0_lo.resize(ns);
-    std::vector<uint8_t> rank(ns);
-    for (size_t i = 0; i < ns; ++i) {
-        uint8_t& dg = P->deg[P->slot_var[i]];
-        rank[i] = dg;
-        if (++dg > 7) { *err = "variable in more than 7 BDDs"; return DISCO_ERR_INVALID_ARG; }
-    }
-    for (size_t i = 0; i < ns; ++i) {
-        int32_t v = P->slot_var[i];
-        int dg = P->deg[v];
-        P->slot_desc[i] = pack_desc(slot_w[i], slot_wn[i], slot_d0[i], slot_d1[i], slot_one[i], rank[i], dg);
-        const double l0 = v < P->n_free ? P->cost[P->free_orig[v]] / dg : 0.0;
-        P->slot_lam0[i] = float(l0);
-        P->slot_lam0_lo[i] = float(l0 - double(P->slot_lam0[i]));
-    }
+    // degree: every free element keeps all its rows (3 closedness + its projection rows); an
+    // auxiliary variable sits in two segments
+    parallel_chunks(P->n_free, nth, [&](int, int64_t lo, int64_t hi) {
+        for (int64_t v = lo; v < hi; ++v) {
+            const int64_t i = P->free_orig[v];
+            P->deg[v] = uint8_t(3 + (proj_row[size_t(2) * i] >= 0) + (proj_row[size_t(2) * i + 1] >= 0));
+        }
+    });
+    for (int64_t v = P->n_free; v < nint; ++v) P->deg[v] = 2;
+    parallel_chunks(nrc, nth, [&](int, int64_t c0, int64_t c1) {
+        for (int64_t c = c0; c < c1; ++c) {
+            const RowChunk& C = chunks[c];
+            const int64_t so = slot_off[c];
+            for (size_t i = 0; i < C.var.size(); ++i) {
+                int32_t v = C.var[i];
+                if (v < 0) v = int32_t(P->n_free + aux_off[c] + (-1 - int64_t(v)));
+                const int dg = P->deg[v];
+                P->slot_var[so + i] = v;
+                P->slot_desc[so + i] = pack_desc(C.w[i], C.wn[i], C.d0[i], C.d1[i], C.one[i], C.rank[i], dg);
+                const double l0 = v < P->n_free ? P->cost[P->free_orig[v]] / dg : 0.0;
+                P->slot_lam0[so + i] = float(l0);
+                P->slot_lam0_lo[so + i] = float(l0 - double(float(l0)));
+            }
+            for (size_t k = 0; k < C.segs.size(); ++k) {
+                Segment sg = C.segs[k];
+                sg.first_slot += so;
+                P->segs[seg_off[c] + k] = sg;
+            }
+        }
+    });
     P->n_nodes = nodes;
     P->max_layers = max_layers;
     P->max_width = max_width;

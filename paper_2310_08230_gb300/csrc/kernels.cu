@@ -173,15 +173,12 @@ __device__ __forceinline__ df pend_layer(const Layer<W>& L, int deg) {
 //   MODE 0: MMA update, store F.       MODE 1: MMA update under fixings, store F.
 //   MODE 2: lower bound (no store).    MODE 3: plain min-sum under fixings, store F.
 template <int W, int MODE>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward(KArgs a) {
+__device__ __forceinline__ void forward_tile(const KArgs& a, const int tile, const TileInfo& ti) {
     constexpr bool kUpdate = MODE <= 1;
     constexpr bool kRound = MODE == 1 || MODE == 3;
     constexpr bool kStoreF = MODE != 2;
     constexpr int P = depth<W>();
     const int lane = threadIdx.x & 31;
-    const int tile = a.tile0 + int(blockIdx.x) * kWarpsPerBlock + int(threadIdx.x >> 5);
-    if (tile >= a.tile_end) return;
-    const TileInfo ti = a.tiles[tile];
     const int64_t sb = ti.slot_base + lane;
     const float* Bl = a.B + ti.node_base + lane;  // B of layer l at Bl + l * W * 32
     float* Fl = a.F + ti.node_base + lane;
@@ -270,21 +267,39 @@ done:
     }
 }
 
+// One width class per launch.
+template <int W, int MODE>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward(KArgs a) {
+    const int tile = a.tile0 + int(blockIdx.x) * kWarpsPerBlock + int(threadIdx.x >> 5);
+    if (tile >= a.tile_end) return;
+    const TileInfo ti = a.tiles[tile];
+    forward_tile<W, MODE>(a, tile, ti);
+}
+
+// Width classes 2, 4 and 8 in one launch (tiles ordered longest first), so that short
+// tiles fill the SMs around the long ones.
+template <int MODE>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_fused(KArgs a) {
+    const int tile = a.tile0 + int(blockIdx.x) * kWarpsPerBlock + int(threadIdx.x >> 5);
+    if (tile >= a.tile_end) return;
+    const TileInfo ti = a.tiles[tile];
+    if (ti.W == 2) forward_tile<2, MODE>(a, tile, ti);
+    else if (ti.W == 4) forward_tile<4, MODE>(a, tile, ti);
+    else forward_tile<8, MODE>(a, tile, ti);
+}
+
 // ---------------------------------------------------------------------------------------
 // Backward half-pass with min-marginal averaging (and plain backward variants).
 //   MODE 0: MMA update, store B.                 MODE 1: MMA update under fixings, store B.
 //   MODE 2: min-marginals under fixings (out).   MODE 3: plain min-sum under fixings, store B.
 template <int W, int MODE>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_backward(KArgs a) {
+__device__ __forceinline__ void backward_tile(const KArgs& a, const TileInfo& ti) {
     constexpr bool kUpdate = MODE <= 1;
     constexpr bool kRound = MODE >= 1;
     constexpr bool kStoreB = MODE != 2;
     constexpr bool kNeedF = MODE != 3;
     constexpr int P = depth<W>();
     const int lane = threadIdx.x & 31;
-    const int tile = a.tile0 + int(blockIdx.x) * kWarpsPerBlock + int(threadIdx.x >> 5);
-    if (tile >= a.tile_end) return;
-    const TileInfo ti = a.tiles[tile];
     const int64_t sb = ti.slot_base + lane;
     const float* Fl = a.F + ti.node_base + lane;
     float* Bl = a.B + ti.node_base + lane;
@@ -380,6 +395,24 @@ done:
     return;
 }
 
+template <int W, int MODE>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_backward(KArgs a) {
+    const int tile = a.tile0 + int(blockIdx.x) * kWarpsPerBlock + int(threadIdx.x >> 5);
+    if (tile >= a.tile_end) return;
+    const TileInfo ti = a.tiles[tile];
+    backward_tile<W, MODE>(a, ti);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_backward_fused(KArgs a) {
+    const int tile = a.tile0 + int(blockIdx.x) * kWarpsPerBlock + int(threadIdx.x >> 5);
+    if (tile >= a.tile_end) return;
+    const TileInfo ti = a.tiles[tile];
+    if (ti.W == 2) backward_tile<2, MODE>(a, ti);
+    else if (ti.W == 4) backward_tile<4, MODE>(a, ti);
+    else backward_tile<8, MODE>(a, ti);
+}
+
 // ---------------------------------------------------------------------------------------
 // Value supports under fixings: which values of each slot's variable lie on some
 // root -> TOP path of its segment that respects the fixings (bit-parallel over nodes).
@@ -419,6 +452,24 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_supports(KArgs a) {
         a.sup_var[size_t(v) * kAccStride + d.rank] = sup;
         rb = ok0 | ok1;
     }
+}
+
+cudaError_t launch_fused(Pass pass, const KArgs& a, cudaStream_t s) {
+    const int n = a.tile_end - a.tile0;
+    if (n <= 0) return cudaSuccess;
+    const dim3 grid((n + kWarpsPerBlock - 1) / kWarpsPerBlock), block(kWarpsPerBlock * 32);
+    switch (pass) {
+        case Pass::FwdMMA: k_forward_fused<0><<<grid, block, 0, s>>>(a); break;
+        case Pass::FwdMMARound: k_forward_fused<1><<<grid, block, 0, s>>>(a); break;
+        case Pass::Lb: k_forward_fused<2><<<grid, block, 0, s>>>(a); break;
+        case Pass::FwdMM: k_forward_fused<3><<<grid, block, 0, s>>>(a); break;
+        case Pass::BwdMMA: k_backward_fused<0><<<grid, block, 0, s>>>(a); break;
+        case Pass::BwdMMARound: k_backward_fused<1><<<grid, block, 0, s>>>(a); break;
+        case Pass::BwdMM: k_backward_fused<2><<<grid, block, 0, s>>>(a); break;
+        case Pass::BwdReset: k_backward_fused<3><<<grid, block, 0, s>>>(a); break;
+        case Pass::Supports: k_supports<8><<<grid, block, 0, s>>>(a); break;
+    }
+    return cudaGetLastError();
 }
 
 template <int W>
@@ -652,6 +703,7 @@ inline int grid_for(int64_t n, int block) {
 
 cudaError_t launch_pass(Pass pass, int W, const KArgs& a, cudaStream_t s) {
     switch (W) {
+        case 0: return launch_fused(pass, a, s);
         case 2: return launch_w<2>(pass, a, s);
         case 4: return launch_w<4>(pass, a, s);
         case 8: return launch_w<8>(pass, a, s);

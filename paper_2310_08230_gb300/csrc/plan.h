@@ -3,10 +3,36 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
+#include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 namespace disco {
+
+// Allocator that leaves trivially constructible elements uninitialised on resize, so that large
+// arrays are first touched by the (parallel) code that fills them instead of being zeroed.
+template <class T>
+struct uninit_alloc : std::allocator<T> {
+    template <class U>
+    struct rebind {
+        using other = uninit_alloc<U>;
+    };
+    uninit_alloc() = default;
+    template <class U>
+    uninit_alloc(const uninit_alloc<U>&) noexcept {}
+    template <class U>
+    void construct(U* p) noexcept {
+        ::new (static_cast<void*>(p)) U;
+    }
+    template <class U, class... A>
+    void construct(U* p, A&&... a) {
+        ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+    }
+};
+template <class T>
+using pod_vector = std::vector<T, uninit_alloc<T>>;
 
 // Widest BDD layer the device kernels accept (node states held in registers).
 constexpr int kMaxWidth = 32;
@@ -38,11 +64,11 @@ struct Plan {
     // ---- problem (P)
     int32_t nvx = 0, nvy = 0;
     int64_t nvars = 0, nrows = 0, n_closed = 0, n_projx = 0, n_projy = 0;
-    std::vector<int32_t> vm, vn;         // 3 per variable: X / Y vertex of each corner
-    std::vector<double> cost;            // normalised c_p per variable
-    std::vector<int64_t> row_ptr;        // rows: closedness, X projection, Y projection
-    std::vector<int32_t> row_var;
-    std::vector<int8_t> row_coef;
+    pod_vector<int32_t> vm, vn;         // 3 per variable: X / Y vertex of each corner
+    pod_vector<double> cost;            // normalised c_p per variable
+    pod_vector<int64_t> row_ptr;        // rows: closedness, X projection, Y projection
+    pod_vector<int32_t> row_var;
+    pod_vector<int8_t> row_coef;
     std::vector<int32_t> rhs;
     // ---- presolve
     std::vector<int8_t> fixed;           // per variable: -1 free, 0 / 1 fixed
@@ -52,10 +78,10 @@ struct Plan {
     std::vector<int32_t> free_orig;      // internal id -> variable id (free ones)
     std::vector<uint8_t> deg;            // slots per internal variable
     // ---- canonical slots: segments by (row, index), layers in order
-    std::vector<int32_t> slot_var;       // internal variable id
-    std::vector<uint32_t> slot_desc;
-    std::vector<float> slot_lam0;        // lambda^0 = c / |J| (high part), 0 for auxiliaries
-    std::vector<float> slot_lam0_lo;     // low part: c / |J| - slot_lam0
+    pod_vector<int32_t> slot_var;       // internal variable id
+    pod_vector<uint32_t> slot_desc;
+    pod_vector<float> slot_lam0;        // lambda^0 = c / |J| (high part), 0 for auxiliaries
+    pod_vector<float> slot_lam0_lo;     // low part: c / |J| - slot_lam0
     std::vector<Segment> segs;
     int64_t n_nodes = 0;
     int32_t max_layers = 0, max_width = 0;
