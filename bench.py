@@ -138,6 +138,7 @@ def gpu_arm(args):
     max_iters = args.max_iters
 
     def step(e2e: bool, stats: dict):
+        t0 = time.perf_counter()
         with torch.cuda.stream(stream):
             if e2e:
                 FX.copy_(FX_pin, non_blocking=True)
@@ -145,6 +146,7 @@ def gpu_arm(args):
         L.check(lib.disco_pair_costs(FX.data_ptr(), FY.data_ptr(), nvx, nvy, dim, d.data_ptr(), sptr), "pair_costs")
         L.check(lib.disco_candidates(d.data_ptr(), nvx, nvy, inst.topk, ctypes.byref(mx), ctypes.byref(my),
                                      allowed.data_ptr(), sptr), "candidates")
+        t1 = time.perf_counter()
         h = ctypes.c_void_p()
         L.check(lib.disco_build(ctypes.byref(mx), ctypes.byref(my), d.data_ptr(), allowed.data_ptr(),
                                 ctypes.byref(opts), ctypes.byref(h)), "build")
@@ -171,13 +173,19 @@ def gpu_arm(args):
         t_conv = (time.perf_counter() - t_dual0) * 1e3
         x = np.zeros(info.nvars, np.uint8)
         cost = ctypes.c_double()
+        t3 = time.perf_counter()
         rc = lib.disco_primal(h, x.ctypes.data, info.nvars, ctypes.byref(cost))
+        t4 = time.perf_counter()
         lib.disco_info(h, ctypes.byref(info))
         stats.update(nnodes=info.nnodes, nslots=info.nslots, nvars_free=info.nvars_free, nvars=info.nvars,
                      iters=info.iterations, conv_iters=iters, lb=lb.value, primal=cost.value, primal_ok=rc == 0,
                      dual_ms=dual_ms, conv_ms=t_conv, build_ms=info.build_ms, bytes_per_iter=info.bytes_per_iter,
-                     ntiles=info.ntiles, max_layers=info.max_layers)
+                     ntiles=info.ntiles, max_layers=info.max_layers, upload_ms=info.upload_ms,
+                     costs_candidates_ms=(t1 - t0) * 1e3, build_call_ms=(t_dual0 - t1) * 1e3,
+                     primal_ms=(t4 - t3) * 1e3)
+        t5 = time.perf_counter()
         lib.disco_free(h)
+        stats["free_ms"] = (time.perf_counter() - t5) * 1e3
         return x
 
     def timed(e2e: bool):
@@ -229,6 +237,8 @@ def gpu_arm(args):
         "ms_to_converged_bound": st["conv_ms"], "converged_iters": st["conv_iters"],
         "dual_node_updates_per_s": 2.0 * st["nnodes"] * st["conv_iters"] / (st["dual_ms"] / 1e3),
         "build_ms": st["build_ms"], "lower_bound": st["lb"], "primal_cost": st["primal"],
+        "breakdown_ms": {k: round(st[k], 3) for k in ("costs_candidates_ms", "build_call_ms", "build_ms", "upload_ms",
+                                                      "conv_ms", "primal_ms", "free_ms")},
         "primal_feasible": st["primal_ok"],
         "rel_gap": (st["primal"] - st["lb"]) / st["primal"] if st["primal"] else None,
         "e2e": {"value": updates / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
@@ -308,7 +318,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--config", default="config3")
-    ap.add_argument("--split-chunk", type=int, default=0)
+    ap.add_argument("--split-chunk", type=int, default=32)
     ap.add_argument("--max-iters", type=int, default=20000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -90,7 +90,8 @@ typedef struct {
     double constant;          /* cost of variables fixed to 1 by presolve */
     double build_ms;          /* host time of disco_build */
     int64_t bytes_per_iter;   /* algorithmic bytes of one iteration (two half-passes) */
-    int64_t reserved[5];
+    double upload_ms;         /* disco_build time after the host compiler: device store, upload */
+    int64_t reserved[4];
 } disco_info_t;
 
 typedef struct disco_handle disco_handle;

@@ -44,7 +44,8 @@ class disco_info_t(ctypes.Structure):
         "nvars", "nrows", "nvars_free", "nvars_aux", "nbdds", "nslots", "nnodes", "max_layers", "max_width",
         "ntiles", "device_bytes", "iterations")] + [("constant", ctypes.c_double), ("build_ms", ctypes.c_double),
                                                    ("bytes_per_iter", ctypes.c_int64),
-                                                   ("reserved", ctypes.c_int64 * 5)]
+                                                   ("upload_ms", ctypes.c_double),
+                                                   ("reserved", ctypes.c_int64 * 4)]
 
 
 V, P, I32, I64, D, F = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_float

@@ -3,8 +3,11 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <mutex>
+#include <thread>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -47,6 +50,33 @@ struct WidthClass {
     int tile0, tile_end;
 };
 
+// Stream-ordered device memory from one library pool per device that keeps freed memory
+// (release threshold = max), so building and freeing many handles does not go back to the
+// driver each time.
+cudaError_t pool_for(int dev, cudaMemPool_t* out) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaError_t e = cudaMemPoolCreate(&pools[dev], &props);
+        if (e != cudaSuccess) return e;
+        uint64_t thr = UINT64_MAX;
+        e = cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &thr);
+        if (e != cudaSuccess) return e;
+    }
+    *out = pools[dev];
+    return cudaSuccess;
+}
+
+int host_threads(const disco_opts& o) {
+    return o.host_threads > 0 ? o.host_threads : int(std::max(1u, std::thread::hardware_concurrency()));
+}
+
 }  // namespace
 
 struct disco_handle {
@@ -83,6 +113,7 @@ struct disco_handle {
     double* h_scalar = nullptr;    // pinned
     int64_t device_bytes = 0;
     int64_t iterations = 0;
+    double upload_ms = 0.0;
     bool has_b = false;
     std::vector<void*> allocations;
     cudaGraphExec_t iter_graph = nullptr;
@@ -90,8 +121,10 @@ struct disco_handle {
     template <class T>
     int alloc(T** p, int64_t n) {
         size_t bytes = size_t(std::max<int64_t>(n, 1)) * sizeof(T);
-        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
-        if (e != cudaSuccess) return fail(DISCO_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        cudaMemPool_t pool;
+        cudaError_t e = pool_for(device, &pool);
+        if (e == cudaSuccess) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(p), bytes, pool, stream);
+        if (e != cudaSuccess) return fail(DISCO_ERR_OOM, std::string("device allocation: ") + cudaGetErrorString(e));
         allocations.push_back(*p);
         device_bytes += int64_t(bytes);
         return DISCO_OK;
@@ -129,7 +162,8 @@ struct disco_handle {
 
     ~disco_handle() {
         if (iter_graph) cudaGraphExecDestroy(iter_graph);
-        for (void* p : allocations) cudaFree(p);
+        for (void* p : allocations) cudaFreeAsync(p, stream);
+        if (stream) cudaStreamSynchronize(stream);
         if (h_counters) cudaFreeHost(h_counters);
         if (h_scalar) cudaFreeHost(h_scalar);
         if (own_stream && stream) cudaStreamDestroy(stream);
@@ -169,9 +203,10 @@ int upload(disco_handle* h) {
     // ---- tiles: segments grouped by width class, longest first within a class
     std::vector<int64_t> order(nseg);
     std::iota(order.begin(), order.end(), 0);
+    std::vector<uint8_t> wcls(static_cast<size_t>(nseg));
+    for (int64_t i = 0; i < nseg; ++i) wcls[i] = uint8_t(width_class(P.segs[i].max_width));
     std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
-        int wa = width_class(P.segs[a].max_width), wb = width_class(P.segs[b].max_width);
-        if (wa != wb) return wa < wb;
+        if (wcls[a] != wcls[b]) return wcls[a] < wcls[b];
         return P.segs[a].n_layers > P.segs[b].n_layers;
     });
     std::vector<TileInfo> tiles;
@@ -220,22 +255,30 @@ int upload(disco_handle* h) {
     h->nint = P.n_free + P.n_aux;
     const int64_t nslots = int64_t(P.slot_var.size());
 
-    std::vector<uint32_t> hvar(slot_base, kNoVar), hdesc(slot_base, 0);
-    std::vector<float> hlam(slot_base, 0.0f), hlam_lo(slot_base, 0.0f);
-    std::vector<int64_t> canon(nslots);
-    for (size_t t = 0; t < tiles.size(); ++t)
-        for (size_t lane = 0; lane < tile_segs[t].size(); ++lane) {
-            const Segment& sg = P.segs[tile_segs[t][lane]];
-            for (int l = 0; l < sg.n_layers; ++l) {
-                const int64_t pos = tiles[t].slot_base + int64_t(l) * 32 + int64_t(lane);
-                const int64_t c = sg.first_slot + l;
-                hvar[pos] = uint32_t(P.slot_var[c]);
-                hdesc[pos] = P.slot_desc[c];
-                hlam[pos] = P.slot_lam0[c];
-                hlam_lo[pos] = P.slot_lam0_lo[c];
-                canon[c] = pos;
+    pod_vector<uint32_t> hvar(slot_base), hdesc(slot_base);
+    pod_vector<float> hlam(slot_base), hlam_lo(slot_base);
+    pod_vector<int64_t> canon(nslots);
+    parallel_chunks(int64_t(tiles.size()), host_threads(h->opts), [&](int, int64_t t0, int64_t t1) {
+        for (int64_t t = t0; t < t1; ++t) {
+            const int64_t b0 = tiles[t].slot_base, b1 = b0 + int64_t(tiles[t].L) * 32;
+            std::fill(hvar.begin() + b0, hvar.begin() + b1, kNoVar);
+            std::fill(hdesc.begin() + b0, hdesc.begin() + b1, 0u);
+            std::fill(hlam.begin() + b0, hlam.begin() + b1, 0.0f);
+            std::fill(hlam_lo.begin() + b0, hlam_lo.begin() + b1, 0.0f);
+            for (size_t lane = 0; lane < tile_segs[t].size(); ++lane) {
+                const Segment& sg = P.segs[tile_segs[t][lane]];
+                for (int l = 0; l < sg.n_layers; ++l) {
+                    const int64_t pos = b0 + int64_t(l) * 32 + int64_t(lane);
+                    const int64_t c = sg.first_slot + l;
+                    hvar[pos] = uint32_t(P.slot_var[c]);
+                    hdesc[pos] = P.slot_desc[c];
+                    hlam[pos] = P.slot_lam0[c];
+                    hlam_lo[pos] = P.slot_lam0_lo[c];
+                    canon[c] = pos;
+                }
             }
         }
+    });
     int rc;
     if ((rc = h->alloc(&h->tiles, h->ntiles))) return rc;
     if ((rc = h->alloc(&h->var, slot_base))) return rc;
@@ -453,7 +496,10 @@ int disco_build(const disco_mesh* X, const disco_mesh* Y, const float* d, const 
     rc = build_plan(MeshIn{X->nv, X->nt, X->T}, MeshIn{Y->nv, Y->nt, Y->T}, hd.data(), allowed ? ha.data() : nullptr,
                     o.split_chunk, o.host_threads, &h->plan, &err);
     if (rc) return fail(rc, "build: " + err);
+    const auto tu = std::chrono::steady_clock::now();
     if ((rc = upload(h.get()))) return rc;
+    h->upload_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tu).count();
+    if (std::getenv("DISCO_TRACE")) std::fprintf(stderr, "disco build %-22s %8.2f ms\n", "device store upload", h->upload_ms);
     *out = h.release();
     return DISCO_OK;
 }
@@ -630,25 +676,41 @@ int disco_primal(disco_handle* h, uint8_t* x_out, int64_t nvars, double* cost) {
         CK(cudaMemcpyAsync(st.data(), h->state, size_t(nint), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
     }
+    const int nth = host_threads(o);
     std::vector<uint8_t> x(static_cast<size_t>(P.nvars), uint8_t(0));
-    for (int64_t i = 0; i < P.nvars; ++i) x[i] = P.fixed[i] == 1 ? 1 : 0;
-    bool all = true;
-    for (int64_t v = 0; v < P.n_free; ++v) {
-        x[P.free_orig[v]] = st[v] == kFix1 ? 1 : 0;
-        all = all && st[v] != kFree;
-    }
+    parallel_chunks(P.nvars, nth, [&](int, int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i) x[i] = P.fixed[i] == 1 ? 1 : 0;
+    });
+    std::vector<uint8_t> undecided(static_cast<size_t>(nth), 0);
+    parallel_chunks(P.n_free, nth, [&](int c, int64_t lo, int64_t hi) {
+        for (int64_t v = lo; v < hi; ++v) {
+            x[P.free_orig[v]] = st[v] == kFix1 ? 1 : 0;
+            if (st[v] == kFree) undecided[c] = 1;
+        }
+    });
+    bool all = std::find(undecided.begin(), undecided.end(), uint8_t(1)) == undecided.end();
     // the dual continues from an unrestricted state
     CK(cudaMemsetAsync(h->state, 0, size_t(nint), s));
     h->has_b = false;
-    // exact check of A x = b
-    bool feasible = all;
-    for (int64_t r = 0; r < P.nrows && feasible; ++r) {
-        int64_t sum = 0;
-        for (int64_t e = P.row_ptr[r]; e < P.row_ptr[r + 1]; ++e) sum += int64_t(P.row_coef[e]) * x[P.row_var[e]];
-        feasible = sum == P.rhs[r];
-    }
+    // exact check of A x = b; cost as a fixed-order sum of per-chunk sums
+    const int nck = 64;
+    std::vector<uint8_t> violated(nck, 0);
+    std::vector<double> part(nck, 0.0);
+    parallel_chunks(nck, nth, [&](int, int64_t c0, int64_t c1) {
+        for (int64_t c = c0; c < c1; ++c) {
+            for (int64_t r = P.nrows * c / nck; r < P.nrows * (c + 1) / nck; ++r) {
+                int64_t sum = 0;
+                for (int64_t e = P.row_ptr[r]; e < P.row_ptr[r + 1]; ++e) sum += int64_t(P.row_coef[e]) * x[P.row_var[e]];
+                if (sum != P.rhs[r]) violated[c] = 1;
+            }
+            double s = 0.0;
+            for (int64_t i = P.nvars * c / nck; i < P.nvars * (c + 1) / nck; ++i) s += x[i] ? P.cost[i] : 0.0;
+            part[c] = s;
+        }
+    });
+    const bool feasible = all && std::find(violated.begin(), violated.end(), uint8_t(1)) == violated.end();
     double c = 0.0;
-    for (int64_t i = 0; i < P.nvars; ++i) c += x[i] ? P.cost[i] : 0.0;
+    for (double s : part) c += s;
     if (cost) *cost = c;
     if ((rc = write_out(x_out, x.data(), x.size(), s))) return rc;
     return feasible ? DISCO_OK : fail(DISCO_ERR_PRIMAL_FAILED, "primal: no feasible assignment within the round limit");
@@ -672,6 +734,7 @@ int disco_info(disco_handle* h, disco_info_t* info) {
     info->iterations = h->iterations;
     info->constant = P.constant;
     info->build_ms = P.build_ms;
+    info->upload_ms = h->upload_ms;
     // per iteration: 8 B per node and 20 B per slot per half-pass, 8 B per variable for the averaging
     info->bytes_per_iter = 2 * (8 * P.n_nodes + 20 * info->nslots + 8 * (P.n_free + P.n_aux));
     return DISCO_OK;

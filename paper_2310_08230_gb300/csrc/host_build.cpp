@@ -25,6 +25,8 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <memory>
 #include <cstring>
 #include <numeric>
@@ -154,151 +156,151 @@ struct Allowed {
 
 // Runs body(lo, hi, out) over [0, n) in contiguous chunks on up to `threads` threads and
 // concatenates the per-chunk outputs in order (the result does not depend on threads).
-template <class F>
-void chunked(int n, int threads, Elems* out, F body) {
-    int nch = std::max(1, std::min(threads * 4, n / 16 + 1));
-    std::vector<Elems> parts(nch);
+// Runs the element generators of all five types over contiguous index chunks on one pool of
+// threads and concatenates the chunk outputs in (type, chunk) order, i.e. canonical order
+// whatever the thread count.
+struct Job {
+    int type, lo, hi;
+};
+
+template <class Gen>
+void run_jobs(const std::vector<Job>& jobs, int threads, Elems* out, Gen gen) {
+    const int nj = int(jobs.size());
+    std::vector<Elems> parts(nj);
     std::atomic<int> next{0};
-    auto run = [&](auto&& job, int njobs) {
+    auto run = [&](auto&& job) {
         next = 0;
         std::vector<std::thread> pool;
         auto worker = [&] {
-            for (int c; (c = next.fetch_add(1)) < njobs;) job(c);
+            for (int c; (c = next.fetch_add(1)) < nj;) job(c);
         };
-        for (int t = 1; t < std::min(threads, njobs); ++t) pool.emplace_back(worker);
+        for (int t = 1; t < std::min(threads, nj); ++t) pool.emplace_back(worker);
         worker();
         for (auto& th : pool) th.join();
     };
-    run([&](int c) {
-        const int lo = int(int64_t(n) * c / nch), hi = int(int64_t(n) * (c + 1) / nch);
-        body(lo, hi, &parts[c]);
-    }, nch);
-    // concatenate in chunk order, copying the parts in parallel
-    std::vector<size_t> off(nch + 1, out->size());
-    for (int c = 0; c < nch; ++c) off[c + 1] = off[c] + parts[c].size();
-    const size_t total = off[nch];
+    run([&](int c) { gen(jobs[c], &parts[c]); });
+    std::vector<size_t> off(nj + 1, out->size());
+    for (int c = 0; c < nj; ++c) off[c + 1] = off[c] + parts[c].size();
+    const size_t total = off[nj];
     out->m.resize(3 * total);
     out->n.resize(3 * total);
     out->type.resize(total);
     out->xe.resize(total);
     out->ye.resize(total);
     run([&](int c) {
-        const Elems& p = parts[c];
+        const Elems& q = parts[c];
         const size_t o = off[c];
-        std::copy(p.m.begin(), p.m.end(), out->m.begin() + 3 * o);
-        std::copy(p.n.begin(), p.n.end(), out->n.begin() + 3 * o);
-        std::copy(p.type.begin(), p.type.end(), out->type.begin() + o);
-        std::copy(p.xe.begin(), p.xe.end(), out->xe.begin() + o);
-        std::copy(p.ye.begin(), p.ye.end(), out->ye.begin() + o);
+        std::copy(q.m.begin(), q.m.end(), out->m.begin() + 3 * o);
+        std::copy(q.n.begin(), q.n.end(), out->n.begin() + 3 * o);
+        std::copy(q.type.begin(), q.type.end(), out->type.begin() + o);
+        std::copy(q.xe.begin(), q.xe.end(), out->xe.begin() + o);
+        std::copy(q.ye.begin(), q.ye.end(), out->ye.begin() + o);
         Elems().m.swap(parts[c].m);
-    }, nch);
+    });
 }
 
 void enumerate(const MeshTopo& X, const MeshTopo& Y, const Allowed& A, int threads, Elems* out) {
     const int32_t* TX = X.T;
     const int32_t* TY = Y.T;
-    // type 0: X triangle t, Y triangle s, rotation r: corner v -> (t_v, s_{(v+r)%3})
-    chunked(X.nt, threads, out, [&](int lo, int hi, Elems* o) {
-        std::vector<int64_t> cand;
-        for (int t = lo; t < hi; ++t) {
-            int m0 = TX[3 * t], m1 = TX[3 * t + 1], m2 = TX[3 * t + 2];
-            cand.clear();
-            A.row.for_each(m0, [&](int n0) {
-                Y.tri_at.for_each(n0, [&](std::pair<int, int> sr) {
-                    const int s = sr.first, r = sr.second;
-                    if (A(m1, TY[3 * s + (r + 1) % 3]) && A(m2, TY[3 * s + (r + 2) % 3])) cand.push_back(int64_t(s) * 3 + r);
-                });
-            });
-            std::sort(cand.begin(), cand.end());
-            for (int64_t c : cand) {
-                int s = int(c / 3), r = int(c % 3);
-                o->push(m0, m1, m2, TY[3 * s + r], TY[3 * s + (r + 1) % 3], TY[3 * s + (r + 2) % 3], 0, t, s);
-            }
-        }
-    });
-    // type 1: X triangle t, Y edge e = (a < b), pattern p: corner v -> (t_v, pattern symbol)
-    chunked(X.nt, threads, out, [&](int lo, int hi, Elems* o) {
-        std::vector<int64_t> cand;
-        for (int t = lo; t < hi; ++t) {
-            int m[3] = {TX[3 * t], TX[3 * t + 1], TX[3 * t + 2]};
-            cand.clear();
-            A.row.for_each(m[0], [&](int n0) {
-                Y.edge_at.for_each(n0, [&](int e) {
-                    const int ab[2] = {Y.edges[e].first, Y.edges[e].second};
-                    const int role = ab[0] == n0 ? 0 : 1;  // patterns whose first corner is n0
-                    for (int p = 0; p < 6; ++p)
-                        if (kEdgePattern[p][0] == role && A(m[1], ab[kEdgePattern[p][1]]) && A(m[2], ab[kEdgePattern[p][2]]))
-                            cand.push_back(int64_t(e) * 6 + p);
-                });
-            });
-            std::sort(cand.begin(), cand.end());
-            for (int64_t c : cand) {
-                int e = int(c / 6), p = int(c % 6);
-                int ab[2] = {Y.edges[e].first, Y.edges[e].second};
-                o->push(m[0], m[1], m[2], ab[kEdgePattern[p][0]], ab[kEdgePattern[p][1]], ab[kEdgePattern[p][2]], 1, t, e);
-            }
-        }
-    });
-    // type 2: X edge e = (a < b), Y triangle s, pattern p: corner v -> (pattern symbol, s_v)
-    chunked(int(X.edges.size()), threads, out, [&](int lo, int hi, Elems* o) {
-        std::vector<int64_t> cand;
-        for (int e = lo; e < hi; ++e) {
-            int ab[2] = {X.edges[e].first, X.edges[e].second};
-            cand.clear();
-            for (int p = 0; p < 6; ++p) {
-                int x0 = ab[kEdgePattern[p][0]], x1 = ab[kEdgePattern[p][1]], x2 = ab[kEdgePattern[p][2]];
-                A.row.for_each(x0, [&](int n0) {
-                    Y.tri_at0.for_each(n0, [&](int s) {
-                        if (A(x1, TY[3 * s + 1]) && A(x2, TY[3 * s + 2])) cand.push_back(int64_t(s) * 6 + p);
+    const int count[5] = {X.nt, X.nt, int(X.edges.size()), X.nt, X.nv};
+    std::vector<Job> jobs;
+    for (int ty = 0; ty < 5; ++ty) {
+        const int nch = std::max(1, std::min(threads * 4, count[ty] / 16 + 1));
+        for (int c = 0; c < nch; ++c)
+            jobs.push_back(Job{ty, int(int64_t(count[ty]) * c / nch), int(int64_t(count[ty]) * (c + 1) / nch)});
+    }
+    run_jobs(jobs, threads, out, [&](const Job& j, Elems* o) {
+        const int lo = j.lo, hi = j.hi;
+        switch (j.type) {
+            case 0: {  // type 0: X triangle t, Y triangle s, rotation r: corner v -> (t_v, s_{(v+r)%3})
+            std::vector<int64_t> cand;
+            for (int t = lo; t < hi; ++t) {
+                int m0 = TX[3 * t], m1 = TX[3 * t + 1], m2 = TX[3 * t + 2];
+                cand.clear();
+                A.row.for_each(m0, [&](int n0) {
+                    Y.tri_at.for_each(n0, [&](std::pair<int, int> sr) {
+                        const int s = sr.first, r = sr.second;
+                        if (A(m1, TY[3 * s + (r + 1) % 3]) && A(m2, TY[3 * s + (r + 2) % 3])) cand.push_back(int64_t(s) * 3 + r);
                     });
                 });
+                std::sort(cand.begin(), cand.end());
+                for (int64_t c : cand) {
+                    int s = int(c / 3), r = int(c % 3);
+                    o->push(m0, m1, m2, TY[3 * s + r], TY[3 * s + (r + 1) % 3], TY[3 * s + (r + 2) % 3], 0, t, s);
+                }
             }
-            std::sort(cand.begin(), cand.end());
-            for (int64_t c : cand) {
-                int s = int(c / 6), p = int(c % 6);
-                o->push(ab[kEdgePattern[p][0]], ab[kEdgePattern[p][1]], ab[kEdgePattern[p][2]], TY[3 * s], TY[3 * s + 1],
-                        TY[3 * s + 2], 2, e, s);
+                break;
             }
-        }
-    });
-    // type 3: X triangle t, Y vertex n
-    chunked(X.nt, threads, out, [&](int lo, int hi, Elems* o) {
-        for (int t = lo; t < hi; ++t) {
-            int m0 = TX[3 * t], m1 = TX[3 * t + 1], m2 = TX[3 * t + 2];
-            A.row.for_each(m0, [&](int n) {
-                if (A(m1, n) && A(m2, n)) o->push(m0, m1, m2, n, n, n, 3, t, n);
-            });
-        }
-    });
-    // type 4: X vertex m, Y triangle s
-    chunked(X.nv, threads, out, [&](int lo, int hi, Elems* o) {
-        std::vector<int> cand;
-        for (int mv = lo; mv < hi; ++mv) {
-            cand.clear();
-            A.row.for_each(mv, [&](int n0) {
-                Y.tri_at0.for_each(n0, [&](int s) {
-                    if (A(mv, TY[3 * s + 1]) && A(mv, TY[3 * s + 2])) cand.push_back(s);
+            case 1: {  // type 1: X triangle t, Y edge e = (a < b), pattern p: corner v -> (t_v, pattern symbol)
+            std::vector<int64_t> cand;
+            for (int t = lo; t < hi; ++t) {
+                int m[3] = {TX[3 * t], TX[3 * t + 1], TX[3 * t + 2]};
+                cand.clear();
+                A.row.for_each(m[0], [&](int n0) {
+                    Y.edge_at.for_each(n0, [&](int e) {
+                        const int ab[2] = {Y.edges[e].first, Y.edges[e].second};
+                        const int role = ab[0] == n0 ? 0 : 1;  // patterns whose first corner is n0
+                        for (int p = 0; p < 6; ++p)
+                            if (kEdgePattern[p][0] == role && A(m[1], ab[kEdgePattern[p][1]]) && A(m[2], ab[kEdgePattern[p][2]]))
+                                cand.push_back(int64_t(e) * 6 + p);
+                    });
                 });
-            });
-            std::sort(cand.begin(), cand.end());
-            for (int s : cand) o->push(mv, mv, mv, TY[3 * s], TY[3 * s + 1], TY[3 * s + 2], 4, mv, s);
+                std::sort(cand.begin(), cand.end());
+                for (int64_t c : cand) {
+                    int e = int(c / 6), p = int(c % 6);
+                    int ab[2] = {Y.edges[e].first, Y.edges[e].second};
+                    o->push(m[0], m[1], m[2], ab[kEdgePattern[p][0]], ab[kEdgePattern[p][1]], ab[kEdgePattern[p][2]], 1, t, e);
+                }
+            }
+                break;
+            }
+            case 2: {  // type 2: X edge e = (a < b), Y triangle s, pattern p: corner v -> (pattern symbol, s_v)
+            std::vector<int64_t> cand;
+            for (int e = lo; e < hi; ++e) {
+                int ab[2] = {X.edges[e].first, X.edges[e].second};
+                cand.clear();
+                for (int p = 0; p < 6; ++p) {
+                    int x0 = ab[kEdgePattern[p][0]], x1 = ab[kEdgePattern[p][1]], x2 = ab[kEdgePattern[p][2]];
+                    A.row.for_each(x0, [&](int n0) {
+                        Y.tri_at0.for_each(n0, [&](int s) {
+                            if (A(x1, TY[3 * s + 1]) && A(x2, TY[3 * s + 2])) cand.push_back(int64_t(s) * 6 + p);
+                        });
+                    });
+                }
+                std::sort(cand.begin(), cand.end());
+                for (int64_t c : cand) {
+                    int s = int(c / 6), p = int(c % 6);
+                    o->push(ab[kEdgePattern[p][0]], ab[kEdgePattern[p][1]], ab[kEdgePattern[p][2]], TY[3 * s], TY[3 * s + 1],
+                            TY[3 * s + 2], 2, e, s);
+                }
+            }
+                break;
+            }
+            case 3: {  // type 3: X triangle t, Y vertex n
+            for (int t = lo; t < hi; ++t) {
+                int m0 = TX[3 * t], m1 = TX[3 * t + 1], m2 = TX[3 * t + 2];
+                A.row.for_each(m0, [&](int n) {
+                    if (A(m1, n) && A(m2, n)) o->push(m0, m1, m2, n, n, n, 3, t, n);
+                });
+            }
+                break;
+            }
+            case 4: {  // type 4: X vertex m, Y triangle s
+            std::vector<int> cand;
+            for (int mv = lo; mv < hi; ++mv) {
+                cand.clear();
+                A.row.for_each(mv, [&](int n0) {
+                    Y.tri_at0.for_each(n0, [&](int s) {
+                        if (A(mv, TY[3 * s + 1]) && A(mv, TY[3 * s + 2])) cand.push_back(s);
+                    });
+                });
+                std::sort(cand.begin(), cand.end());
+                for (int s : cand) o->push(mv, mv, mv, TY[3 * s], TY[3 * s + 1], TY[3 * s + 2], 4, mv, s);
+            }
+                break;
+            }
         }
     });
-}
-
-// Runs body(chunk, lo, hi) over [0, n) split into `nch` contiguous chunks on threads.
-template <class F>
-void parallel_chunks(int64_t n, int nch, F body) {
-    if (nch <= 1 || n < 2) {
-        body(0, int64_t(0), n);
-        return;
-    }
-    std::vector<std::thread> pool;
-    for (int c = 0; c < nch; ++c) {
-        const int64_t lo = n * c / nch, hi = n * (c + 1) / nch;
-        pool.emplace_back([&body, c, lo, hi] { body(c, lo, hi); });
-    }
-    for (auto& th : pool) th.join();
 }
 
 // One boundary edge of one element: its smaller product vertex (m, n) is implied by the
@@ -326,11 +328,24 @@ struct RowChunk {
     int rc = 0;
 };
 
+// Phase timer: with DISCO_TRACE set in the environment, each phase's wall time goes to stderr.
+struct Trace {
+    bool on = std::getenv("DISCO_TRACE") != nullptr;
+    std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+    void mark(const char* phase) {
+        if (!on) return;
+        const auto n = std::chrono::steady_clock::now();
+        std::fprintf(stderr, "disco build %-22s %8.2f ms\n", phase, std::chrono::duration<double, std::milli>(n - t).count());
+        t = n;
+    }
+};
+
 }  // namespace
 
 int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8_t* mask, int split_chunk,
                int threads, Plan* P, std::string* err) {
     auto t0 = std::chrono::steady_clock::now();
+    Trace tr;
     if (threads <= 0) threads = std::max(1u, std::thread::hardware_concurrency());
     MeshTopo X, Y;
     int chiX = 0, chiY = 0;
@@ -343,6 +358,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     P->nvx = nvx;
     P->nvy = nvy;
 
+    tr.mark("meshes");
     // ---- candidate rows
     Allowed A;
     A.full = mask == nullptr;
@@ -374,6 +390,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         }
     });
 
+    tr.mark("candidate rows");
     // ---- product space
     Elems E;
     enumerate(X, Y, A, threads, &E);
@@ -384,6 +401,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     P->vm = std::move(E.m);
     P->vn = std::move(E.n);
 
+    tr.mark("product space");
     // ---- costs: mean of the three pair costs, normalised by the largest
     const int nth = threads;
     P->cost.resize(nv);
@@ -408,6 +426,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         });
     }
 
+    tr.mark("costs");
     // ---- closedness rows: product edge (p, q), p < q in (m, n) order. Entries are bucketed by
     // the X vertex of p, each bucket sorted by (key, entry), rows are the runs of equal keys.
     if (uint64_t(nvx) * uint64_t(nvy) >= (uint64_t(1) << 32)) { *err = "meshes too large"; return DISCO_ERR_INVALID_ARG; }
@@ -458,6 +477,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                 }
         });
     }
+    tr.mark("closedness buckets");
     // order each bucket by (smaller vertex, larger vertex, entry); count rows per bucket
     std::vector<int64_t> brows(size_t(nvx) + 1, 0);
     const bool packed = nvy < (1 << 16);
@@ -511,6 +531,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     ent.reset();
     P->rhs.assign(size_t(n_closed), 0);
 
+    tr.mark("closedness rows");
     // ---- projection rows (counting sort keeps the element order inside a row)
     std::vector<int32_t> proj_row(size_t(2) * nv, -1);  // element -> X / Y projection row
     int64_t proj_end = ne;
@@ -562,11 +583,12 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     P->row_ptr.push_back(proj_end);
     const int64_t nr = P->nrows;
 
+    tr.mark("projection rows");
     // ---- presolve: saturated rows force all their free variables, to a fixpoint. Rounds
     // are bulk-synchronous (decide on a snapshot, apply, recount the touched rows), so the
     // result is the unique arc-consistent closure whatever the thread count.
     std::vector<int32_t> res(P->rhs.begin(), P->rhs.end());
-    std::vector<int32_t> npos(static_cast<size_t>(nr)), nneg(static_cast<size_t>(nr));
+    pod_vector<int32_t> npos(static_cast<size_t>(nr)), nneg(static_cast<size_t>(nr));
     P->fixed.assign(size_t(nv), -1);
     auto recount = [&](int64_t r) {
         int32_t rs = P->rhs[r], np = 0, nn = 0;
@@ -579,12 +601,21 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         npos[r] = np;
         nneg[r] = nn;
     };
-    parallel_chunks(nr, nth, [&](int, int64_t lo, int64_t hi) {
-        for (int64_t r = lo; r < hi; ++r) recount(r);
-    });
     {
-        std::vector<int64_t> frontier(static_cast<size_t>(nr));
-        std::iota(frontier.begin(), frontier.end(), int64_t(0));
+        // nothing is fixed yet: the counts are the coefficient counts; every row is in round 1
+        std::vector<std::vector<int64_t>> first(nth);
+        parallel_chunks(nr, nth, [&](int c, int64_t lo, int64_t hi) {
+            for (int64_t r = lo; r < hi; ++r) {
+                int32_t np = 0, nn = 0;
+                for (int64_t e = P->row_ptr[r]; e < P->row_ptr[r + 1]; ++e) (P->row_coef[e] > 0 ? np : nn)++;
+                npos[r] = np;
+                nneg[r] = nn;
+                // only saturated or violated rows can act
+                if (res[r] == np || res[r] == -nn || res[r] > np || res[r] < -nn) first[c].push_back(r);
+            }
+        });
+        std::vector<int64_t> frontier;
+        for (auto& x : first) frontier.insert(frontier.end(), x.begin(), x.end());
         std::vector<uint8_t> touched(static_cast<size_t>(nr), 0);
         std::atomic<int> bad{0};
         while (!frontier.empty() && !bad.load()) {
@@ -607,9 +638,6 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
             });
             if (bad.load()) break;
             // apply: first writer wins, a different value is a conflict; mark the touched rows
-            bool any = false;
-            for (auto& pc : prop) any = any || !pc.empty();
-            if (!any) break;
             parallel_chunks(nth, nth, [&](int c, int64_t, int64_t) {
                 for (auto [v, val] : prop[c]) {
                     int8_t expect = -1;
@@ -624,7 +652,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                 }
             });
             if (bad.load()) break;
-            // the touched rows are recounted and form the next frontier
+            // the touched rows, in row order, are recounted and form the next frontier
             std::vector<std::vector<int64_t>> next(nth);
             parallel_chunks(nr, nth, [&](int c, int64_t lo, int64_t hi) {
                 for (int64_t r = lo; r < hi; ++r)
@@ -641,6 +669,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     }
     for (int64_t r = 0; r < nr; ++r)
         if (npos[r] + nneg[r] == 0 && res[r] != 0) { *err = "presolve: violated row"; return DISCO_ERR_INFEASIBLE; }
+    tr.mark("presolve");
     P->constant = 0.0;
     std::vector<int32_t> internal(size_t(nv), -1);
     P->free_orig.clear();
@@ -653,6 +682,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     }
     P->n_free = int64_t(P->free_orig.size());
 
+    tr.mark("internal ids");
     // ---- BDD segments, compiled in parallel over row ranges; slot rank = which of the
     // variable's rows this is (closedness corner 0..2, then projection rows), so it is known
     // locally; auxiliaries get rank 0 in the left segment and 1 in the right one
@@ -755,6 +785,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     });
     for (const RowChunk& C : chunks)
         if (C.rc) { *err = C.err; return C.rc; }
+    tr.mark("bdd segments");
     // global offsets of slots, segments and auxiliaries per chunk
     std::vector<int64_t> slot_off(nrc + 1, 0), seg_off(nrc + 1, 0), aux_off(nrc + 1, 0);
     int64_t nodes = 0;
@@ -807,6 +838,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
             }
         }
     });
+    tr.mark("slot arrays");
     P->n_nodes = nodes;
     P->max_layers = max_layers;
     P->max_width = max_width;

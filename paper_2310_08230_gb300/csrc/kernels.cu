@@ -23,7 +23,7 @@ namespace disco {
 namespace {
 
 constexpr float BIG = 1e30f;
-constexpr int kWarpsPerBlock = 4;
+constexpr int kWarpsPerBlock = 2;
 
 struct Desc {
     int w, wn, d0, d1, one, rank, deg;
@@ -131,7 +131,7 @@ struct Layer {
 };
 
 template <int W>
-__host__ __device__ constexpr int depth() { return W <= 8 ? 4 : 2; }
+__host__ __device__ constexpr int depth() { return W <= 2 ? 4 : (W <= 4 ? 3 : 2); }
 
 __device__ __forceinline__ void load_head(const KArgs& a, int64_t si, bool ok, uint32_t& v, uint32_t& d) {
     v = ok ? __ldg(a.var + si) : kNoVar;

@@ -6,6 +6,7 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -33,6 +34,21 @@ struct uninit_alloc : std::allocator<T> {
 };
 template <class T>
 using pod_vector = std::vector<T, uninit_alloc<T>>;
+
+// Runs body(chunk, lo, hi) over [0, n) split into `nch` contiguous chunks on threads.
+template <class F>
+inline void parallel_chunks(int64_t n, int nch, F body) {
+    if (nch <= 1 || n < 2) {
+        body(0, int64_t(0), n);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (int c = 0; c < nch; ++c) {
+        const int64_t lo = n * c / nch, hi = n * (c + 1) / nch;
+        pool.emplace_back([&body, c, lo, hi] { body(c, lo, hi); });
+    }
+    for (auto& th : pool) th.join();
+}
 
 // Widest BDD layer the device kernels accept (node states held in registers).
 constexpr int kMaxWidth = 32;
