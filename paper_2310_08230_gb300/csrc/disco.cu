@@ -192,6 +192,7 @@ int to_host(const T* src, size_t n, std::vector<T>* out) {
 int width_class(int w) {
     if (w <= 2) return 2;
     if (w <= 4) return 4;
+    if (w <= 6) return 6;
     if (w <= 8) return 8;
     if (w <= 16) return 16;
     return 32;
@@ -220,7 +221,7 @@ int upload(disco_handle* h) {
         tiles.push_back(TileInfo{0, 0, L, W});
         tile_segs.push_back(ts);
     }
-    // classes 2, 4, 8 share one launch, longest tiles first; 16 and 32 launch on their own
+    // classes 2, 4, 6, 8 share one launch, longest tiles first; 16 and 32 launch on their own
     std::vector<size_t> tord(tiles.size());
     std::iota(tord.begin(), tord.end(), size_t(0));
     std::stable_sort(tord.begin(), tord.end(), [&](size_t a, size_t b) {

@@ -41,14 +41,18 @@ __device__ __forceinline__ Desc decode(uint32_t x) {
     return d;
 }
 
-// a[s + k] for a runtime k in [-2, 2] (s is a compile-time index after unrolling); BIG outside.
+// x[j + 1] = a[j + k] for every j in [-1, W] and a runtime k in {-1, 0, 1} (BIG outside
+// [0, W)). With x = the other layer's costs shifted by the 0-arc offset d0, an arithmetic
+// 1-arc (d1 = d0 +- 1) is x shifted by one more place, which stays inside [-1, W].
 template <int W>
-__device__ __forceinline__ float at_shift(const float (&a)[W], int s, int k) {
-    float r = BIG;
+__device__ __forceinline__ void shift_ext(const float (&a)[W], int k, float (&x)[W + 2]) {
 #pragma unroll
-    for (int j = -2; j <= 2; ++j)
-        if (s + j >= 0 && s + j < W) r = (k == j) ? a[s + j] : r;
-    return r;
+    for (int j = -1; j <= W; ++j) {
+        const float lo = (j - 1 >= 0 && j - 1 < W) ? a[(j - 1 >= 0 && j - 1 < W) ? j - 1 : 0] : BIG;
+        const float mid = (j >= 0 && j < W) ? a[(j >= 0 && j < W) ? j : 0] : BIG;
+        const float hi = (j + 1 >= 0 && j + 1 < W) ? a[(j + 1 >= 0 && j + 1 < W) ? j + 1 : 0] : BIG;
+        x[j + 1] = k < 0 ? lo : (k == 0 ? mid : hi);
+    }
 }
 
 // a[i] for a runtime i; BIG outside [0, W).
@@ -223,14 +227,18 @@ __device__ __forceinline__ void forward_tile(const KArgs& a, const int tile, con
                 float removed = 0.0f;
                 if (c.st == kFree) {
                     Lm = df_add(Lm, p);
+                    // hx[s + 1] = b of node s's 0-child, hx[s + 1 + a] = b of its arithmetic 1-child
+                    float hx[W + 2];
+                    shift_ext(c.nb, d.d0, hx);
+                    const bool up = d.d1 > d.d0;
                     float m0 = BIG, m1 = BIG;
 #pragma unroll
-                    for (int s = 0; s < W; ++s) m0 = fminf(m0, f[s] + at_shift(c.nb, s, d.d0));
+                    for (int s = 0; s < W; ++s) m0 = fminf(m0, f[s] + hx[s + 1]);
                     if (d.one) {
                         m1 = f[0] + at_dyn(c.nb, d.d1);
                     } else {
 #pragma unroll
-                        for (int s = 0; s < W; ++s) m1 = fminf(m1, f[s] + at_shift(c.nb, s, d.d1));
+                        for (int s = 0; s < W; ++s) m1 = fminf(m1, f[s] + (up ? hx[s + 2] : hx[s]));
                     }
                     const float M = (m1 + Lm.hi) - m0;
                     removed = a.omega * M;
@@ -243,12 +251,16 @@ __device__ __forceinline__ void forward_tile(const KArgs& a, const int tile, con
             } else {
                 lm = df_add(Lm, p).hi;
             }
+            // gx[s + 1] = f of node s's 0-parent, gx[s + 1 - a] = f of its arithmetic 1-parent
+            float gx[W + 2];
+            shift_ext(f, -d.d0, gx);
+            const bool upf = d.d1 > d.d0;
             float fn[W];
 #pragma unroll
             for (int s = 0; s < W; ++s) {
-                float v0 = al0 ? at_shift(f, s, -d.d0) : BIG;
+                const float v0 = al0 ? gx[s + 1] : BIG;
                 float v1 = BIG;
-                if (al1) v1 = (d.one ? (s == d.d1 ? f[0] : BIG) : at_shift(f, s, -d.d1)) + lm;
+                if (al1) v1 = (d.one ? (s == d.d1 ? f[0] : BIG) : (upf ? gx[s] : gx[s + 2])) + lm;
                 fn[s] = s < d.wn ? fminf(v0, v1) : BIG;
             }
 #pragma unroll
@@ -276,7 +288,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward(KArgs a) {
     forward_tile<W, MODE>(a, tile, ti);
 }
 
-// Width classes 2, 4 and 8 in one launch (tiles ordered longest first), so that short
+// Width classes 2, 4, 6 and 8 in one launch (tiles ordered longest first), so that short
 // tiles fill the SMs around the long ones.
 template <int MODE>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_fused(KArgs a) {
@@ -285,6 +297,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_fused(KArgs a) 
     const TileInfo ti = a.tiles[tile];
     if (ti.W == 2) forward_tile<2, MODE>(a, tile, ti);
     else if (ti.W == 4) forward_tile<4, MODE>(a, tile, ti);
+    else if (ti.W == 6) forward_tile<6, MODE>(a, tile, ti);
     else forward_tile<8, MODE>(a, tile, ti);
 }
 
@@ -336,16 +349,20 @@ __device__ __forceinline__ void backward_tile(const KArgs& a, const TileInfo& ti
                 const bool al0 = c.st != kFix1, al1 = c.st != kFix0;
                 float lm = Lm.hi;
                 const float b1 = d.one ? at_dyn(bn, d.d1) : BIG;  // target of node 0's 1-arc (one-hot chains)
+                // hx[s + 1] = b of node s's 0-child, hx[s + 1 + a] = b of its arithmetic 1-child
+                float hx[W + 2];
+                shift_ext(bn, d.d0, hx);
+                const bool up = d.d1 > d.d0;
                 if (kNeedF) {
                     float m0 = BIG, m1 = BIG;
 #pragma unroll
-                    for (int s = 0; s < W; ++s) m0 = fminf(m0, c.nb[s] + (al0 ? at_shift(bn, s, d.d0) : BIG));
+                    for (int s = 0; s < W; ++s) m0 = fminf(m0, c.nb[s] + (al0 ? hx[s + 1] : BIG));
                     if (al1) {
                         if (d.one) {
                             m1 = c.nb[0] + b1;
                         } else {
 #pragma unroll
-                            for (int s = 0; s < W; ++s) m1 = fminf(m1, c.nb[s] + at_shift(bn, s, d.d1));
+                            for (int s = 0; s < W; ++s) m1 = fminf(m1, c.nb[s] + (up ? hx[s + 2] : hx[s]));
                         }
                     }
                     if (kUpdate) {
@@ -372,9 +389,9 @@ __device__ __forceinline__ void backward_tile(const KArgs& a, const TileInfo& ti
                 float bc[W];
 #pragma unroll
                 for (int s = 0; s < W; ++s) {
-                    float v0 = al0 ? at_shift(bn, s, d.d0) : BIG;
+                    const float v0 = al0 ? hx[s + 1] : BIG;
                     float v1 = BIG;
-                    if (al1) v1 = (d.one ? (s == 0 ? b1 : BIG) : at_shift(bn, s, d.d1)) + lm;
+                    if (al1) v1 = (d.one ? (s == 0 ? b1 : BIG) : (up ? hx[s + 2] : hx[s])) + lm;
                     bc[s] = s < d.w ? fminf(v0, v1) : BIG;
                 }
                 if (kStoreB) {
@@ -410,6 +427,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_backward_fused(KArgs a)
     const TileInfo ti = a.tiles[tile];
     if (ti.W == 2) backward_tile<2, MODE>(a, ti);
     else if (ti.W == 4) backward_tile<4, MODE>(a, ti);
+    else if (ti.W == 6) backward_tile<6, MODE>(a, ti);
     else backward_tile<8, MODE>(a, ti);
 }
 

@@ -56,7 +56,7 @@ enum class Pass {
 };
 
 // Launches `pass` over the tiles [a.tile0, a.tile_end) of width class W (2, 4, 8, 16, 32);
-// W = 0: tiles of classes 2, 4 and 8 mixed in one launch (each tile carries its class).
+// W = 0: tiles of classes 2, 4, 6 and 8 mixed in one launch (each tile carries its class).
 cudaError_t launch_pass(Pass pass, int W, const KArgs& a, cudaStream_t s);
 
 cudaError_t launch_sum_tiles(const double* tile_sum, int64_t n, double add, double* out, cudaStream_t s);
