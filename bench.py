@@ -249,9 +249,105 @@ def gpu_arm(args):
                      "alg_bytes_per_launch": alg_bytes, "launch_ms": half_pass_ms, "peak_kind": kind},
         "clocks": clk.summary(),
     }
+    if not args.no_batched:
+        line["batched"] = batched_vs_single(torch)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)
+
+
+def batched_vs_single(torch, iters: int = 300, n_pairs: int = 64, split_chunk: int = 32) -> dict:
+    """64 uneven pairs: one batched handle against the same pairs solved one after another.
+
+    Both sides run the whole path per pair (pair costs, candidates, build, `iters` dual
+    iterations, bound, rounding) on device-resident features; times are CUDA-event times on
+    one stream with host work in between included."""
+    from paper_2310_08230_gb300 import _lib as L
+    from paper_2310_08230_gb300.api import _mesh, default_opts
+    from synth import instances as I
+
+    lib = L.lib()
+    insts = I.config4(n_pairs)
+    stream = torch.cuda.Stream()
+    sptr = int(stream.cuda_stream)
+    feats = [(torch.from_numpy(i.FX).cuda(), torch.from_numpy(i.FY).cuda()) for i in insts]
+    ds = [torch.empty((i.X.nv, i.Y.nv), dtype=torch.float32, device="cuda") for i in insts]
+    al = [torch.empty((i.X.nv, i.Y.nv), dtype=torch.uint8, device="cuda") for i in insts]
+    meshes = [(_mesh(i.X.T, i.X.nv), _mesh(i.Y.T, i.Y.nv)) for i in insts]
+    opts = default_opts(stream=sptr, split_chunk=split_chunk)
+
+    def costs(k):
+        i = insts[k]
+        (FX, FY), d, a = feats[k], ds[k], al[k]
+        (mx, _), (my, _) = meshes[k]
+        L.check(lib.disco_pair_costs(FX.data_ptr(), FY.data_ptr(), i.X.nv, i.Y.nv, i.FX.shape[1], d.data_ptr(), sptr),
+                "pair_costs")
+        L.check(lib.disco_candidates(d.data_ptr(), i.X.nv, i.Y.nv, i.topk, ctypes.byref(mx), ctypes.byref(my),
+                                     a.data_ptr(), sptr), "candidates")
+
+    def batched():
+        for k in range(n_pairs):
+            costs(k)
+        MX = (L.disco_mesh * n_pairs)(*[m[0][0] for m in meshes])
+        MY = (L.disco_mesh * n_pairs)(*[m[1][0] for m in meshes])
+        dp = (ctypes.c_void_p * n_pairs)(*[d.data_ptr() for d in ds])
+        ap = (ctypes.c_void_p * n_pairs)(*[a.data_ptr() for a in al])
+        h = ctypes.c_void_p()
+        L.check(lib.disco_build_batch(n_pairs, MX, MY, ctypes.cast(dp, ctypes.c_void_p), ctypes.cast(ap, ctypes.c_void_p),
+                                      ctypes.byref(opts), ctypes.byref(h)), "build_batch")
+        info = L.disco_info_t()
+        lib.disco_info(h, ctypes.byref(info))
+        L.check(lib.disco_dual(h, iters), "dual")
+        lbs = np.zeros(n_pairs)
+        L.check(lib.disco_lower_bounds(h, lbs.ctypes.data_as(L.c_double_p), n_pairs), "lbs")
+        x = np.zeros(info.nvars, np.uint8)
+        cs = np.zeros(n_pairs)
+        st = np.zeros(n_pairs, np.int32)
+        lib.disco_primal_batch(h, x.ctypes.data, info.nvars, cs.ctypes.data_as(L.c_double_p),
+                               st.ctypes.data_as(L.c_int32_p), n_pairs)
+        lib.disco_free(h)
+        return info.nnodes, lbs, cs, st
+
+    def single():
+        nodes, lbs, cs, st = 0, [], [], []
+        for k in range(n_pairs):
+            costs(k)
+            (mx, _), (my, _) = meshes[k]
+            h = ctypes.c_void_p()
+            L.check(lib.disco_build(ctypes.byref(mx), ctypes.byref(my), ds[k].data_ptr(), al[k].data_ptr(),
+                                    ctypes.byref(opts), ctypes.byref(h)), "build")
+            info = L.disco_info_t()
+            lib.disco_info(h, ctypes.byref(info))
+            nodes += info.nnodes
+            L.check(lib.disco_dual(h, iters), "dual")
+            lb = ctypes.c_double()
+            L.check(lib.disco_lower_bound(h, ctypes.byref(lb)), "lb")
+            x = np.zeros(info.nvars, np.uint8)
+            c = ctypes.c_double()
+            rc = lib.disco_primal(h, x.ctypes.data, info.nvars, ctypes.byref(c))
+            lib.disco_free(h)
+            lbs.append(lb.value)
+            cs.append(c.value)
+            st.append(rc)
+        return nodes, np.array(lbs), np.array(cs), np.array(st)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    timed(batched)  # warm-up (pool, modules)
+    tb, (nodes, lbs_b, cs_b, st_b) = timed(batched)
+    ts, (nodes_s, lbs_s, cs_s, st_s) = timed(single)
+    upd = 2.0 * nodes * iters
+    return {"pairs": n_pairs, "iters": iters, "bdd_nodes": int(nodes), "batched_ms": tb, "one_by_one_ms": ts,
+            "batched_node_updates_per_s": upd / (tb / 1e3), "one_by_one_node_updates_per_s": upd / (ts / 1e3),
+            "speedup": ts / tb, "feasible_batched": int((st_b == 0).sum()), "feasible_one_by_one": int((st_s == 0).sum()),
+            "max_rel_bound_diff": float(np.max(np.abs(lbs_b - lbs_s) / np.maximum(np.abs(lbs_s), 1e-12)))}
 
 
 def cpu_baseline(seconds: float) -> dict:
@@ -322,6 +418,7 @@ def main():
     ap.add_argument("--max-iters", type=int, default=20000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

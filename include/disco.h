@@ -71,7 +71,10 @@ typedef struct {
     int32_t device;           /* [0] CUDA device ordinal */
     void *stream;             /* [NULL] cudaStream_t to issue work on; NULL = own stream */
     int32_t host_threads;     /* [0] threads for the host compiler; 0 = hardware concurrency */
-    int32_t reserved[7];
+    int32_t split_max_segments; /* [8] at most this many segments per row when splitting (0 = no
+                                 cap): a one-hot chain carries cost information across one cut
+                                 per half-pass, so very long rows are cut into longer segments */
+    int32_t reserved[6];
 } disco_opts;
 
 typedef struct {
@@ -147,7 +150,8 @@ int disco_build(const disco_mesh *X, const disco_mesh *Y, const float *d, const 
 
 /*
  * Host-only compilation, for inspection (no CUDA call): runs the same compiler as
- * disco_build on host arrays d and allowed (allowed may be NULL) and fills *info (iterations,
+ * disco_build (split options as in disco_opts) on host arrays d and allowed (allowed may be
+ * NULL) and fills *info (iterations,
  * ntiles, device_bytes = 0). Optional outputs, each ignored when NULL or too small:
  *   slot_var[nslots]   variable of every slot in canonical order: a matching-element id,
  *                      or nvars + k for the k-th auxiliary variable of splitting;
@@ -156,8 +160,41 @@ int disco_build(const disco_mesh *X, const disco_mesh *Y, const float *d, const 
  * Call once with NULL outputs to learn the sizes. Errors as disco_build.
  */
 int disco_compile_host(const disco_mesh *X, const disco_mesh *Y, const float *d, const uint8_t *allowed,
-                       int32_t split_chunk, disco_info_t *info, int32_t *slot_var, int32_t *slot_width,
-                       int64_t nslots, int8_t *fixed, int64_t nvars);
+                       int32_t split_chunk, int32_t split_max_segments, disco_info_t *info,
+                       int32_t *slot_var, int32_t *slot_width, int64_t nslots, int8_t *fixed,
+                       int64_t nvars);
+
+/*
+ * Batched build (BASELINE pattern "batching"; the paper solves one pair at a time): n
+ * independent shape pairs in ONE handle and one device store, so that every half-pass of
+ * every pair runs in the same kernel launches. X, Y: n meshes each (host); d[i], allowed[i]:
+ * per pair as in disco_build (allowed may be NULL, or hold NULL entries). The pairs are
+ * compiled on the host side by side. On a batch handle the single-instance calls act on all
+ * pairs: disco_dual iterates all of them, disco_lower_bound returns the sum of their bounds,
+ * disco_min_marginals / disco_get_state / disco_set_state concatenate the pairs' canonical
+ * slots (and variables) in pair order, disco_primal writes the pairs' x one after another
+ * (disco_instance_info gives each pair's sizes) and returns the summed cost; disco_info
+ * reports totals. Errors as disco_build (the message names the failing pair).
+ */
+int disco_build_batch(int32_t n, const disco_mesh *X, const disco_mesh *Y, const float *const *d,
+                      const uint8_t *const *allowed, const disco_opts *opts, disco_handle **out);
+
+/* Number of pairs in the handle (1 for disco_build). */
+int disco_batch_size(disco_handle *h, int32_t *n);
+
+/* Per-pair lower bounds (as disco_lower_bound) into lb[0 .. n). Synchronises. */
+int disco_lower_bounds(disco_handle *h, double *lb, int32_t n);
+
+/* Sizes of pair i of the handle (ntiles = its warp tiles). */
+int disco_instance_info(disco_handle *h, int32_t i, disco_info_t *info);
+
+/*
+ * Rounding of all pairs (as disco_primal). x_out: sum of the pairs' nvars bytes, pair after
+ * pair; costs[i] (may be NULL): pair i's c^T x; status[i] (may be NULL): DISCO_OK or
+ * DISCO_ERR_PRIMAL_FAILED for pair i. Returns DISCO_OK iff every pair is feasible.
+ */
+int disco_primal_batch(disco_handle *h, uint8_t *x_out, int64_t nvars, double *costs, int32_t *status,
+                       int32_t n);
 
 /* Runs `iters` dual iterations (forward + backward half-pass of deferred min-marginal
  * averaging, Alg. 1 "MMA"). Asynchronous on the handle's stream. */
@@ -198,7 +235,8 @@ int disco_set_state(disco_handle *h, const float *lam, int64_t n, const float *p
 /* Problem and store statistics. */
 int disco_info(disco_handle *h, disco_info_t *info);
 
-/* Releases the handle (NULL is allowed). */
+/* Releases the handle (NULL is allowed). A handle built on a caller's stream must be freed
+ * before that stream is destroyed (its device memory is returned on that stream). */
 void disco_free(disco_handle *h);
 
 /* Static string for a return code. */

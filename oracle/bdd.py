@@ -18,8 +18,10 @@ Plain Python, explicit node graphs. Test infrastructure only (see
 
 Readings: a cut whose next layer has a single node needs no auxiliary variable
 (both parts share no variable); segments are balanced: a row of n layers with
-chunk c > 0 and n > c is cut into ceil(n/c) segments at layers
-floor(s n / ceil(n/c)).
+chunk c > 0 and n > c is cut into S = min(ceil(n/c), K) segments at layers
+floor(s n / S), K = the segment cap (0 = none). The cap keeps very long rows in
+few segments: a one-hot chain carries cost information across one cut per
+half-pass.
 """
 from __future__ import annotations
 
@@ -167,19 +169,21 @@ def split(bdd: BDD, cut: int, aux_ids: list | None) -> tuple[BDD, BDD]:
     return left, right
 
 
-def segment_bounds(n: int, chunk: int) -> list:
+def segment_bounds(n: int, chunk: int, max_segments: int = 8) -> list:
     """Layer indices where segments start (balanced), plus n."""
     if chunk <= 0 or n <= chunk:
         return [0, n]
     nseg = -(-n // chunk)
+    if max_segments > 0:
+        nseg = min(nseg, max_segments)
     return [(s * n) // nseg for s in range(nseg + 1)]
 
 
-def split_row(bdd: BDD, chunk: int, next_aux: int) -> tuple[list, list, int]:
+def split_row(bdd: BDD, chunk: int, next_aux: int, max_segments: int = 8) -> tuple[list, list, int]:
     """Cut a row's BDD into balanced segments. Returns (segments, aux var ids, next free id).
 
     Auxiliary ids are handed out cut by cut (left to right), y_1..y_k within a cut."""
-    bounds = segment_bounds(bdd.n_layers, chunk)
+    bounds = segment_bounds(bdd.n_layers, chunk, max_segments)
     segs = []
     aux = []
     rest = bdd
@@ -253,7 +257,7 @@ def flatten(bdds: list, rows: list, nvars: int, nvars_total: int, cost: np.ndarr
                          cost, free, const, bdds)
 
 
-def decompose(prob, fixed: np.ndarray, const: float, chunk: int = 0) -> Decomposition:
+def decompose(prob, fixed: np.ndarray, const: float, chunk: int = 0, max_segments: int = 8) -> Decomposition:
     """Compile every row that still has free variables (after presolve) into BDD segments.
 
     Fixed variables are substituted into the right-hand side. Rows keep their order
@@ -270,7 +274,7 @@ def decompose(prob, fixed: np.ndarray, const: float, chunk: int = 0) -> Decompos
             assert rr == 0
             continue
         bdd, _ = compile_row(v[sel], a[sel], rr)
-        segs, _aux, next_aux = split_row(bdd, chunk, next_aux)
+        segs, _aux, next_aux = split_row(bdd, chunk, next_aux, max_segments)
         bdds += segs
         rows += [r] * len(segs)
     cost = np.concatenate([prob.cost, np.zeros(next_aux - prob.nvars)])

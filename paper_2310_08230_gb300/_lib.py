@@ -35,7 +35,8 @@ class disco_opts(ctypes.Structure):
         ("conv_rel_tol", ctypes.c_double), ("primal_rounds", ctypes.c_int32), ("primal_inner_iters", ctypes.c_int32),
         ("perturb_delta0", ctypes.c_float), ("perturb_growth", ctypes.c_float), ("tie_tau", ctypes.c_float),
         ("propagate_limit", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
-        ("host_threads", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7),
+        ("host_threads", ctypes.c_int32), ("split_max_segments", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 6),
     ]
 
 
@@ -57,7 +58,13 @@ SIGNATURES = {
                                                 ctypes.POINTER(disco_mesh), P, P]),
     "disco_build": (ctypes.c_int, [ctypes.POINTER(disco_mesh), ctypes.POINTER(disco_mesh), P, P,
                                    ctypes.POINTER(disco_opts), ctypes.POINTER(ctypes.c_void_p)]),
-    "disco_compile_host": (ctypes.c_int, [ctypes.POINTER(disco_mesh), ctypes.POINTER(disco_mesh), P, P, I32,
+    "disco_build_batch": (ctypes.c_int, [I32, ctypes.POINTER(disco_mesh), ctypes.POINTER(disco_mesh), P, P,
+                                         ctypes.POINTER(disco_opts), ctypes.POINTER(ctypes.c_void_p)]),
+    "disco_batch_size": (ctypes.c_int, [P, c_int32_p]),
+    "disco_lower_bounds": (ctypes.c_int, [P, c_double_p, I32]),
+    "disco_instance_info": (ctypes.c_int, [P, I32, ctypes.POINTER(disco_info_t)]),
+    "disco_primal_batch": (ctypes.c_int, [P, P, I64, c_double_p, c_int32_p, I32]),
+    "disco_compile_host": (ctypes.c_int, [ctypes.POINTER(disco_mesh), ctypes.POINTER(disco_mesh), P, P, I32, I32,
                                           ctypes.POINTER(disco_info_t), P, P, I64, P, I64]),
     "disco_dual": (ctypes.c_int, [P, I32]),
     "disco_lower_bound": (ctypes.c_int, [P, c_double_p]),

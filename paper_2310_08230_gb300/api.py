@@ -147,6 +147,67 @@ class Solver:
                                         None if pp is None else pp.ctypes.data, 0 if pp is None else pp.shape[0]),
                 "disco_set_state")
 
+    @classmethod
+    def batch(cls, pairs, **opts) -> "Solver":
+        """One handle over several pairs: ``pairs`` = [(TX, TY, d, allowed_or_None), ...]."""
+        self = cls.__new__(cls)
+        n = len(pairs)
+        meshes_x = (L.disco_mesh * n)()
+        meshes_y = (L.disco_mesh * n)()
+        keep = []
+        dptr = (ctypes.c_void_p * n)()
+        aptr = (ctypes.c_void_p * n)()
+        for i, (TX, TY, d, allowed) in enumerate(pairs):
+            if isinstance(d, np.ndarray):
+                d = np.ascontiguousarray(d, dtype=np.float32)
+            if isinstance(allowed, np.ndarray):
+                allowed = np.ascontiguousarray(allowed, dtype=np.uint8)
+            mx, tx = _mesh(TX, int(d.shape[0]))
+            my, ty = _mesh(TY, int(d.shape[1]))
+            meshes_x[i] = mx
+            meshes_y[i] = my
+            dptr[i] = _ptr(d)
+            aptr[i] = None if allowed is None else _ptr(allowed)
+            keep += [tx, ty, d, allowed]
+        self.opts = default_opts(**opts)
+        h = ctypes.c_void_p()
+        L.check(L.lib().disco_build_batch(n, meshes_x, meshes_y, ctypes.cast(dptr, ctypes.c_void_p),
+                                          ctypes.cast(aptr, ctypes.c_void_p), ctypes.byref(self.opts),
+                                          ctypes.byref(h)), "disco_build_batch")
+        self.h = h
+        self._keep = keep
+        return self
+
+    def batch_size(self) -> int:
+        n = ctypes.c_int32()
+        L.check(L.lib().disco_batch_size(self.h, ctypes.byref(n)), "disco_batch_size")
+        return n.value
+
+    def lower_bounds(self) -> np.ndarray:
+        n = self.batch_size()
+        out = np.zeros(n, np.float64)
+        L.check(L.lib().disco_lower_bounds(self.h, out.ctypes.data_as(L.c_double_p), n), "disco_lower_bounds")
+        return out
+
+    def instance_info(self, i: int) -> dict:
+        inf = L.disco_info_t()
+        L.check(L.lib().disco_instance_info(self.h, int(i), ctypes.byref(inf)), "disco_instance_info")
+        return {k: getattr(inf, k) for k, _ in inf._fields_ if k != "reserved"}
+
+    def primal_batch(self) -> tuple[list, np.ndarray, np.ndarray]:
+        """Per pair: (x_i, cost_i, feasible_i)."""
+        n = self.batch_size()
+        sizes = [self.instance_info(i)["nvars"] for i in range(n)]
+        x = np.zeros(sum(sizes), np.uint8)
+        costs = np.zeros(n, np.float64)
+        status = np.zeros(n, np.int32)
+        rc = L.lib().disco_primal_batch(self.h, x.ctypes.data, x.shape[0], costs.ctypes.data_as(L.c_double_p),
+                                        status.ctypes.data_as(L.c_int32_p), n)
+        if rc not in (L.DISCO_OK, L.DISCO_ERR_PRIMAL_FAILED):
+            L.check(rc, "disco_primal_batch")
+        xs = np.split(x, np.cumsum(sizes)[:-1])
+        return xs, costs, status == 0
+
     def close(self) -> None:
         if getattr(self, "h", None):
             L.lib().disco_free(self.h)

@@ -84,7 +84,11 @@ struct disco_handle {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     disco_opts opts{};
-    Plan plan;
+    std::vector<Plan> plans;              // one per instance
+    std::vector<int64_t> var_base;        // internal variable offset per instance (n + 1)
+    std::vector<int64_t> slot_base;       // canonical slot offset per instance (n + 1)
+    std::vector<int64_t> elem_base;       // matching-element offset per instance (n + 1)
+    std::vector<int32_t> inst_tile_ptr;   // tiles of instance i: inst_tiles[ptr[i] .. ptr[i+1])
     std::vector<WidthClass> classes;
     int64_t ntiles = 0, nslots_tile = 0, nnodes_tile = 0, nint = 0;
     // device buffers
@@ -98,7 +102,10 @@ struct disco_handle {
     float* acc[2] = {nullptr, nullptr};
     int cur = 0;
     double* tile_sum = nullptr;
-    double* scalar = nullptr;      // [0] lower bound
+    double* scalar = nullptr;      // per instance: lower bound
+    double* consts = nullptr;      // per instance: presolve constant
+    int32_t* d_inst_tile_ptr = nullptr;
+    int32_t* d_inst_tiles = nullptr;
     int64_t* canon_pos = nullptr;  // canonical slot -> tile slot
     uint8_t* deg = nullptr;
     uint8_t* state = nullptr;
@@ -108,12 +115,16 @@ struct disco_handle {
     float* mm_var = nullptr;
     float* mm_slot = nullptr;
     float* tmp = nullptr;          // nslots floats (canonical-order staging)
-    int* counters = nullptr;
-    int* h_counters = nullptr;     // pinned
-    double* h_scalar = nullptr;    // pinned
+    int* counters = nullptr;       // 4 per instance
+    int32_t* var_inst = nullptr;   // instance of every internal variable
+    int* h_counters = nullptr;     // pinned, 4 per instance
+    double* h_scalar = nullptr;    // pinned, one per instance
     int64_t device_bytes = 0;
     int64_t iterations = 0;
     double upload_ms = 0.0;
+    int64_t n_inst() const { return int64_t(plans.size()); }
+    int64_t nslots() const { return slot_base.back(); }
+    int64_t nelems() const { return elem_base.back(); }
     bool has_b = false;
     std::vector<void*> allocations;
     cudaGraphExec_t iter_graph = nullptr;
@@ -199,45 +210,72 @@ int width_class(int w) {
 }
 
 int upload(disco_handle* h) {
-    const Plan& P = h->plan;
-    const int64_t nseg = int64_t(P.segs.size());
-    // ---- tiles: segments grouped by width class, longest first within a class
-    std::vector<int64_t> order(nseg);
-    std::iota(order.begin(), order.end(), 0);
-    std::vector<uint8_t> wcls(static_cast<size_t>(nseg));
-    for (int64_t i = 0; i < nseg; ++i) wcls[i] = uint8_t(width_class(P.segs[i].max_width));
-    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
-        if (wcls[a] != wcls[b]) return wcls[a] < wcls[b];
-        return P.segs[a].n_layers > P.segs[b].n_layers;
-    });
+    const int64_t ni = h->n_inst();
+    const int nth = host_threads(h->opts);
+    h->var_base.assign(size_t(ni) + 1, 0);
+    h->slot_base.assign(size_t(ni) + 1, 0);
+    h->elem_base.assign(size_t(ni) + 1, 0);
+    for (int64_t i = 0; i < ni; ++i) {
+        const Plan& P = h->plans[i];
+        h->var_base[i + 1] = h->var_base[i] + P.n_free + P.n_aux;
+        h->slot_base[i + 1] = h->slot_base[i] + int64_t(P.slot_var.size());
+        h->elem_base[i + 1] = h->elem_base[i] + P.nvars;
+    }
+    h->nint = h->var_base[ni];
+    if (h->nint >= (int64_t(1) << 32) - 1) return fail(DISCO_ERR_INVALID_ARG, "build: too many variables");
+    // ---- tiles: per instance, segments grouped by width class, longest first; a tile never
+    // mixes instances (its bound sum belongs to one instance)
+    struct TileSeg {
+        int32_t inst;
+        int64_t seg;
+    };
     std::vector<TileInfo> tiles;
-    std::vector<std::vector<int64_t>> tile_segs;
-    for (int64_t i = 0; i < nseg;) {
-        const int W = width_class(P.segs[order[i]].max_width);
-        std::vector<int64_t> ts;
-        for (int k = 0; k < 32 && i < nseg && width_class(P.segs[order[i]].max_width) == W; ++k, ++i) ts.push_back(order[i]);
-        int L = 0;
-        for (int64_t sg : ts) L = std::max(L, P.segs[sg].n_layers);
-        tiles.push_back(TileInfo{0, 0, L, W});
-        tile_segs.push_back(ts);
+    std::vector<std::vector<TileSeg>> tile_segs;
+    std::vector<int32_t> tile_inst;
+    for (int64_t i = 0; i < ni; ++i) {
+        const Plan& P = h->plans[i];
+        const int64_t nseg = int64_t(P.segs.size());
+        std::vector<int64_t> order(nseg);
+        std::iota(order.begin(), order.end(), 0);
+        std::vector<uint8_t> wcls(static_cast<size_t>(nseg));
+        for (int64_t k = 0; k < nseg; ++k) wcls[k] = uint8_t(width_class(P.segs[k].max_width));
+        std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+            if (wcls[x] != wcls[y]) return wcls[x] < wcls[y];
+            return P.segs[x].n_layers > P.segs[y].n_layers;
+        });
+        for (int64_t k = 0; k < nseg;) {
+            const int W = wcls[order[k]];
+            std::vector<TileSeg> ts;
+            int L = 0;
+            for (int q = 0; q < 32 && k < nseg && wcls[order[k]] == W; ++q, ++k) {
+                ts.push_back(TileSeg{int32_t(i), order[k]});
+                L = std::max(L, P.segs[order[k]].n_layers);
+            }
+            tiles.push_back(TileInfo{0, 0, L, W});
+            tile_segs.push_back(std::move(ts));
+            tile_inst.push_back(int32_t(i));
+        }
     }
     // classes 2, 4, 6, 8 share one launch, longest tiles first; 16 and 32 launch on their own
     std::vector<size_t> tord(tiles.size());
     std::iota(tord.begin(), tord.end(), size_t(0));
-    std::stable_sort(tord.begin(), tord.end(), [&](size_t a, size_t b) {
-        const int ga = tiles[a].W <= 8 ? 0 : tiles[a].W, gb = tiles[b].W <= 8 ? 0 : tiles[b].W;
-        if (ga != gb) return ga < gb;
-        return tiles[a].L > tiles[b].L;
+    std::stable_sort(tord.begin(), tord.end(), [&](size_t x, size_t y) {
+        const int gx = tiles[x].W <= 8 ? 0 : tiles[x].W, gy = tiles[y].W <= 8 ? 0 : tiles[y].W;
+        if (gx != gy) return gx < gy;
+        return tiles[x].L > tiles[y].L;
     });
     {
         std::vector<TileInfo> t2;
-        std::vector<std::vector<int64_t>> s2;
+        std::vector<std::vector<TileSeg>> s2;
+        std::vector<int32_t> i2;
         for (size_t k : tord) {
             t2.push_back(tiles[k]);
-            s2.push_back(tile_segs[k]);
+            s2.push_back(std::move(tile_segs[k]));
+            i2.push_back(tile_inst[k]);
         }
         tiles.swap(t2);
         tile_segs.swap(s2);
+        tile_inst.swap(i2);
     }
     h->classes.clear();
     int64_t slot_base = 0, node_base = 0;
@@ -253,13 +291,21 @@ int upload(disco_handle* h) {
     h->ntiles = int64_t(tiles.size());
     h->nslots_tile = slot_base;
     h->nnodes_tile = node_base;
-    h->nint = P.n_free + P.n_aux;
-    const int64_t nslots = int64_t(P.slot_var.size());
+    // tiles of each instance, in tile order (the bound sums them in this fixed order)
+    h->inst_tile_ptr.assign(size_t(ni) + 1, 0);
+    for (int32_t i : tile_inst) ++h->inst_tile_ptr[i + 1];
+    for (int64_t i = 0; i < ni; ++i) h->inst_tile_ptr[i + 1] += h->inst_tile_ptr[i];
+    std::vector<int32_t> inst_tiles(tiles.size());
+    {
+        std::vector<int32_t> pos(h->inst_tile_ptr.begin(), h->inst_tile_ptr.end() - 1);
+        for (size_t t = 0; t < tiles.size(); ++t) inst_tiles[pos[tile_inst[t]]++] = int32_t(t);
+    }
+    const int64_t nslots = h->nslots();
 
     pod_vector<uint32_t> hvar(slot_base), hdesc(slot_base);
     pod_vector<float> hlam(slot_base), hlam_lo(slot_base);
     pod_vector<int64_t> canon(nslots);
-    parallel_chunks(int64_t(tiles.size()), host_threads(h->opts), [&](int, int64_t t0, int64_t t1) {
+    parallel_chunks(int64_t(tiles.size()), nth, [&](int, int64_t t0, int64_t t1) {
         for (int64_t t = t0; t < t1; ++t) {
             const int64_t b0 = tiles[t].slot_base, b1 = b0 + int64_t(tiles[t].L) * 32;
             std::fill(hvar.begin() + b0, hvar.begin() + b1, kNoVar);
@@ -267,19 +313,31 @@ int upload(disco_handle* h) {
             std::fill(hlam.begin() + b0, hlam.begin() + b1, 0.0f);
             std::fill(hlam_lo.begin() + b0, hlam_lo.begin() + b1, 0.0f);
             for (size_t lane = 0; lane < tile_segs[t].size(); ++lane) {
-                const Segment& sg = P.segs[tile_segs[t][lane]];
+                const int32_t i = tile_segs[t][lane].inst;
+                const Plan& P = h->plans[i];
+                const Segment& sg = P.segs[tile_segs[t][lane].seg];
+                const uint32_t vb = uint32_t(h->var_base[i]);
+                const int64_t cb = h->slot_base[i];
                 for (int l = 0; l < sg.n_layers; ++l) {
                     const int64_t pos = b0 + int64_t(l) * 32 + int64_t(lane);
                     const int64_t c = sg.first_slot + l;
-                    hvar[pos] = uint32_t(P.slot_var[c]);
+                    hvar[pos] = vb + uint32_t(P.slot_var[c]);
                     hdesc[pos] = P.slot_desc[c];
                     hlam[pos] = P.slot_lam0[c];
                     hlam_lo[pos] = P.slot_lam0_lo[c];
-                    canon[c] = pos;
+                    canon[cb + c] = pos;
                 }
             }
         }
     });
+    std::vector<uint8_t> deg(static_cast<size_t>(h->nint));
+    std::vector<int32_t> var_inst(static_cast<size_t>(h->nint));
+    std::vector<double> consts(static_cast<size_t>(ni));
+    for (int64_t i = 0; i < ni; ++i) {
+        std::copy(h->plans[i].deg.begin(), h->plans[i].deg.end(), deg.begin() + h->var_base[i]);
+        std::fill(var_inst.begin() + h->var_base[i], var_inst.begin() + h->var_base[i + 1], int32_t(i));
+        consts[i] = h->plans[i].constant;
+    }
     int rc;
     if ((rc = h->alloc(&h->tiles, h->ntiles))) return rc;
     if ((rc = h->alloc(&h->var, slot_base))) return rc;
@@ -291,7 +349,10 @@ int upload(disco_handle* h) {
     if ((rc = h->alloc(&h->acc[0], h->nint * kAccStride))) return rc;
     if ((rc = h->alloc(&h->acc[1], h->nint * kAccStride))) return rc;
     if ((rc = h->alloc(&h->tile_sum, h->ntiles))) return rc;
-    if ((rc = h->alloc(&h->scalar, 4))) return rc;
+    if ((rc = h->alloc(&h->scalar, ni))) return rc;
+    if ((rc = h->alloc(&h->consts, ni))) return rc;
+    if ((rc = h->alloc(&h->d_inst_tile_ptr, ni + 1))) return rc;
+    if ((rc = h->alloc(&h->d_inst_tiles, h->ntiles))) return rc;
     if ((rc = h->alloc(&h->canon_pos, nslots))) return rc;
     if ((rc = h->alloc(&h->deg, h->nint))) return rc;
     if ((rc = h->alloc(&h->state, h->nint))) return rc;
@@ -301,9 +362,10 @@ int upload(disco_handle* h) {
     if ((rc = h->alloc(&h->mm_var, h->nint * kAccStride))) return rc;
     if ((rc = h->alloc(&h->mm_slot, slot_base))) return rc;
     if ((rc = h->alloc(&h->tmp, std::max(nslots, h->nint)))) return rc;
-    if ((rc = h->alloc(&h->counters, 4))) return rc;
-    CK(cudaMallocHost(&h->h_counters, 4 * sizeof(int)));
-    CK(cudaMallocHost(&h->h_scalar, 4 * sizeof(double)));
+    if ((rc = h->alloc(&h->counters, 4 * ni))) return rc;
+    if ((rc = h->alloc(&h->var_inst, h->nint))) return rc;
+    CK(cudaMallocHost(&h->h_counters, size_t(4 * std::max<int64_t>(ni, 1)) * sizeof(int)));
+    CK(cudaMallocHost(&h->h_scalar, size_t(std::max<int64_t>(ni, 1)) * sizeof(double)));
     cudaStream_t s = h->stream;
     if ((rc = copy_in(h->tiles, tiles.data(), tiles.size() * sizeof(TileInfo), s))) return rc;
     if ((rc = copy_in(h->var, hvar.data(), hvar.size() * 4, s))) return rc;
@@ -311,7 +373,11 @@ int upload(disco_handle* h) {
     if ((rc = copy_in(h->lam, hlam.data(), hlam.size() * 4, s))) return rc;
     if ((rc = copy_in(h->lam_lo, hlam_lo.data(), hlam_lo.size() * 4, s))) return rc;
     if ((rc = copy_in(h->canon_pos, canon.data(), canon.size() * 8, s))) return rc;
-    if ((rc = copy_in(h->deg, P.deg.data(), P.deg.size(), s))) return rc;
+    if ((rc = copy_in(h->deg, deg.data(), deg.size(), s))) return rc;
+    if ((rc = copy_in(h->var_inst, var_inst.data(), var_inst.size() * 4, s))) return rc;
+    if ((rc = copy_in(h->consts, consts.data(), consts.size() * 8, s))) return rc;
+    if ((rc = copy_in(h->d_inst_tile_ptr, h->inst_tile_ptr.data(), h->inst_tile_ptr.size() * 4, s))) return rc;
+    if ((rc = copy_in(h->d_inst_tiles, inst_tiles.data(), inst_tiles.size() * 4, s))) return rc;
     CK(cudaMemsetAsync(h->F, 0, size_t(node_base) * 4, s));
     CK(cudaMemsetAsync(h->B, 0, size_t(node_base) * 4, s));
     CK(cudaMemsetAsync(h->acc[0], 0, size_t(h->nint) * kAccStride * 4, s));
@@ -340,13 +406,24 @@ int run_iterations(disco_handle* h, int iters) {
     return DISCO_OK;
 }
 
-int lower_bound(disco_handle* h, double* lb) {
+// Per-instance lower bounds E(lambda + pend) + constant into h->h_scalar[0 .. n).
+int lower_bounds(disco_handle* h) {
     int rc = h->pass(Pass::Lb);
     if (rc) return rc;
-    CK(launch_sum_tiles(h->tile_sum, h->ntiles, h->plan.constant, h->scalar, h->stream));
-    CK(cudaMemcpyAsync(h->h_scalar, h->scalar, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(launch_sum_instances(h->tile_sum, h->d_inst_tile_ptr, h->d_inst_tiles, h->consts, h->n_inst(), h->scalar,
+                            h->stream));
+    CK(cudaMemcpyAsync(h->h_scalar, h->scalar, size_t(h->n_inst()) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    *lb = h->h_scalar[0];
+    return DISCO_OK;
+}
+
+// Sum of the instances' bounds (the bound of a single instance).
+int lower_bound(disco_handle* h, double* lb) {
+    int rc = lower_bounds(h);
+    if (rc) return rc;
+    double s = 0.0;
+    for (int64_t i = 0; i < h->n_inst(); ++i) s += h->h_scalar[i];
+    *lb = s;
     return DISCO_OK;
 }
 
@@ -382,6 +459,7 @@ int disco_default_opts(disco_opts* o) {
     o->device = 0;
     o->stream = nullptr;
     o->host_threads = 0;
+    o->split_max_segments = 8;
     return DISCO_OK;
 }
 
@@ -469,13 +547,20 @@ int disco_candidates(const float* d, int32_t nvx, int32_t nvy, int32_t k, const 
     return DISCO_OK;
 }
 
-int disco_build(const disco_mesh* X, const disco_mesh* Y, const float* d, const uint8_t* allowed, const disco_opts* opts,
-                disco_handle** out) {
-    if (!X || !Y || !d || !out || !X->T || !Y->T) return fail(DISCO_ERR_INVALID_ARG, "build: null argument");
+}  // extern "C"
+
+namespace {
+
+// Builds a handle over n instances (host compiler per instance, one device store).
+int build_handle(int32_t n, const disco_mesh* X, const disco_mesh* Y, const float* const* d,
+                 const uint8_t* const* allowed, const disco_opts* opts, disco_handle** out) {
+    if (!out || n < 1 || !X || !Y || !d) return fail(DISCO_ERR_INVALID_ARG, "build: null argument");
     *out = nullptr;
+    for (int32_t i = 0; i < n; ++i)
+        if (!X[i].T || !Y[i].T || !d[i]) return fail(DISCO_ERR_INVALID_ARG, "build: null mesh or cost array");
     disco_opts o;
     if (opts) o = *opts; else disco_default_opts(&o);
-    if (!(o.omega > 0.0f && o.omega <= 1.0f) || o.split_chunk < 0 || o.lb_every < 1)
+    if (!(o.omega > 0.0f && o.omega <= 1.0f) || o.split_chunk < 0 || o.split_max_segments < 0 || o.lb_every < 1)
         return fail(DISCO_ERR_INVALID_ARG, "build: bad options");
     std::unique_ptr<disco_handle> h(new disco_handle());
     h->device = o.device;
@@ -487,16 +572,31 @@ int disco_build(const disco_mesh* X, const disco_mesh* Y, const float* d, const 
         CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
         h->own_stream = true;
     }
-    const size_t npair = size_t(X->nv) * size_t(Y->nv);
-    std::vector<float> hd;
-    std::vector<uint8_t> ha;
+    // costs and masks on the host (they may be device arrays)
+    std::vector<std::vector<float>> hd(n);
+    std::vector<std::vector<uint8_t>> ha(n);
     int rc;
-    if ((rc = to_host(d, npair, &hd))) return rc;
-    if (allowed && (rc = to_host(allowed, npair, &ha))) return rc;
-    std::string err;
-    rc = build_plan(MeshIn{X->nv, X->nt, X->T}, MeshIn{Y->nv, Y->nt, Y->T}, hd.data(), allowed ? ha.data() : nullptr,
-                    o.split_chunk, o.host_threads, &h->plan, &err);
-    if (rc) return fail(rc, "build: " + err);
+    for (int32_t i = 0; i < n; ++i) {
+        const size_t npair = size_t(X[i].nv) * size_t(Y[i].nv);
+        if ((rc = to_host(d[i], npair, &hd[i]))) return rc;
+        if (allowed && allowed[i] && (rc = to_host(allowed[i], npair, &ha[i]))) return rc;
+    }
+    // one instance uses every host thread; several instances are compiled side by side
+    const int hw = host_threads(o);
+    const int outer = std::max(1, std::min<int>(n, hw));
+    const int inner = std::max(1, hw / outer);
+    h->plans.resize(size_t(n));
+    std::vector<int> rcs(n, DISCO_OK);
+    std::vector<std::string> errs(n);
+    parallel_chunks(n, outer, [&](int, int64_t i0, int64_t i1) {
+        for (int64_t i = i0; i < i1; ++i)
+            rcs[i] = build_plan(MeshIn{X[i].nv, X[i].nt, X[i].T}, MeshIn{Y[i].nv, Y[i].nt, Y[i].T}, hd[i].data(),
+                                (allowed && allowed[i]) ? ha[i].data() : nullptr, o.split_chunk, o.split_max_segments,
+                                inner, &h->plans[i],
+                                &errs[i]);
+    });
+    for (int32_t i = 0; i < n; ++i)
+        if (rcs[i]) return fail(rcs[i], "build: instance " + std::to_string(i) + ": " + errs[i]);
     const auto tu = std::chrono::steady_clock::now();
     if ((rc = upload(h.get()))) return rc;
     h->upload_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tu).count();
@@ -505,14 +605,72 @@ int disco_build(const disco_mesh* X, const disco_mesh* Y, const float* d, const 
     return DISCO_OK;
 }
 
+void fill_info(const Plan& P, disco_info_t* info) {
+    info->nvars += P.nvars;
+    info->nrows += P.nrows;
+    info->nvars_free += P.n_free;
+    info->nvars_aux += P.n_aux;
+    info->nbdds += int64_t(P.segs.size());
+    info->nslots += int64_t(P.slot_var.size());
+    info->nnodes += P.n_nodes;
+    info->max_layers = std::max<int64_t>(info->max_layers, P.max_layers);
+    info->max_width = std::max<int64_t>(info->max_width, P.max_width);
+    info->constant += P.constant;
+    info->build_ms = std::max(info->build_ms, P.build_ms);
+}
+
+}  // namespace
+
+extern "C" {
+
+int disco_build(const disco_mesh* X, const disco_mesh* Y, const float* d, const uint8_t* allowed, const disco_opts* opts,
+                disco_handle** out) {
+    if (!X || !Y || !d) return fail(DISCO_ERR_INVALID_ARG, "build: null argument");
+    const float* dd[1] = {d};
+    const uint8_t* aa[1] = {allowed};
+    return build_handle(1, X, Y, dd, aa, opts, out);
+}
+
+int disco_build_batch(int32_t n, const disco_mesh* X, const disco_mesh* Y, const float* const* d,
+                      const uint8_t* const* allowed, const disco_opts* opts, disco_handle** out) {
+    return build_handle(n, X, Y, d, allowed, opts, out);
+}
+
+int disco_batch_size(disco_handle* h, int32_t* n) {
+    if (!h || !n) return fail(DISCO_ERR_INVALID_ARG, "batch_size: null argument");
+    *n = int32_t(h->n_inst());
+    return DISCO_OK;
+}
+
+int disco_lower_bounds(disco_handle* h, double* lb, int32_t n) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!lb || n < h->n_inst()) return fail(DISCO_ERR_INVALID_ARG, "lower_bounds: output too small");
+    if ((rc = lower_bounds(h))) return rc;
+    for (int64_t i = 0; i < h->n_inst(); ++i) lb[i] = h->h_scalar[i];
+    return DISCO_OK;
+}
+
+int disco_instance_info(disco_handle* h, int32_t i, disco_info_t* info) {
+    if (!h || !info || i < 0 || i >= h->n_inst()) return fail(DISCO_ERR_INVALID_ARG, "instance_info: bad argument");
+    std::memset(info, 0, sizeof(*info));
+    const Plan& P = h->plans[i];
+    fill_info(P, info);
+    info->ntiles = h->inst_tile_ptr[i + 1] - h->inst_tile_ptr[i];
+    info->iterations = h->iterations;
+    info->bytes_per_iter = 2 * (8 * P.n_nodes + 20 * info->nslots + 8 * (P.n_free + P.n_aux));
+    return DISCO_OK;
+}
+
 int disco_compile_host(const disco_mesh* X, const disco_mesh* Y, const float* d, const uint8_t* allowed,
-                       int32_t split_chunk, disco_info_t* info, int32_t* slot_var, int32_t* slot_width, int64_t nslots,
-                       int8_t* fixed, int64_t nvars) {
-    if (!X || !Y || !d || !info || !X->T || !Y->T || split_chunk < 0)
+                       int32_t split_chunk, int32_t split_max_segments, disco_info_t* info, int32_t* slot_var,
+                       int32_t* slot_width, int64_t nslots, int8_t* fixed, int64_t nvars) {
+    if (!X || !Y || !d || !info || !X->T || !Y->T || split_chunk < 0 || split_max_segments < 0)
         return fail(DISCO_ERR_INVALID_ARG, "compile_host: bad arguments");
     Plan P;
     std::string err;
-    int rc = build_plan(MeshIn{X->nv, X->nt, X->T}, MeshIn{Y->nv, Y->nt, Y->T}, d, allowed, split_chunk, 0, &P, &err);
+    int rc = build_plan(MeshIn{X->nv, X->nt, X->T}, MeshIn{Y->nv, Y->nt, Y->T}, d, allowed, split_chunk,
+                        split_max_segments, 0, &P, &err);
     if (rc) return fail(rc, "compile_host: " + err);
     std::memset(info, 0, sizeof(*info));
     info->nvars = P.nvars;
@@ -580,7 +738,7 @@ int disco_converge(disco_handle* h, int32_t max_iters, int32_t* iters_done, doub
 int disco_min_marginals(disco_handle* h, float* out, int64_t n) {
     int rc = check_handle(h);
     if (rc) return rc;
-    const int64_t ns = int64_t(h->plan.slot_var.size());
+    const int64_t ns = h->nslots();
     if (!out || n < ns) return fail(DISCO_ERR_INVALID_ARG, "min_marginals: output too small");
     if ((rc = h->pass(Pass::FwdMM))) return rc;
     if ((rc = h->pass(Pass::BwdMM))) return rc;
@@ -591,7 +749,7 @@ int disco_min_marginals(disco_handle* h, float* out, int64_t n) {
 int disco_get_state(disco_handle* h, float* lam, int64_t n, float* pend, int64_t n_pend) {
     int rc = check_handle(h);
     if (rc) return rc;
-    const int64_t ns = int64_t(h->plan.slot_var.size());
+    const int64_t ns = h->nslots();
     if (!lam || n < ns || (pend && n_pend < h->nint)) return fail(DISCO_ERR_INVALID_ARG, "get_state: output too small");
     CK(launch_gather_f32(h->lam, h->canon_pos, ns, h->tmp, h->stream));
     if ((rc = write_out(lam, h->tmp, size_t(ns) * 4, h->stream))) return rc;
@@ -605,7 +763,7 @@ int disco_get_state(disco_handle* h, float* lam, int64_t n, float* pend, int64_t
 int disco_set_state(disco_handle* h, const float* lam, int64_t n, const float* pend, int64_t n_pend) {
     int rc = check_handle(h);
     if (rc) return rc;
-    const int64_t ns = int64_t(h->plan.slot_var.size());
+    const int64_t ns = h->nslots();
     if (!lam || n < ns || (pend && n_pend < h->nint)) return fail(DISCO_ERR_INVALID_ARG, "set_state: input too small");
     CK(cudaMemcpyAsync(h->tmp, lam, size_t(ns) * 4, cudaMemcpyDefault, h->stream));
     CK(launch_scatter_f32(h->tmp, h->canon_pos, ns, h->lam, h->stream));
@@ -621,64 +779,13 @@ int disco_set_state(disco_handle* h, const float* lam, int64_t n, const float* p
     return DISCO_OK;
 }
 
-int disco_primal(disco_handle* h, uint8_t* x_out, int64_t nvars, double* cost) {
-    int rc = check_handle(h);
-    if (rc) return rc;
-    const Plan& P = h->plan;
-    if (!x_out || nvars < P.nvars) return fail(DISCO_ERR_INVALID_ARG, "primal: output too small");
-    const disco_opts& o = h->opts;
-    cudaStream_t s = h->stream;
-    const int64_t nint = h->nint;
-    CK(cudaMemsetAsync(h->state, 0, size_t(nint), s));
-    float delta = o.perturb_delta0;
-    bool done = nint == 0;
-    for (int r = 0; r < o.primal_rounds && !done; ++r) {
-        // 1. lambda <- lambda + pend; min-marginals under the fixings
-        CK(launch_flush(h->var, h->desc, h->nslots_tile, h->acc[h->cur], h->lam, h->lam_lo, s));
-        CK(cudaMemsetAsync(h->acc[0], 0, size_t(nint) * kAccStride * 4, s));
-        CK(cudaMemsetAsync(h->acc[1], 0, size_t(nint) * kAccStride * 4, s));
-        if ((rc = h->pass(Pass::FwdMM))) return rc;
-        if ((rc = h->pass(Pass::BwdMM))) return rc;
-        // 2. agreement: every slot strictly positive -> 0, strictly negative -> 1
-        CK(launch_decide(h->mm_var, h->deg, h->state, nint, o.tie_tau, h->trial, s));
-        // 3. propagate the trial fixings to a fixpoint
-        bool conflict = false;
-        int sweeps = 0;
-        for (;;) {
-            CK(cudaMemsetAsync(h->counters, 0, 4 * sizeof(int), s));
-            uint8_t* keep = h->state;
-            h->state = h->trial;  // the support pass reads the trial fixings
-            rc = h->pass(Pass::Supports);
-            h->state = keep;
-            if (rc) return rc;
-            CK(launch_apply(h->sup, h->deg, nint, h->trial, h->counters, s));
-            CK(cudaMemcpyAsync(h->h_counters, h->counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            if (h->h_counters[1] > 0) { conflict = true; break; }
-            if (h->h_counters[0] == 0) break;
-            if (++sweeps > o.propagate_limit) return fail(DISCO_ERR_TIMEOUT, "primal: propagation did not settle");
-        }
-        if (!conflict) {
-            CK(cudaMemcpyAsync(h->state, h->trial, size_t(nint), cudaMemcpyDeviceToDevice, s));
-            if (h->h_counters[2] == 0) { done = true; break; }
-        }
-        // 4. push undecided variables towards their majority, then continue the dual
-        CK(launch_perturb(h->var, h->desc, h->nslots_tile, h->mm_var, h->state, delta, h->lam, h->lam_lo, s));
-        delta *= o.perturb_growth;
-        if ((rc = h->pass(Pass::BwdReset))) return rc;
-        for (int t = 0; t < o.primal_inner_iters; ++t) {
-            if ((rc = h->pass(Pass::FwdMMARound))) return rc;
-            if ((rc = h->pass(Pass::BwdMMARound))) return rc;
-        }
-    }
-    // read x back: presolve values, then the rounded internal variables
-    std::vector<uint8_t> st(static_cast<size_t>(nint), uint8_t(0));
-    if (nint) {
-        CK(cudaMemcpyAsync(st.data(), h->state, size_t(nint), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-    }
-    const int nth = host_threads(o);
-    std::vector<uint8_t> x(static_cast<size_t>(P.nvars), uint8_t(0));
+}  // extern "C"
+
+namespace {
+
+// x of one instance from its presolve values and the rounded internal variables; exact check
+// of A x = b and the cost (a fixed-order sum of per-chunk sums). Returns feasibility.
+bool assemble_instance(const Plan& P, const uint8_t* st, int nth, uint8_t* x, double* cost) {
     parallel_chunks(P.nvars, nth, [&](int, int64_t lo, int64_t hi) {
         for (int64_t i = lo; i < hi; ++i) x[i] = P.fixed[i] == 1 ? 1 : 0;
     });
@@ -689,11 +796,7 @@ int disco_primal(disco_handle* h, uint8_t* x_out, int64_t nvars, double* cost) {
             if (st[v] == kFree) undecided[c] = 1;
         }
     });
-    bool all = std::find(undecided.begin(), undecided.end(), uint8_t(1)) == undecided.end();
-    // the dual continues from an unrestricted state
-    CK(cudaMemsetAsync(h->state, 0, size_t(nint), s));
-    h->has_b = false;
-    // exact check of A x = b; cost as a fixed-order sum of per-chunk sums
+    const bool all = std::find(undecided.begin(), undecided.end(), uint8_t(1)) == undecided.end();
     const int nck = 64;
     std::vector<uint8_t> violated(nck, 0);
     std::vector<double> part(nck, 0.0);
@@ -709,35 +812,143 @@ int disco_primal(disco_handle* h, uint8_t* x_out, int64_t nvars, double* cost) {
             part[c] = s;
         }
     });
-    const bool feasible = all && std::find(violated.begin(), violated.end(), uint8_t(1)) == violated.end();
     double c = 0.0;
-    for (double s : part) c += s;
-    if (cost) *cost = c;
+    for (double q : part) c += q;
+    *cost = c;
+    return all && std::find(violated.begin(), violated.end(), uint8_t(1)) == violated.end();
+}
+
+// Rounding of every instance of the handle at once (the fixings of one instance never touch
+// another's BDDs); x_out holds the instances' elements one after another.
+int primal_all(disco_handle* h, uint8_t* x_out, double* costs, int32_t* status) {
+    const disco_opts& o = h->opts;
+    cudaStream_t s = h->stream;
+    const int64_t nint = h->nint;
+    int rc;
+    CK(cudaMemsetAsync(h->state, 0, size_t(nint), s));
+    float delta = o.perturb_delta0;
+    bool done = nint == 0;
+    for (int r = 0; r < o.primal_rounds && !done; ++r) {
+        // 1. lambda <- lambda + pend; min-marginals under the fixings
+        CK(launch_flush(h->var, h->desc, h->nslots_tile, h->acc[h->cur], h->lam, h->lam_lo, s));
+        CK(cudaMemsetAsync(h->acc[0], 0, size_t(nint) * kAccStride * 4, s));
+        CK(cudaMemsetAsync(h->acc[1], 0, size_t(nint) * kAccStride * 4, s));
+        if ((rc = h->pass(Pass::FwdMM))) return rc;
+        if ((rc = h->pass(Pass::BwdMM))) return rc;
+        // 2. agreement: every slot strictly positive -> 0, strictly negative -> 1
+        CK(launch_decide(h->mm_var, h->deg, h->state, nint, o.tie_tau, h->trial, s));
+        // 3. propagate the trial fixings to a fixpoint; an instance whose trial runs into a
+        //    conflict keeps its fixings of the previous round (other instances go on)
+        const int64_t ni = h->n_inst();
+        std::vector<uint8_t> reverted(static_cast<size_t>(ni), 0);
+        int sweeps = 0;
+        for (;;) {
+            CK(cudaMemsetAsync(h->counters, 0, size_t(4 * ni) * sizeof(int), s));
+            uint8_t* keep = h->state;
+            h->state = h->trial;  // the support pass reads the trial fixings
+            rc = h->pass(Pass::Supports);
+            h->state = keep;
+            if (rc) return rc;
+            CK(launch_apply(h->sup, h->deg, h->var_inst, nint, h->trial, h->counters, s));
+            CK(cudaMemcpyAsync(h->h_counters, h->counters, size_t(4 * ni) * sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            bool changed = false;
+            for (int64_t i = 0; i < ni; ++i) {
+                if (reverted[i]) continue;
+                if (h->h_counters[4 * i + 1] > 0) {
+                    reverted[i] = 1;
+                    const int64_t v0 = h->var_base[i], v1 = h->var_base[i + 1];
+                    CK(cudaMemcpyAsync(h->trial + v0, h->state + v0, size_t(v1 - v0), cudaMemcpyDeviceToDevice, s));
+                } else if (h->h_counters[4 * i] > 0) {
+                    changed = true;
+                }
+            }
+            if (!changed) break;
+            if (++sweeps > o.propagate_limit) return fail(DISCO_ERR_TIMEOUT, "primal: propagation did not settle");
+        }
+        CK(cudaMemcpyAsync(h->state, h->trial, size_t(nint), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(h->counters, 0, size_t(4 * ni) * sizeof(int), s));
+        CK(launch_count_free(h->state, h->deg, h->var_inst, nint, h->counters, s));
+        CK(cudaMemcpyAsync(h->h_counters, h->counters, size_t(4 * ni) * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        int64_t left = 0;
+        for (int64_t i = 0; i < ni; ++i) left += h->h_counters[4 * i + 2];
+        if (left == 0) { done = true; break; }
+        // 4. push undecided variables towards their majority, then continue the dual
+        CK(launch_perturb(h->var, h->desc, h->nslots_tile, h->mm_var, h->state, delta, h->lam, h->lam_lo, s));
+        delta *= o.perturb_growth;
+        if ((rc = h->pass(Pass::BwdReset))) return rc;
+        for (int t = 0; t < o.primal_inner_iters; ++t) {
+            if ((rc = h->pass(Pass::FwdMMARound))) return rc;
+            if ((rc = h->pass(Pass::BwdMMARound))) return rc;
+        }
+    }
+    // read the fixings back
+    std::vector<uint8_t> st(static_cast<size_t>(nint), uint8_t(0));
+    if (nint) {
+        CK(cudaMemcpyAsync(st.data(), h->state, size_t(nint), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    // the dual continues from an unrestricted state
+    CK(cudaMemsetAsync(h->state, 0, size_t(nint), s));
+    h->has_b = false;
+    const int64_t ni = h->n_inst();
+    const int hw = host_threads(o);
+    const int outer = std::max(1, std::min<int>(int(ni), hw));
+    std::vector<uint8_t> x(static_cast<size_t>(h->nelems()), uint8_t(0));
+    std::vector<uint8_t> ok(static_cast<size_t>(ni), 0);
+    std::vector<double> cs(static_cast<size_t>(ni), 0.0);
+    parallel_chunks(ni, outer, [&](int, int64_t i0, int64_t i1) {
+        for (int64_t i = i0; i < i1; ++i)
+            ok[i] = assemble_instance(h->plans[i], st.data() + h->var_base[i], std::max(1, hw / outer),
+                                      x.data() + h->elem_base[i], &cs[i]);
+    });
+    bool all = true;
+    for (int64_t i = 0; i < ni; ++i) {
+        if (costs) costs[i] = cs[i];
+        if (status) status[i] = ok[i] ? DISCO_OK : DISCO_ERR_PRIMAL_FAILED;
+        all = all && ok[i];
+    }
     if ((rc = write_out(x_out, x.data(), x.size(), s))) return rc;
-    return feasible ? DISCO_OK : fail(DISCO_ERR_PRIMAL_FAILED, "primal: no feasible assignment within the round limit");
+    return all ? DISCO_OK : fail(DISCO_ERR_PRIMAL_FAILED, "primal: no feasible assignment within the round limit");
+}
+
+}  // namespace
+
+extern "C" {
+
+int disco_primal(disco_handle* h, uint8_t* x_out, int64_t nvars, double* cost) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!x_out || nvars < h->nelems()) return fail(DISCO_ERR_INVALID_ARG, "primal: output too small");
+    std::vector<double> cs(static_cast<size_t>(h->n_inst()), 0.0);
+    rc = primal_all(h, x_out, cs.data(), nullptr);
+    if (cost) {
+        double c = 0.0;
+        for (double q : cs) c += q;
+        *cost = c;
+    }
+    return rc;
+}
+
+int disco_primal_batch(disco_handle* h, uint8_t* x_out, int64_t nvars, double* costs, int32_t* status, int32_t n) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!x_out || nvars < h->nelems() || n < h->n_inst())
+        return fail(DISCO_ERR_INVALID_ARG, "primal_batch: output too small");
+    return primal_all(h, x_out, costs, status);
 }
 
 int disco_info(disco_handle* h, disco_info_t* info) {
     if (!h || !info) return fail(DISCO_ERR_INVALID_ARG, "info: null argument");
     std::memset(info, 0, sizeof(*info));
-    const Plan& P = h->plan;
-    info->nvars = P.nvars;
-    info->nrows = P.nrows;
-    info->nvars_free = P.n_free;
-    info->nvars_aux = P.n_aux;
-    info->nbdds = int64_t(P.segs.size());
-    info->nslots = int64_t(P.slot_var.size());
-    info->nnodes = P.n_nodes;
-    info->max_layers = P.max_layers;
-    info->max_width = P.max_width;
+    for (const Plan& P : h->plans) fill_info(P, info);
     info->ntiles = h->ntiles;
     info->device_bytes = h->device_bytes;
     info->iterations = h->iterations;
-    info->constant = P.constant;
-    info->build_ms = P.build_ms;
     info->upload_ms = h->upload_ms;
     // per iteration: 8 B per node and 20 B per slot per half-pass, 8 B per variable for the averaging
-    info->bytes_per_iter = 2 * (8 * P.n_nodes + 20 * info->nslots + 8 * (P.n_free + P.n_aux));
+    info->bytes_per_iter = 2 * (8 * info->nnodes + 20 * info->nslots + 8 * (info->nvars_free + info->nvars_aux));
     return DISCO_OK;
 }
 

@@ -16,7 +16,9 @@
 // per product edge, +1 for an element crossing it from its lexicographically smaller
 // product vertex (m, n), -1 otherwise; presolve fixes every variable some row forces
 // (generalised arc consistency to a fixpoint); c_p = mean of the three pair costs,
-// normalised by the largest kept c_p; segments are balanced (cut at floor(s n / S)).
+// normalised by the largest kept c_p; segments are balanced (cut at floor(s n / S)) with
+// S = min(ceil(n / chunk), the segment cap): a one-hot chain carries cost information across
+// one cut per half-pass, so very long rows stay in few segments.
 //
 // For a +-1 row with residual right-hand side r, the nodes of layer l are the partial sums
 // sigma of the first l variables that are reachable from 0 and from which r is reachable:
@@ -343,7 +345,7 @@ struct Trace {
 }  // namespace
 
 int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8_t* mask, int split_chunk,
-               int threads, Plan* P, std::string* err) {
+               int split_max_segments, int threads, Plan* P, std::string* err) {
     auto t0 = std::chrono::steady_clock::now();
     Trace tr;
     if (threads <= 0) threads = std::max(1u, std::thread::hardware_concurrency());
@@ -738,7 +740,8 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                     if (l < n) (fc[l] > 0 ? ppre : qpre)++;
                 }
                 if (C.rc) break;
-                const int nseg = (split_chunk > 0 && n > split_chunk) ? (n + split_chunk - 1) / split_chunk : 1;
+                int nseg = (split_chunk > 0 && n > split_chunk) ? (n + split_chunk - 1) / split_chunk : 1;
+                if (split_max_segments > 0) nseg = std::min(nseg, split_max_segments);
                 std::vector<int64_t> cut_aux(size_t(nseg) + 1, -1);  // local id of y_1 of the cut before segment s
                 for (int s = 1; s < nseg; ++s) {
                     const int b = int(int64_t(s) * n / nseg);

@@ -91,12 +91,15 @@ __device__ __forceinline__ df df_add_f(df a, float b) {
     two_sum(a.hi, b, s, e);
     return fast2sum(s, e + a.lo);
 }
-// a / n for a small positive integer n: the remainder a.hi - q n is exact with an FMA.
+// a / n for a small positive integer n. q = a.hi * (1/n) is within an ulp of a.hi / n, so the
+// remainder a.hi - q n is exact with an FMA (the classic division-by-reciprocal argument);
+// the low part needs only single precision.
 __device__ __forceinline__ df df_div_i(df a, int n) {
     const float fn = float(n);
-    const float q = a.hi / fn;
+    const float rcp = n == 2 ? 0.5f : (n == 3 ? 0.333333343f : (n == 4 ? 0.25f : (n == 5 ? 0.2f : 1.0f / fn)));
+    const float q = a.hi * rcp;
     const float r = fmaf(-q, fn, a.hi) + a.lo;
-    return fast2sum(q, r / fn);
+    return fast2sum(q, r * rcp);
 }
 
 // Deferred mean of variable v: sum of its deg removed masses (rank order) / deg, in df.
@@ -119,56 +122,87 @@ __device__ __forceinline__ uint64_t shl(uint64_t x, int k) { return k >= 0 ? (x 
 __device__ __forceinline__ uint64_t low_mask(int n) { return n >= 64 ? ~0ull : ((1ull << n) - 1ull); }
 
 // ---------------------------------------------------------------------------------------
-// Inputs of one layer of one lane, loaded ahead of their use. A lane's layers form a
-// sequential recurrence only through the node costs it keeps in registers; every load
-// (variable, descriptor, lambda, the averaging sector, the other direction's node costs) is
-// independent of it, so the kernels keep a ring of kDepth layers in flight: descriptors are
-// fetched 2 * kDepth layers ahead, the loads that need the variable id kDepth layers ahead.
-template <int W>
-struct Layer {
-    uint32_t v, desc;
-    float lam, lo;
-    float4 acc;   // acc_in[v * 8 + 0..3]
-    float acc4;   // acc_in[v * 8 + 4] (variables in five BDDs)
-    uint8_t st;
-    float nb[W];  // forward: B of the next layer; backward: F of this layer
-};
+// Inputs of one layer of one lane are staged in shared memory ahead of their use. A lane's
+// layers form a sequential recurrence only through the node costs it keeps in registers;
+// every load (lambda, its low part, the variable's averaging sector, the other direction's
+// node costs) is independent of it. Each lane therefore keeps kRing layers in flight with
+// asynchronous copies (cp.async, one commit group per layer) into its own slots of a
+// per-warp ring; descriptors and variable ids are fetched kRing layers before the copies
+// that need them. Lanes only ever read their own slots, so no warp synchronisation is needed.
+constexpr int kRing = 3;
 
+// Stage layout (floats, per warp): lam[32] lo[32] acc4[32] acc[32][4] nodes[W][32].
 template <int W>
-__host__ __device__ constexpr int depth() { return W <= 2 ? 4 : (W <= 4 ? 3 : 2); }
+__host__ __device__ constexpr int stage_floats() { return (7 + W) * 32; }
+template <int W>
+__host__ __device__ constexpr int ring_floats() { return kRing * stage_floats<W>(); }
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ void load_head(const KArgs& a, int64_t si, bool ok, uint32_t& v, uint32_t& d) {
     v = ok ? __ldg(a.var + si) : kNoVar;
     d = ok ? __ldg(a.desc + si) : 0u;
 }
 
-// NODES: 0 none, 1 = B of layer l + 1 (count wn), 2 = F of layer l (count w)
-template <int W, bool ROUND, int NODES>
-__device__ __forceinline__ void load_body(const KArgs& a, int64_t si, const float* node_row, uint32_t v, uint32_t dsc,
-                                          Layer<W>& L) {
-    L.v = v;
-    L.desc = dsc;
-    if (v == kNoVar) return;
-    L.lam = a.lam[si];
-    L.lo = a.lam_lo[si];
-    const float* ap = a.acc_in + size_t(v) * kAccStride;
-    L.acc = __ldg(reinterpret_cast<const float4*>(ap));
-    const int deg = int((dsc >> 25) & 7u);
-    L.acc4 = deg > 4 ? __ldg(ap + 4) : 0.0f;
-    L.st = ROUND ? __ldg(a.state + v) : kFree;
-    if (NODES) {
-        const int n = NODES == 1 ? int((dsc >> 6) & 63u) + 1 : int(dsc & 63u) + 1;
+// Copies of one layer's inputs into stage `st` (this lane's slots), then one commit.
+// NODES: 0 none, 1 = B of layer l + 1 (count wn), 2 = F of layer l (count w).
+template <int W, int NODES>
+__device__ __forceinline__ void stage_issue(const KArgs& a, float* st, int lane, int64_t si, const float* node_row,
+                                            uint32_t v, uint32_t dsc) {
+    if (v != kNoVar) {
+        cp_async4(st + lane, a.lam + si);
+        cp_async4(st + 32 + lane, a.lam_lo + si);
+        const float* ap = a.acc_in + size_t(v) * kAccStride;
+        cp_async16(st + 96 + 4 * lane, ap);
+        if (int((dsc >> 25) & 7u) > 4) cp_async4(st + 64 + lane, ap + 4);
+        if (NODES) {
+            const int n = NODES == 1 ? int((dsc >> 6) & 63u) + 1 : int(dsc & 63u) + 1;
 #pragma unroll
-        for (int s = 0; s < W; ++s) L.nb[s] = s < n ? __ldg(node_row + s * 32) : BIG;
+            for (int s = 0; s < W; ++s)
+                if (s < n) cp_async4(st + (7 + s) * 32 + lane, node_row + s * 32);
+        }
+    }
+    cp_commit();
+}
+
+// The staged inputs of one layer, read back into registers.
+template <int W>
+struct Staged {
+    float lam, lo;
+    float4 acc;
+    float acc4;
+    float nb[W];
+};
+
+template <int W, int NODES>
+__device__ __forceinline__ void stage_read(const float* st, int lane, const Desc& d, Staged<W>& x) {
+    x.lam = st[lane];
+    x.lo = st[32 + lane];
+    x.acc = *reinterpret_cast<const float4*>(st + 96 + 4 * lane);
+    x.acc4 = d.deg > 4 ? st[64 + lane] : 0.0f;
+    if (NODES) {
+        const int n = NODES == 1 ? d.wn : d.w;
+#pragma unroll
+        for (int s = 0; s < W; ++s) x.nb[s] = s < n ? st[(7 + s) * 32 + lane] : BIG;
     }
 }
 
 template <int W>
-__device__ __forceinline__ df pend_layer(const Layer<W>& L, int deg) {
-    df s = df_add_f(df{L.acc.x, 0.0f}, L.acc.y);
-    if (deg > 2) s = df_add_f(s, L.acc.z);
-    if (deg > 3) s = df_add_f(s, L.acc.w);
-    if (deg > 4) s = df_add_f(s, L.acc4);
+__device__ __forceinline__ df pend_staged(const Staged<W>& x, int deg) {
+    df s = df_add_f(df{x.acc.x, 0.0f}, x.acc.y);
+    if (deg > 2) s = df_add_f(s, x.acc.z);
+    if (deg > 3) s = df_add_f(s, x.acc.w);
+    if (deg > 4) s = df_add_f(s, x.acc4);
     return df_div_i(s, deg);
 }
 
@@ -177,11 +211,13 @@ __device__ __forceinline__ df pend_layer(const Layer<W>& L, int deg) {
 //   MODE 0: MMA update, store F.       MODE 1: MMA update under fixings, store F.
 //   MODE 2: lower bound (no store).    MODE 3: plain min-sum under fixings, store F.
 template <int W, int MODE>
-__device__ __forceinline__ void forward_tile(const KArgs& a, const int tile, const TileInfo& ti) {
+__device__ __forceinline__ void forward_tile(const KArgs& a, const int tile, const TileInfo& ti, float* ring) {
     constexpr bool kUpdate = MODE <= 1;
     constexpr bool kRound = MODE == 1 || MODE == 3;
     constexpr bool kStoreF = MODE != 2;
-    constexpr int P = depth<W>();
+    constexpr int NODES = kUpdate ? 1 : 0;
+    constexpr int P = kRing;
+    constexpr int SF = stage_floats<W>();
     const int lane = threadIdx.x & 31;
     const int64_t sb = ti.slot_base + lane;
     const float* Bl = a.B + ti.node_base + lane;  // B of layer l at Bl + l * W * 32
@@ -190,32 +226,30 @@ __device__ __forceinline__ void forward_tile(const KArgs& a, const int tile, con
     float f[W];
 #pragma unroll
     for (int s = 0; s < W; ++s) f[s] = s == 0 ? 0.0f : BIG;
-    Layer<W> ring[P];
-    uint32_t hv[P], hd[P];
+    uint32_t cv[P], cd[P], hv[P], hd[P];  // descriptors of layers l (staged) and l + P (next to stage)
 #pragma unroll
     for (int k = 0; k < P; ++k) {
-        uint32_t v, d;
-        load_head(a, sb + int64_t(k) * 32, k < L, v, d);
-        load_body<W, kRound, kUpdate ? 1 : 0>(a, sb + int64_t(k) * 32, Bl + int64_t(k + 1) * W * 32, v, d, ring[k]);
+        load_head(a, sb + int64_t(k) * 32, k < L, cv[k], cd[k]);
+        stage_issue<W, NODES>(a, ring + k * SF, lane, sb + int64_t(k) * 32, Bl + int64_t(k + 1) * W * 32, cv[k], cd[k]);
         load_head(a, sb + int64_t(k + P) * 32, k + P < L, hv[k], hd[k]);
     }
     for (int l0 = 0; l0 < L; l0 += P) {
 #pragma unroll
         for (int k = 0; k < P; ++k) {
             const int l = l0 + k;
-            if (ring[k].v == kNoVar) goto done;
-            // issue the loads of layer l + P and the descriptor of layer l + 2P first
-            Layer<W> nxt;
-            load_body<W, kRound, kUpdate ? 1 : 0>(a, sb + int64_t(l + P) * 32, Bl + int64_t(l + P + 1) * W * 32, hv[k],
-                                                  hd[k], nxt);
+            const uint32_t v = cv[k];
+            if (v == kNoVar) goto done;
+            cp_wait<P - 1>();
+            const Desc d = decode(cd[k]);
+            Staged<W> c;
+            stage_read<W, NODES>(ring + k * SF, lane, d, c);
             uint32_t nv, nd;
             load_head(a, sb + int64_t(l + 2 * P) * 32, l + 2 * P < L, nv, nd);
-            const Layer<W>& c = ring[k];
             const int64_t si = sb + int64_t(l) * 32;
-            const Desc d = decode(c.desc);
-            const df p = pend_layer(c, d.deg);
+            const df p = pend_staged(c, d.deg);
             df Lm{c.lam, c.lo};
-            const bool al0 = c.st != kFix1, al1 = c.st != kFix0;
+            const uint8_t st = kRound ? __ldg(a.state + v) : kFree;
+            const bool al0 = st != kFix1, al1 = st != kFix0;
             float lm = Lm.hi;
             if (kStoreF) {
                 float* Fr = Fl + int64_t(l) * W * 32;
@@ -225,7 +259,7 @@ __device__ __forceinline__ void forward_tile(const KArgs& a, const int tile, con
             }
             if (kUpdate) {
                 float removed = 0.0f;
-                if (c.st == kFree) {
+                if (st == kFree) {
                     Lm = df_add(Lm, p);
                     // hx[s + 1] = b of node s's 0-child, hx[s + 1 + a] = b of its arithmetic 1-child
                     float hx[W + 2];
@@ -247,7 +281,7 @@ __device__ __forceinline__ void forward_tile(const KArgs& a, const int tile, con
                     a.lam_lo[si] = Lm.lo;
                     lm = Lm.hi;
                 }
-                a.acc_out[size_t(c.v) * kAccStride + d.rank] = removed;
+                a.acc_out[size_t(v) * kAccStride + d.rank] = removed;
             } else {
                 lm = df_add(Lm, p).hi;
             }
@@ -255,22 +289,25 @@ __device__ __forceinline__ void forward_tile(const KArgs& a, const int tile, con
             float gx[W + 2];
             shift_ext(f, -d.d0, gx);
             const bool upf = d.d1 > d.d0;
-            float fn[W];
+            const float f0 = f[0];  // a one-hot 1-arc leaves node 0 (read before f is overwritten)
 #pragma unroll
             for (int s = 0; s < W; ++s) {
                 const float v0 = al0 ? gx[s + 1] : BIG;
                 float v1 = BIG;
-                if (al1) v1 = (d.one ? (s == d.d1 ? f[0] : BIG) : (upf ? gx[s] : gx[s + 2])) + lm;
-                fn[s] = s < d.wn ? fminf(v0, v1) : BIG;
+                if (al1) v1 = (d.one ? (s == d.d1 ? f0 : BIG) : (upf ? gx[s] : gx[s + 2])) + lm;
+                f[s] = s < d.wn ? fminf(v0, v1) : BIG;
             }
-#pragma unroll
-            for (int s = 0; s < W; ++s) f[s] = fn[s];
-            ring[k] = nxt;
+            // stage layer l + P into the slot just consumed
+            stage_issue<W, NODES>(a, ring + k * SF, lane, sb + int64_t(l + P) * 32, Bl + int64_t(l + P + 1) * W * 32,
+                                  hv[k], hd[k]);
+            cv[k] = hv[k];
+            cd[k] = hd[k];
             hv[k] = nv;
             hd[k] = nd;
         }
     }
 done:
+    cp_wait<0>();
     if (MODE == 2) {
         double x = double(f[0]);  // cost of the cheapest root -> TOP path (0 for an empty lane)
 #pragma unroll
@@ -279,26 +316,29 @@ done:
     }
 }
 
-// One width class per launch.
+// One width class per launch; dynamic shared memory: kWarpsPerBlock rings of width W.
 template <int W, int MODE>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward(KArgs a) {
+    extern __shared__ float smem[];
     const int tile = a.tile0 + int(blockIdx.x) * kWarpsPerBlock + int(threadIdx.x >> 5);
     if (tile >= a.tile_end) return;
     const TileInfo ti = a.tiles[tile];
-    forward_tile<W, MODE>(a, tile, ti);
+    forward_tile<W, MODE>(a, tile, ti, smem + (threadIdx.x >> 5) * ring_floats<W>());
 }
 
 // Width classes 2, 4, 6 and 8 in one launch (tiles ordered longest first), so that short
-// tiles fill the SMs around the long ones.
+// tiles fill the SMs around the long ones; every warp's ring is sized for width 8.
 template <int MODE>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_fused(KArgs a) {
+    extern __shared__ float smem[];
     const int tile = a.tile0 + int(blockIdx.x) * kWarpsPerBlock + int(threadIdx.x >> 5);
     if (tile >= a.tile_end) return;
     const TileInfo ti = a.tiles[tile];
-    if (ti.W == 2) forward_tile<2, MODE>(a, tile, ti);
-    else if (ti.W == 4) forward_tile<4, MODE>(a, tile, ti);
-    else if (ti.W == 6) forward_tile<6, MODE>(a, tile, ti);
-    else forward_tile<8, MODE>(a, tile, ti);
+    float* ring = smem + (threadIdx.x >> 5) * ring_floats<8>();
+    if (ti.W == 2) forward_tile<2, MODE>(a, tile, ti, ring);
+    else if (ti.W == 4) forward_tile<4, MODE>(a, tile, ti, ring);
+    else if (ti.W == 6) forward_tile<6, MODE>(a, tile, ti, ring);
+    else forward_tile<8, MODE>(a, tile, ti, ring);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -306,12 +346,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_fused(KArgs a) 
 //   MODE 0: MMA update, store B.                 MODE 1: MMA update under fixings, store B.
 //   MODE 2: min-marginals under fixings (out).   MODE 3: plain min-sum under fixings, store B.
 template <int W, int MODE>
-__device__ __forceinline__ void backward_tile(const KArgs& a, const TileInfo& ti) {
+__device__ __forceinline__ void backward_tile(const KArgs& a, const TileInfo& ti, float* ring) {
     constexpr bool kUpdate = MODE <= 1;
     constexpr bool kRound = MODE >= 1;
     constexpr bool kStoreB = MODE != 2;
     constexpr bool kNeedF = MODE != 3;
-    constexpr int P = depth<W>();
+    constexpr int NODES = kNeedF ? 2 : 0;
+    constexpr int P = kRing;
+    constexpr int SF = stage_floats<W>();
     const int lane = threadIdx.x & 31;
     const int64_t sb = ti.slot_base + lane;
     const float* Fl = a.F + ti.node_base + lane;
@@ -320,14 +362,12 @@ __device__ __forceinline__ void backward_tile(const KArgs& a, const TileInfo& ti
     float bn[W];
 #pragma unroll
     for (int s = 0; s < W; ++s) bn[s] = s == 0 ? 0.0f : BIG;
-    Layer<W> ring[P];
-    uint32_t hv[P], hd[P];
+    uint32_t cv[P], cd[P], hv[P], hd[P];
 #pragma unroll
     for (int k = 0; k < P; ++k) {
         const int l = L - 1 - k;
-        uint32_t v, d;
-        load_head(a, sb + int64_t(l) * 32, l >= 0, v, d);
-        load_body<W, kRound, kNeedF ? 2 : 0>(a, sb + int64_t(l) * 32, Fl + int64_t(l) * W * 32, v, d, ring[k]);
+        load_head(a, sb + int64_t(l) * 32, l >= 0, cv[k], cd[k]);
+        stage_issue<W, NODES>(a, ring + k * SF, lane, sb + int64_t(l) * 32, Fl + int64_t(l) * W * 32, cv[k], cd[k]);
         load_head(a, sb + int64_t(l - P) * 32, l - P >= 0, hv[k], hd[k]);
     }
     for (int l0 = L - 1; l0 >= 0; l0 -= P) {
@@ -335,18 +375,19 @@ __device__ __forceinline__ void backward_tile(const KArgs& a, const TileInfo& ti
         for (int k = 0; k < P; ++k) {
             const int l = l0 - k;
             if (l < 0) goto done;
-            Layer<W> nxt;
-            load_body<W, kRound, kNeedF ? 2 : 0>(a, sb + int64_t(l - P) * 32, Fl + int64_t(l - P) * W * 32, hv[k], hd[k],
-                                                 nxt);
             uint32_t nv, nd;
             load_head(a, sb + int64_t(l - 2 * P) * 32, l - 2 * P >= 0, nv, nd);
-            const Layer<W>& c = ring[k];
-            if (c.v != kNoVar) {
+            const uint32_t v = cv[k];
+            if (v != kNoVar) {
+                cp_wait<P - 1>();
+                const Desc d = decode(cd[k]);
+                Staged<W> c;
+                stage_read<W, NODES>(ring + k * SF, lane, d, c);
                 const int64_t si = sb + int64_t(l) * 32;
-                const Desc d = decode(c.desc);
-                const df p = pend_layer(c, d.deg);
+                const df p = pend_staged(c, d.deg);
                 df Lm{c.lam, c.lo};
-                const bool al0 = c.st != kFix1, al1 = c.st != kFix0;
+                const uint8_t st = kRound ? __ldg(a.state + v) : kFree;
+                const bool al0 = st != kFix1, al1 = st != kFix0;
                 float lm = Lm.hi;
                 const float b1 = d.one ? at_dyn(bn, d.d1) : BIG;  // target of node 0's 1-arc (one-hot chains)
                 // hx[s + 1] = b of node s's 0-child, hx[s + 1 + a] = b of its arithmetic 1-child
@@ -367,7 +408,7 @@ __device__ __forceinline__ void backward_tile(const KArgs& a, const TileInfo& ti
                     }
                     if (kUpdate) {
                         float removed = 0.0f;
-                        if (c.st == kFree) {
+                        if (st == kFree) {
                             Lm = df_add(Lm, p);
                             const float M = (m1 + Lm.hi) - m0;
                             removed = a.omega * M;
@@ -376,59 +417,58 @@ __device__ __forceinline__ void backward_tile(const KArgs& a, const TileInfo& ti
                             a.lam_lo[si] = Lm.lo;
                             lm = Lm.hi;
                         }
-                        a.acc_out[size_t(c.v) * kAccStride + d.rank] = removed;
+                        a.acc_out[size_t(v) * kAccStride + d.rank] = removed;
                     } else {
                         lm = df_add(Lm, p).hi;
                         const float M = (m1 + lm) - m0;
                         a.mm_slot[si] = M;
-                        a.mm_var[size_t(c.v) * kAccStride + d.rank] = M;
+                        a.mm_var[size_t(v) * kAccStride + d.rank] = M;
                     }
                 } else {
                     lm = df_add(Lm, p).hi;
                 }
-                float bc[W];
+                float* Br = Bl + int64_t(l) * W * 32;
 #pragma unroll
                 for (int s = 0; s < W; ++s) {
                     const float v0 = al0 ? hx[s + 1] : BIG;
                     float v1 = BIG;
                     if (al1) v1 = (d.one ? (s == 0 ? b1 : BIG) : (up ? hx[s + 2] : hx[s])) + lm;
-                    bc[s] = s < d.w ? fminf(v0, v1) : BIG;
+                    bn[s] = s < d.w ? fminf(v0, v1) : BIG;
+                    if (kStoreB && s < d.w) Br[s * 32] = bn[s];
                 }
-                if (kStoreB) {
-                    float* Br = Bl + int64_t(l) * W * 32;
-#pragma unroll
-                    for (int s = 0; s < W; ++s)
-                        if (s < d.w) Br[s * 32] = bc[s];
-                }
-#pragma unroll
-                for (int s = 0; s < W; ++s) bn[s] = bc[s];
             }
-            ring[k] = nxt;
+            stage_issue<W, NODES>(a, ring + k * SF, lane, sb + int64_t(l - P) * 32, Fl + int64_t(l - P) * W * 32, hv[k],
+                                  hd[k]);
+            cv[k] = hv[k];
+            cd[k] = hd[k];
             hv[k] = nv;
             hd[k] = nd;
         }
     }
 done:
-    return;
+    cp_wait<0>();
 }
 
 template <int W, int MODE>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_backward(KArgs a) {
+    extern __shared__ float smem[];
     const int tile = a.tile0 + int(blockIdx.x) * kWarpsPerBlock + int(threadIdx.x >> 5);
     if (tile >= a.tile_end) return;
     const TileInfo ti = a.tiles[tile];
-    backward_tile<W, MODE>(a, ti);
+    backward_tile<W, MODE>(a, ti, smem + (threadIdx.x >> 5) * ring_floats<W>());
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_backward_fused(KArgs a) {
+    extern __shared__ float smem[];
     const int tile = a.tile0 + int(blockIdx.x) * kWarpsPerBlock + int(threadIdx.x >> 5);
     if (tile >= a.tile_end) return;
     const TileInfo ti = a.tiles[tile];
-    if (ti.W == 2) backward_tile<2, MODE>(a, ti);
-    else if (ti.W == 4) backward_tile<4, MODE>(a, ti);
-    else if (ti.W == 6) backward_tile<6, MODE>(a, ti);
-    else backward_tile<8, MODE>(a, ti);
+    float* ring = smem + (threadIdx.x >> 5) * ring_floats<8>();
+    if (ti.W == 2) backward_tile<2, MODE>(a, ti, ring);
+    else if (ti.W == 4) backward_tile<4, MODE>(a, ti, ring);
+    else if (ti.W == 6) backward_tile<6, MODE>(a, ti, ring);
+    else backward_tile<8, MODE>(a, ti, ring);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -476,15 +516,16 @@ cudaError_t launch_fused(Pass pass, const KArgs& a, cudaStream_t s) {
     const int n = a.tile_end - a.tile0;
     if (n <= 0) return cudaSuccess;
     const dim3 grid((n + kWarpsPerBlock - 1) / kWarpsPerBlock), block(kWarpsPerBlock * 32);
+    const size_t sm = size_t(kWarpsPerBlock) * ring_floats<8>() * sizeof(float);
     switch (pass) {
-        case Pass::FwdMMA: k_forward_fused<0><<<grid, block, 0, s>>>(a); break;
-        case Pass::FwdMMARound: k_forward_fused<1><<<grid, block, 0, s>>>(a); break;
-        case Pass::Lb: k_forward_fused<2><<<grid, block, 0, s>>>(a); break;
-        case Pass::FwdMM: k_forward_fused<3><<<grid, block, 0, s>>>(a); break;
-        case Pass::BwdMMA: k_backward_fused<0><<<grid, block, 0, s>>>(a); break;
-        case Pass::BwdMMARound: k_backward_fused<1><<<grid, block, 0, s>>>(a); break;
-        case Pass::BwdMM: k_backward_fused<2><<<grid, block, 0, s>>>(a); break;
-        case Pass::BwdReset: k_backward_fused<3><<<grid, block, 0, s>>>(a); break;
+        case Pass::FwdMMA: k_forward_fused<0><<<grid, block, sm, s>>>(a); break;
+        case Pass::FwdMMARound: k_forward_fused<1><<<grid, block, sm, s>>>(a); break;
+        case Pass::Lb: k_forward_fused<2><<<grid, block, sm, s>>>(a); break;
+        case Pass::FwdMM: k_forward_fused<3><<<grid, block, sm, s>>>(a); break;
+        case Pass::BwdMMA: k_backward_fused<0><<<grid, block, sm, s>>>(a); break;
+        case Pass::BwdMMARound: k_backward_fused<1><<<grid, block, sm, s>>>(a); break;
+        case Pass::BwdMM: k_backward_fused<2><<<grid, block, sm, s>>>(a); break;
+        case Pass::BwdReset: k_backward_fused<3><<<grid, block, sm, s>>>(a); break;
         case Pass::Supports: k_supports<8><<<grid, block, 0, s>>>(a); break;
     }
     return cudaGetLastError();
@@ -495,21 +536,38 @@ cudaError_t launch_w(Pass pass, const KArgs& a, cudaStream_t s) {
     const int n = a.tile_end - a.tile0;
     if (n <= 0) return cudaSuccess;
     const dim3 grid((n + kWarpsPerBlock - 1) / kWarpsPerBlock), block(kWarpsPerBlock * 32);
+    const size_t sm = size_t(kWarpsPerBlock) * ring_floats<W>() * sizeof(float);
     switch (pass) {
-        case Pass::FwdMMA: k_forward<W, 0><<<grid, block, 0, s>>>(a); break;
-        case Pass::FwdMMARound: k_forward<W, 1><<<grid, block, 0, s>>>(a); break;
-        case Pass::Lb: k_forward<W, 2><<<grid, block, 0, s>>>(a); break;
-        case Pass::FwdMM: k_forward<W, 3><<<grid, block, 0, s>>>(a); break;
-        case Pass::BwdMMA: k_backward<W, 0><<<grid, block, 0, s>>>(a); break;
-        case Pass::BwdMMARound: k_backward<W, 1><<<grid, block, 0, s>>>(a); break;
-        case Pass::BwdMM: k_backward<W, 2><<<grid, block, 0, s>>>(a); break;
-        case Pass::BwdReset: k_backward<W, 3><<<grid, block, 0, s>>>(a); break;
+        case Pass::FwdMMA: k_forward<W, 0><<<grid, block, sm, s>>>(a); break;
+        case Pass::FwdMMARound: k_forward<W, 1><<<grid, block, sm, s>>>(a); break;
+        case Pass::Lb: k_forward<W, 2><<<grid, block, sm, s>>>(a); break;
+        case Pass::FwdMM: k_forward<W, 3><<<grid, block, sm, s>>>(a); break;
+        case Pass::BwdMMA: k_backward<W, 0><<<grid, block, sm, s>>>(a); break;
+        case Pass::BwdMMARound: k_backward<W, 1><<<grid, block, sm, s>>>(a); break;
+        case Pass::BwdMM: k_backward<W, 2><<<grid, block, sm, s>>>(a); break;
+        case Pass::BwdReset: k_backward<W, 3><<<grid, block, sm, s>>>(a); break;
         case Pass::Supports: k_supports<W><<<grid, block, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------
+// Per instance: its tiles' sums in its fixed tile order plus its constant (one block each).
+__global__ void k_sum_instances(const double* __restrict__ x, const int32_t* __restrict__ ptr,
+                                const int32_t* __restrict__ tiles, const double* __restrict__ add, double* out) {
+    __shared__ double sh[256];
+    const int i = blockIdx.x;
+    double s = 0.0;
+    for (int k = ptr[i] + threadIdx.x; k < ptr[i + 1]; k += blockDim.x) s += x[tiles[k]];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (int(threadIdx.x) < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[i] = sh[0] + add[i];
+}
+
 __global__ void k_sum_tiles(const double* __restrict__ x, int64_t n, double add, double* out) {
     __shared__ double sh[1024];
     double s = 0.0;
@@ -573,12 +631,14 @@ __global__ void k_decide(const float* __restrict__ mm_var, const uint8_t* __rest
     }
 }
 
-// counters[0]: newly forced variables, counters[1]: conflicts, counters[2]: free variables left
-__global__ void k_apply(const uint8_t* __restrict__ sup, const uint8_t* __restrict__ deg, int64_t n, uint8_t* state,
-                        int* counters) {
+// Per instance (4 counters each, instance of variable v = inst[v]): [0] newly forced
+// variables, [1] conflicts, [2] free variables left.
+__global__ void k_apply(const uint8_t* __restrict__ sup, const uint8_t* __restrict__ deg,
+                        const int32_t* __restrict__ inst, int64_t n, uint8_t* state, int* counters) {
     for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
         const int dg = deg[v];
         if (dg == 0) continue;
+        int* c = counters + 4 * inst[v];
         bool can0 = true, can1 = true;
         for (int r = 0; r < dg; ++r) {
             const uint8_t s = sup[v * kAccStride + r];
@@ -587,13 +647,20 @@ __global__ void k_apply(const uint8_t* __restrict__ sup, const uint8_t* __restri
         }
         const uint8_t st = state[v];
         if ((st == kFix0 && !can0) || (st == kFix1 && !can1) || (st == kFree && !can0 && !can1)) {
-            atomicAdd(counters + 1, 1);
+            atomicAdd(c + 1, 1);
         } else if (st == kFree) {
-            if (!can0) { state[v] = kFix1; atomicAdd(counters, 1); }
-            else if (!can1) { state[v] = kFix0; atomicAdd(counters, 1); }
-            else atomicAdd(counters + 2, 1);
+            if (!can0) { state[v] = kFix1; atomicAdd(c, 1); }
+            else if (!can1) { state[v] = kFix0; atomicAdd(c, 1); }
+            else atomicAdd(c + 2, 1);
         }
     }
+}
+
+// Free variables per instance into counters[4 * i + 2].
+__global__ void k_count_free(const uint8_t* __restrict__ state, const uint8_t* __restrict__ deg,
+                             const int32_t* __restrict__ inst, int64_t n, int* counters) {
+    for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x)
+        if (deg[v] && state[v] == kFree) atomicAdd(counters + 4 * inst[v] + 2, 1);
 }
 
 __global__ void k_perturb(const uint32_t* __restrict__ var, const uint32_t* __restrict__ desc, int64_t n,
@@ -731,6 +798,11 @@ cudaError_t launch_pass(Pass pass, int W, const KArgs& a, cudaStream_t s) {
     }
 }
 
+cudaError_t launch_sum_instances(const double* tile_sum, const int32_t* ptr, const int32_t* tiles, const double* add,
+                                 int64_t n, double* out, cudaStream_t s) {
+    if (n > 0) k_sum_instances<<<unsigned(n), 256, 0, s>>>(tile_sum, ptr, tiles, add, out);
+    return cudaGetLastError();
+}
 cudaError_t launch_sum_tiles(const double* tile_sum, int64_t n, double add, double* out, cudaStream_t s) {
     k_sum_tiles<<<1, 1024, 0, s>>>(tile_sum, n, add, out);
     return cudaGetLastError();
@@ -761,9 +833,14 @@ cudaError_t launch_decide(const float* mm_var, const uint8_t* deg, const uint8_t
     if (n > 0) k_decide<<<grid_for(n, 256), 256, 0, s>>>(mm_var, deg, state, n, tau, trial);
     return cudaGetLastError();
 }
-cudaError_t launch_apply(const uint8_t* sup_var, const uint8_t* deg, int64_t n, uint8_t* state, int* counters,
-                         cudaStream_t s) {
-    if (n > 0) k_apply<<<grid_for(n, 256), 256, 0, s>>>(sup_var, deg, n, state, counters);
+cudaError_t launch_apply(const uint8_t* sup_var, const uint8_t* deg, const int32_t* inst, int64_t n, uint8_t* state,
+                         int* counters, cudaStream_t s) {
+    if (n > 0) k_apply<<<grid_for(n, 256), 256, 0, s>>>(sup_var, deg, inst, n, state, counters);
+    return cudaGetLastError();
+}
+cudaError_t launch_count_free(const uint8_t* state, const uint8_t* deg, const int32_t* inst, int64_t n, int* counters,
+                              cudaStream_t s) {
+    if (n > 0) k_count_free<<<grid_for(n, 256), 256, 0, s>>>(state, deg, inst, n, counters);
     return cudaGetLastError();
 }
 cudaError_t launch_perturb(const uint32_t* var, const uint32_t* desc, int64_t n, const float* mm_var,

@@ -60,6 +60,8 @@ enum class Pass {
 cudaError_t launch_pass(Pass pass, int W, const KArgs& a, cudaStream_t s);
 
 cudaError_t launch_sum_tiles(const double* tile_sum, int64_t n, double add, double* out, cudaStream_t s);
+cudaError_t launch_sum_instances(const double* tile_sum, const int32_t* ptr, const int32_t* tiles, const double* add,
+                                 int64_t n, double* out, cudaStream_t s);
 cudaError_t launch_gather_f32(const float* src, const int64_t* pos, int64_t n, float* dst, cudaStream_t s);
 cudaError_t launch_scatter_f32(const float* src, const int64_t* pos, int64_t n, float* dst, cudaStream_t s);
 cudaError_t launch_pend(const float* acc, const uint8_t* deg, int64_t n, float* pend, cudaStream_t s);
@@ -68,8 +70,10 @@ cudaError_t launch_flush(const uint32_t* var, const uint32_t* desc, int64_t nslo
                          float* lam_lo, cudaStream_t s);
 cudaError_t launch_decide(const float* mm_var, const uint8_t* deg, const uint8_t* state, int64_t n, float tau,
                           uint8_t* trial, cudaStream_t s);
-cudaError_t launch_apply(const uint8_t* sup_var, const uint8_t* deg, int64_t n, uint8_t* state, int* counters,
-                         cudaStream_t s);
+cudaError_t launch_apply(const uint8_t* sup_var, const uint8_t* deg, const int32_t* inst, int64_t n, uint8_t* state,
+                         int* counters, cudaStream_t s);
+cudaError_t launch_count_free(const uint8_t* state, const uint8_t* deg, const int32_t* inst, int64_t n, int* counters,
+                              cudaStream_t s);
 cudaError_t launch_perturb(const uint32_t* var, const uint32_t* desc, int64_t nslots, const float* mm_var,
                            const uint8_t* state, float delta, float* lam, float* lam_lo, cudaStream_t s);
 cudaError_t launch_pair_costs(const float* FX, const float* FY, int nvx, int nvy, int dim, float* d, cudaStream_t s);

@@ -111,6 +111,6 @@ struct MeshIn {
 
 // Returns 0 or a negative DISCO_ERR_* code (err receives a message).
 int build_plan(const MeshIn& X, const MeshIn& Y, const float* d, const uint8_t* allowed,
-               int split_chunk, int threads, Plan* out, std::string* err);
+               int split_chunk, int split_max_segments, int threads, Plan* out, std::string* err);
 
 }  // namespace disco

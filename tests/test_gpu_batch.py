@@ -1,0 +1,86 @@
+"""Batched solving: several pairs in one handle give the same per-pair results as solving
+each pair alone (every lane's arithmetic is independent of its tile placement), and the
+per-pair bounds match the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import bdd as B
+from oracle import problem as P
+from oracle import solver as S
+from synth import instances as I
+from synth import meshes as M
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_08230_gb300.build import build
+
+    build()
+    from paper_2310_08230_gb300.api import Solver
+
+    return Solver
+
+
+def _pairs():
+    out = []
+    for inst in (I.tet(), I.config1(), I.config2()):
+        prob, d, allowed = P.make_problem(inst)
+        out.append((inst, d, None if inst.topk is None else allowed))
+    rng = np.random.Generator(np.random.PCG64(21))
+    X = M.torus(5, 6)
+    Y, FX, FY, perm = I.make_pair(X, rng, 16, 0.05, deform=True)
+    inst = I.Instance("torus60", X, Y, FX, FY, perm, 6, 50)
+    prob, d, allowed = P.make_problem(inst)
+    out.append((inst, d, allowed))
+    return out
+
+
+@pytest.mark.parametrize("chunk", [0, 16])
+def test_batch_matches_single_instances(lib, chunk):
+    Solver = lib
+    pairs = _pairs()
+    iters = 60
+    batch = Solver.batch([(i.X.T, i.Y.T, d.astype(np.float32), a) for i, d, a in pairs], split_chunk=chunk)
+    assert batch.batch_size() == len(pairs)
+    batch.dual(iters)
+    lbs = batch.lower_bounds()
+    mm_b = batch.min_marginals()
+    assert batch.lower_bound() == pytest.approx(lbs.sum(), rel=1e-12)
+    singles, mms = [], []
+    for inst, d, a in pairs:
+        s = Solver(inst.X.T, inst.Y.T, d.astype(np.float32), a, split_chunk=chunk)
+        s.dual(iters)
+        singles.append(s.lower_bound())
+        mms.append(s.min_marginals())
+        s.close()
+    np.testing.assert_allclose(lbs, singles, rtol=1e-12, atol=0)
+    np.testing.assert_array_equal(mm_b, np.concatenate(mms))
+    xs, costs, ok = batch.primal_batch()
+    assert ok.all()
+    for (inst, d, a), x, c, lb in zip(pairs, xs, costs, lbs):
+        prob = P.build_problem(inst.X.T, inst.Y.T, d, a)
+        assert not np.any(prob.residual(x))
+        assert lb <= c + 1e-6 * abs(c)
+    batch.close()
+
+
+def test_batch_bounds_match_oracle(lib):
+    Solver = lib
+    pairs = _pairs()
+    iters = 40
+    batch = Solver.batch([(i.X.T, i.Y.T, d.astype(np.float32), a) for i, d, a in pairs])
+    batch.dual(iters)
+    lbs = batch.lower_bounds()
+    for (inst, d, a), lb in zip(pairs, lbs):
+        prob = P.build_problem(inst.X.T, inst.Y.T, d, a)
+        fixed, const = P.presolve(prob)
+        o = S.DualOracle(B.decompose(prob, fixed, const, 0))
+        o.iterate(iters)
+        ref = o.lower_bound()
+        assert abs(lb - ref) <= 1e-5 * max(abs(ref), 1e-3)
+    batch.close()

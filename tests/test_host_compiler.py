@@ -43,13 +43,13 @@ def test_struct_layouts_match_header(L):
     assert ctypes.sizeof(L.disco_mesh) == 24
 
 
-def _compile(L, inst, allowed, d, chunk):
+def _compile(L, inst, allowed, d, chunk, maxseg=8):
     mx = L.disco_mesh(inst.X.nv, inst.X.nt, None, inst.X.T.ctypes.data)
     my = L.disco_mesh(inst.Y.nv, inst.Y.nt, None, inst.Y.T.ctypes.data)
     info = L.disco_info_t()
     d32 = np.ascontiguousarray(d, np.float32)
     a8 = None if allowed is None else np.ascontiguousarray(allowed, np.uint8)
-    args = (ctypes.byref(mx), ctypes.byref(my), d32.ctypes.data, None if a8 is None else a8.ctypes.data, chunk,
+    args = (ctypes.byref(mx), ctypes.byref(my), d32.ctypes.data, None if a8 is None else a8.ctypes.data, chunk, maxseg,
             ctypes.byref(info))
     L.check(L.lib().disco_compile_host(*args, None, None, 0, None, 0), "compile")
     sv = np.empty(info.nslots, np.int32)
@@ -60,14 +60,15 @@ def _compile(L, inst, allowed, d, chunk):
     return info, sv, sw, fx
 
 
-@pytest.mark.parametrize("which,chunk", [("tet", 0), ("tet", 5), ("config1", 0), ("config1", 7), ("config2", 0),
-                                         ("config2", 16)])
-def test_host_compiler_matches_oracle(L, which, chunk):
+@pytest.mark.parametrize("which,chunk,maxseg", [("tet", 0, 8), ("tet", 5, 8), ("tet", 5, 0), ("config1", 0, 8),
+                                                ("config1", 7, 8), ("config1", 7, 3), ("config2", 0, 8),
+                                                ("config2", 16, 8), ("config2", 16, 0)])
+def test_host_compiler_matches_oracle(L, which, chunk, maxseg):
     inst = getattr(I, which)()
     prob, d, allowed = P.make_problem(inst)
     fixed, const = P.presolve(prob)
-    dec = B.decompose(prob, fixed, const, chunk)
-    info, sv, sw, fx = _compile(L, inst, None if inst.topk is None else allowed, d, chunk)
+    dec = B.decompose(prob, fixed, const, chunk, maxseg)
+    info, sv, sw, fx = _compile(L, inst, None if inst.topk is None else allowed, d, chunk, maxseg)
     assert info.nvars == prob.nvars
     assert info.nrows == prob.nrows
     assert np.array_equal(fx, fixed)
@@ -90,26 +91,26 @@ def test_host_compiler_errors(L):
     t = M.torus(3, 4)
     mt = L.disco_mesh(t.nv, t.nt, None, t.T.ctypes.data)
     dt = np.ones((inst.X.nv, t.nv), np.float32)
-    rc = L.lib().disco_compile_host(ctypes.byref(mx), ctypes.byref(mt), dt.ctypes.data, None, 0, ctypes.byref(info),
-                                    None, None, 0, None, 0)
+    rc = L.lib().disco_compile_host(ctypes.byref(mx), ctypes.byref(mt), dt.ctypes.data, None, 0, 8,
+                                    ctypes.byref(info), None, None, 0, None, 0)
     assert rc == L.DISCO_ERR_GENUS_MISMATCH
     # flipped triangle
     T = inst.Y.T.copy()
     T[0] = T[0][[0, 2, 1]]
     my = L.disco_mesh(inst.Y.nv, inst.Y.nt, None, T.ctypes.data)
-    rc = L.lib().disco_compile_host(ctypes.byref(mx), ctypes.byref(my), d.ctypes.data, None, 0, ctypes.byref(info),
-                                    None, None, 0, None, 0)
+    rc = L.lib().disco_compile_host(ctypes.byref(mx), ctypes.byref(my), d.ctypes.data, None, 0, 8,
+                                    ctypes.byref(info), None, None, 0, None, 0)
     assert rc == L.DISCO_ERR_NONMANIFOLD
     # negative / NaN costs
     bad = d.copy()
     bad[0, 0] = np.nan
     my = L.disco_mesh(inst.Y.nv, inst.Y.nt, None, inst.Y.T.ctypes.data)
-    rc = L.lib().disco_compile_host(ctypes.byref(mx), ctypes.byref(my), bad.ctypes.data, None, 0, ctypes.byref(info),
-                                    None, None, 0, None, 0)
+    rc = L.lib().disco_compile_host(ctypes.byref(mx), ctypes.byref(my), bad.ctypes.data, None, 0, 8,
+                                    ctypes.byref(info), None, None, 0, None, 0)
     assert rc == L.DISCO_ERR_INVALID_ARG
     # a candidate mask that leaves a triangle without any element
     allowed = np.zeros((inst.X.nv, inst.Y.nv), np.uint8)
-    rc = L.lib().disco_compile_host(ctypes.byref(mx), ctypes.byref(my), d.ctypes.data, allowed.ctypes.data, 0,
+    rc = L.lib().disco_compile_host(ctypes.byref(mx), ctypes.byref(my), d.ctypes.data, allowed.ctypes.data, 0, 8,
                                     ctypes.byref(info), None, None, 0, None, 0)
     assert rc == L.DISCO_ERR_INFEASIBLE
     assert b"element" in L.lib().disco_last_error() or b"empty" in L.lib().disco_last_error()
