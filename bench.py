@@ -42,6 +42,27 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _traffic(workload: str, split_chunk: int):
+    """DRAM bytes per half-pass launch from the committed ncu summary of this workload, or
+    None when the half-pass kernels changed since the counters were taken (source hash)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "halfpass_config3_icosphere4.md")
+    src = os.path.join(ROOT, "paper_2310_08230_gb300", "csrc", "kernels.cu")
+    if workload != "icosphere4-5120T-top16" or split_chunk != 32 or not os.path.exists(path):
+        return None
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    fields = {}
+    with open(path) as f:
+        for ln in f:
+            if ":" in ln and ln.split(":")[0] in ("kernels_cu_sha256_16", "traffic_bytes_per_launch"):
+                k, v = ln.split(":", 1)
+                fields[k] = v.strip()
+    if fields.get("kernels_cu_sha256_16") != h:
+        return None
+    return int(fields["traffic_bytes_per_launch"])
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -205,11 +226,13 @@ def gpu_arm(args):
     for _ in range(args.warmup):
         timed(False)
     times, stats_all = [], []
+    launches0 = lib.disco_kernel_launches()
     with Clocks() as clk:
         for _ in range(args.steps):
             t, st = timed(False)
             times.append(t)
             stats_all.append(st)
+    launches = lib.disco_kernel_launches() - launches0  # whole timed region (all steps)
     e2e_times = [timed(True)[0] for _ in range(max(1, min(args.steps, 3)))]
     ms = float(np.mean(times))
     if world > 1:
@@ -243,9 +266,9 @@ def gpu_arm(args):
         "rel_gap": (st["primal"] - st["lb"]) / st["primal"] if st["primal"] else None,
         "e2e": {"value": updates / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(FX_h.nbytes + FY_h.nbytes), "d2h_bytes_per_step": int(st["nvars"]) + 8},
-        "gpu_launches": None,
+        "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "half-pass (k_forward/k_backward MMA, all width classes)",
+                     "traffic": _traffic(inst.name, args.split_chunk), "kernel": "half-pass (k_forward/k_backward MMA, all width classes)",
                      "alg_bytes_per_launch": alg_bytes, "launch_ms": half_pass_ms, "peak_kind": kind},
         "clocks": clk.summary(),
     }

@@ -245,6 +245,10 @@ const char *disco_strerror(int code);
 /* Most recent error message of the calling thread ("" if none). */
 const char *disco_last_error(void);
 
+/* Number of CUDA kernel launches this library has issued in the process so far (all
+ * handles and devices): a caller can difference it around a region to count its launches. */
+int64_t disco_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

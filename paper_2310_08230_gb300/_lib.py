@@ -77,6 +77,7 @@ SIGNATURES = {
     "disco_free": (None, [P]),
     "disco_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "disco_last_error": (ctypes.c_char_p, []),
+    "disco_kernel_launches": (ctypes.c_int64, []),
 }
 
 _lib = None

@@ -481,6 +481,8 @@ const char* disco_strerror(int code) {
 
 const char* disco_last_error(void) { return g_last_error.c_str(); }
 
+int64_t disco_kernel_launches(void) { return g_launches.load(); }
+
 int disco_pair_costs(const float* FX, const float* FY, int32_t nvx, int32_t nvy, int32_t dim, float* d, void* stream) {
     if (!FX || !FY || !d || nvx <= 0 || nvy <= 0 || dim <= 0) return fail(DISCO_ERR_INVALID_ARG, "pair_costs: bad arguments");
     if (!is_device_ptr(FX) || !is_device_ptr(FY) || !is_device_ptr(d))

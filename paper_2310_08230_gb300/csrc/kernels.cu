@@ -15,11 +15,15 @@
 // writes the mass it removes to acc_out[i * 8 + r]; the next half-pass reads the deg values
 // of acc_in[i * 8 ..] (one 32-byte sector) and adds their mean. Sums run in rank order, so
 // every result is deterministic.
+#include <atomic>
 #include <cfloat>
 
 #include "kernels.h"
 
 namespace disco {
+
+std::atomic<int64_t> g_launches{0};
+
 namespace {
 
 constexpr float BIG = 1e30f;
@@ -518,15 +522,15 @@ cudaError_t launch_fused(Pass pass, const KArgs& a, cudaStream_t s) {
     const dim3 grid((n + kWarpsPerBlock - 1) / kWarpsPerBlock), block(kWarpsPerBlock * 32);
     const size_t sm = size_t(kWarpsPerBlock) * ring_floats<8>() * sizeof(float);
     switch (pass) {
-        case Pass::FwdMMA: k_forward_fused<0><<<grid, block, sm, s>>>(a); break;
-        case Pass::FwdMMARound: k_forward_fused<1><<<grid, block, sm, s>>>(a); break;
-        case Pass::Lb: k_forward_fused<2><<<grid, block, sm, s>>>(a); break;
-        case Pass::FwdMM: k_forward_fused<3><<<grid, block, sm, s>>>(a); break;
-        case Pass::BwdMMA: k_backward_fused<0><<<grid, block, sm, s>>>(a); break;
-        case Pass::BwdMMARound: k_backward_fused<1><<<grid, block, sm, s>>>(a); break;
-        case Pass::BwdMM: k_backward_fused<2><<<grid, block, sm, s>>>(a); break;
-        case Pass::BwdReset: k_backward_fused<3><<<grid, block, sm, s>>>(a); break;
-        case Pass::Supports: k_supports<8><<<grid, block, 0, s>>>(a); break;
+        case Pass::FwdMMA: k_forward_fused<0><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
+        case Pass::FwdMMARound: k_forward_fused<1><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
+        case Pass::Lb: k_forward_fused<2><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
+        case Pass::FwdMM: k_forward_fused<3><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
+        case Pass::BwdMMA: k_backward_fused<0><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
+        case Pass::BwdMMARound: k_backward_fused<1><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
+        case Pass::BwdMM: k_backward_fused<2><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
+        case Pass::BwdReset: k_backward_fused<3><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
+        case Pass::Supports: k_supports<8><<<grid, block, 0, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
     }
     return cudaGetLastError();
 }
@@ -538,15 +542,15 @@ cudaError_t launch_w(Pass pass, const KArgs& a, cudaStream_t s) {
     const dim3 grid((n + kWarpsPerBlock - 1) / kWarpsPerBlock), block(kWarpsPerBlock * 32);
     const size_t sm = size_t(kWarpsPerBlock) * ring_floats<W>() * sizeof(float);
     switch (pass) {
-        case Pass::FwdMMA: k_forward<W, 0><<<grid, block, sm, s>>>(a); break;
-        case Pass::FwdMMARound: k_forward<W, 1><<<grid, block, sm, s>>>(a); break;
-        case Pass::Lb: k_forward<W, 2><<<grid, block, sm, s>>>(a); break;
-        case Pass::FwdMM: k_forward<W, 3><<<grid, block, sm, s>>>(a); break;
-        case Pass::BwdMMA: k_backward<W, 0><<<grid, block, sm, s>>>(a); break;
-        case Pass::BwdMMARound: k_backward<W, 1><<<grid, block, sm, s>>>(a); break;
-        case Pass::BwdMM: k_backward<W, 2><<<grid, block, sm, s>>>(a); break;
-        case Pass::BwdReset: k_backward<W, 3><<<grid, block, sm, s>>>(a); break;
-        case Pass::Supports: k_supports<W><<<grid, block, 0, s>>>(a); break;
+        case Pass::FwdMMA: k_forward<W, 0><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
+        case Pass::FwdMMARound: k_forward<W, 1><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
+        case Pass::Lb: k_forward<W, 2><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
+        case Pass::FwdMM: k_forward<W, 3><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
+        case Pass::BwdMMA: k_backward<W, 0><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
+        case Pass::BwdMMARound: k_backward<W, 1><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
+        case Pass::BwdMM: k_backward<W, 2><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
+        case Pass::BwdReset: k_backward<W, 3><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
+        case Pass::Supports: k_supports<W><<<grid, block, 0, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
     }
     return cudaGetLastError();
 }
@@ -801,70 +805,85 @@ cudaError_t launch_pass(Pass pass, int W, const KArgs& a, cudaStream_t s) {
 cudaError_t launch_sum_instances(const double* tile_sum, const int32_t* ptr, const int32_t* tiles, const double* add,
                                  int64_t n, double* out, cudaStream_t s) {
     if (n > 0) k_sum_instances<<<unsigned(n), 256, 0, s>>>(tile_sum, ptr, tiles, add, out);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 cudaError_t launch_sum_tiles(const double* tile_sum, int64_t n, double add, double* out, cudaStream_t s) {
     k_sum_tiles<<<1, 1024, 0, s>>>(tile_sum, n, add, out);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 cudaError_t launch_gather_f32(const float* src, const int64_t* pos, int64_t n, float* dst, cudaStream_t s) {
     if (n > 0) k_gather<<<grid_for(n, 256), 256, 0, s>>>(src, pos, n, dst);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 cudaError_t launch_scatter_f32(const float* src, const int64_t* pos, int64_t n, float* dst, cudaStream_t s) {
     if (n > 0) k_scatter<<<grid_for(n, 256), 256, 0, s>>>(src, pos, n, dst);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 cudaError_t launch_pend(const float* acc, const uint8_t* deg, int64_t n, float* pend, cudaStream_t s) {
     if (n > 0) k_pend<<<grid_for(n, 256), 256, 0, s>>>(acc, deg, n, pend);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 cudaError_t launch_set_pend(const float* pend, const uint8_t* deg, int64_t n, float* acc, cudaStream_t s) {
     if (n > 0) k_set_pend<<<grid_for(n, 256), 256, 0, s>>>(pend, deg, n, acc);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 cudaError_t launch_flush(const uint32_t* var, const uint32_t* desc, int64_t n, const float* acc, float* lam,
                          float* lam_lo, cudaStream_t s) {
     if (n > 0) k_flush<<<grid_for(n, 256), 256, 0, s>>>(var, desc, n, acc, lam, lam_lo);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 cudaError_t launch_decide(const float* mm_var, const uint8_t* deg, const uint8_t* state, int64_t n, float tau,
                           uint8_t* trial, cudaStream_t s) {
     if (n > 0) k_decide<<<grid_for(n, 256), 256, 0, s>>>(mm_var, deg, state, n, tau, trial);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 cudaError_t launch_apply(const uint8_t* sup_var, const uint8_t* deg, const int32_t* inst, int64_t n, uint8_t* state,
                          int* counters, cudaStream_t s) {
     if (n > 0) k_apply<<<grid_for(n, 256), 256, 0, s>>>(sup_var, deg, inst, n, state, counters);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 cudaError_t launch_count_free(const uint8_t* state, const uint8_t* deg, const int32_t* inst, int64_t n, int* counters,
                               cudaStream_t s) {
     if (n > 0) k_count_free<<<grid_for(n, 256), 256, 0, s>>>(state, deg, inst, n, counters);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 cudaError_t launch_perturb(const uint32_t* var, const uint32_t* desc, int64_t n, const float* mm_var,
                            const uint8_t* state, float delta, float* lam, float* lam_lo, cudaStream_t s) {
     if (n > 0) k_perturb<<<grid_for(n, 256), 256, 0, s>>>(var, desc, n, mm_var, state, delta, lam, lam_lo);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 cudaError_t launch_pair_costs(const float* FX, const float* FY, int nvx, int nvy, int dim, float* d, cudaStream_t s) {
     const dim3 grid((nvy + kPT - 1) / kPT, (nvx + kPT - 1) / kPT);
     k_pair_costs<<<grid, 256, 0, s>>>(FX, FY, nvx, nvy, dim, d);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 cudaError_t launch_transpose(const float* src, int rows, int cols, float* dst, cudaStream_t s) {
     const dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
     k_transpose<<<grid, block, 0, s>>>(src, rows, cols, dst);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 cudaError_t launch_topk_rows(const float* d, int rows, int cols, int k, int32_t* idx, cudaStream_t s) {
     k_topk_rows<<<(rows + 7) / 8, 256, 0, s>>>(d, rows, cols, k, idx);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 cudaError_t launch_dilate(const int32_t* topk, int rows, int k, const int32_t* ring_ptr, const int32_t* ring, int nvy,
                           bool transposed, uint8_t* allowed, cudaStream_t s) {
     k_dilate<<<rows, dim3(8, 8), 0, s>>>(topk, rows, k, ring_ptr, ring, nvy, transposed, allowed);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 

@@ -5,7 +5,12 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 namespace disco {
+
+// Kernel launches issued by this library so far (all devices, all handles).
+extern std::atomic<int64_t> g_launches;
 
 // A warp tile: 32 BDD segments (one per lane) of one width class.
 //   slot (layer l, lane)      at slot_base + l * 32 + lane              (var, desc, lambda)

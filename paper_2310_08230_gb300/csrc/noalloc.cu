@@ -205,6 +205,7 @@ extern "C" int disco_candidates_noalloc(const float* d, int32_t nvx, int32_t nvy
             k_count<<<(3 * nt + 255) / 256, 256, 0, s>>>(T, 3 * nt, cur);
             k_scan<<<1, 1024, 0, s>>>(cur, nv, ptr, cur);
             k_fill<<<(3 * nt + 255) / 256, 256, 0, s>>>(T, nt, cur, inc);
+            disco::g_launches.fetch_add(3, std::memory_order_relaxed);
             e = cudaGetLastError();
         }
     }
@@ -217,6 +218,7 @@ extern "C" int disco_candidates_noalloc(const float* d, int32_t nvx, int32_t nvy
         const int32_t* TX = mesh[0];
         k_mark<<<nvy, dim3(8, 8), 0, s>>>(topk, nvy, k, TX + kTriInts, TX + kTriInts + kPtrInts, TX, nvy, true,
                                           allowed);
+        disco::g_launches.fetch_add(3, std::memory_order_relaxed);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
