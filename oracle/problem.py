@@ -91,14 +91,15 @@ def candidate_pairs(d: np.ndarray, k: int, TX: np.ndarray, TY: np.ndarray) -> np
     Y vertices of m, or m lies in the closed 1-ring of one of the k feature-nearest X
     vertices of n (ties to the lower index)."""
     nx, ny = d.shape
-    cxy = np.zeros((nx, ny), dtype=np.int64)  # n0 among the k nearest of m
-    cyx = np.zeros((nx, ny), dtype=np.int64)  # m0 among the k nearest of n
+    # 0/1 indicator matrices; the products below count ring hits, exact in float64
+    cxy = np.zeros((nx, ny), dtype=np.float64)  # n0 among the k nearest of m
+    cyx = np.zeros((nx, ny), dtype=np.float64)  # m0 among the k nearest of n
     rows = np.argsort(d, axis=1, kind="stable")[:, : min(k, ny)]
     cxy[np.arange(nx)[:, None], rows] = 1
     cols = np.argsort(d, axis=0, kind="stable")[: min(k, nx), :]
     cyx[cols, np.arange(ny)[None, :]] = 1
-    AX = closed_one_ring(nx, TX).astype(np.int64)
-    AY = closed_one_ring(ny, TY).astype(np.int64)
+    AX = closed_one_ring(nx, TX).astype(np.float64)
+    AY = closed_one_ring(ny, TY).astype(np.float64)
     return ((cxy @ AY) > 0) | ((AX @ cyx) > 0)
 
 

@@ -480,25 +480,53 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         });
     }
     tr.mark("closedness buckets");
-    // order each bucket by (smaller vertex, larger vertex, entry); count rows per bucket
+    // order each bucket by (smaller vertex, larger vertex, entry); count rows per bucket.
+    // Entries arrive in entry order. The smaller product vertex (m, n) of an edge is a corner
+    // of an element, so n is a candidate of m: a stable counting sort on n's position in the
+    // candidate row of m, then a stable sort by the larger vertex inside each group.
     std::vector<int64_t> brows(size_t(nvx) + 1, 0);
-    const bool packed = nvy < (1 << 16);
     parallel_chunks(nth * 4, nth, [&](int, int64_t c0, int64_t c1) {
-        std::vector<uint64_t> key;
+        std::vector<int32_t> pos_of(static_cast<size_t>(nvy), -1);
+        std::vector<int64_t> cnt;
         std::vector<EdgeEntry> tmp;
         for (int64_t c = c0; c < c1; ++c)
             for (int64_t m = int64_t(nvx) * c / (nth * 4); m < int64_t(nvx) * (c + 1) / (nth * 4); ++m) {
                 const int64_t b0 = bstart[m], b1 = bstart[m + 1], nb = b1 - b0;
-                if (packed && nb < (int64_t(1) << 16)) {
-                    // entries arrive in id order: (lo_n, hi, position) in one integer sorts them
-                    key.resize(size_t(nb));
-                    for (int64_t e = 0; e < nb; ++e)
-                        key[e] = (uint64_t(ent[b0 + e].lo_n) << 48) | (uint64_t(ent[b0 + e].hi) << 16) | uint64_t(e);
-                    std::sort(key.begin(), key.end());
-                    tmp.assign(ent.get() + b0, ent.get() + b1);
-                    for (int64_t e = 0; e < nb; ++e) ent[b0 + e] = tmp[key[e] & 0xFFFFu];
-                } else {
+                const int32_t* cand = A.row.item.data() + A.row.ptr[m];
+                const int ncand = A.row.ptr[m + 1] - A.row.ptr[m];
+                for (int i = 0; i < ncand; ++i) pos_of[cand[i]] = i;
+                bool ok = true;
+                for (int64_t e = b0; e < b1 && ok; ++e) {
+                    const int32_t p = pos_of[ent[e].lo_n];
+                    ok = p >= 0 && p < ncand && cand[p] == int32_t(ent[e].lo_n);
+                }
+                if (!ok) {
                     std::sort(ent.get() + b0, ent.get() + b1);
+                } else {
+                    cnt.assign(size_t(ncand) + 1, 0);
+                    for (int64_t e = b0; e < b1; ++e) ++cnt[size_t(pos_of[ent[e].lo_n]) + 1];
+                    for (int i = 0; i < ncand; ++i) cnt[i + 1] += cnt[i];
+                    tmp.resize(size_t(nb));
+                    for (int64_t e = b0; e < b1; ++e) tmp[size_t(cnt[pos_of[ent[e].lo_n]]++)] = ent[e];
+                    // cnt[i] is now the end of group i
+                    int64_t g0 = 0;
+                    for (int i = 0; i < ncand; ++i) {
+                        const int64_t g1 = cnt[i];
+                        EdgeEntry* g = tmp.data() + g0;
+                        const int64_t ng = g1 - g0;
+                        if (ng <= 64) {
+                            for (int64_t x = 1; x < ng; ++x) {
+                                const EdgeEntry v = g[x];
+                                int64_t y = x;
+                                for (; y > 0 && g[y - 1].hi > v.hi; --y) g[y] = g[y - 1];
+                                g[y] = v;
+                            }
+                        } else {
+                            std::stable_sort(g, g + ng, [](const EdgeEntry& a, const EdgeEntry& b) { return a.hi < b.hi; });
+                        }
+                        g0 = g1;
+                    }
+                    std::copy(tmp.begin(), tmp.end(), ent.get() + b0);
                 }
                 int64_t r = 0;
                 for (int64_t e = b0; e < b1; ++e)
@@ -516,17 +544,29 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     P->row_var.resize(size_t(ne + nproj_entries));
     P->row_coef.resize(size_t(ne + nproj_entries));
     pod_vector<int32_t> row_ent(static_cast<size_t>(ne + nproj_entries));  // corner (0..2) or 3 + side
-    pod_vector<int64_t> elem_row(static_cast<size_t>(ne));     // element corner -> its closedness row
+    pod_vector<int32_t> elem_row(static_cast<size_t>(ne));     // element corner -> its closedness row
+    pod_vector<int8_t> elem_coef(static_cast<size_t>(ne));     // and its coefficient there
+    // presolve state of every row: residual right-hand side, free +1 / -1 entries
+    struct RowState {
+        int32_t res, np, nn, queued;
+    };
+    pod_vector<RowState> rs(static_cast<size_t>(n_closed + X.nt + Y.nt));
     parallel_chunks(nvx, nth * 4, [&](int, int64_t lo, int64_t hi) {
         for (int64_t m = lo; m < hi; ++m) {
             int64_t r = brows[m] - 1;
             for (int64_t e = bstart[m]; e < bstart[m + 1]; ++e) {
-                if (e == bstart[m] || !ent[e].same_edge(ent[e - 1])) P->row_ptr[++r] = e;
+                if (e == bstart[m] || !ent[e].same_edge(ent[e - 1])) {
+                    P->row_ptr[++r] = e;
+                    rs[r] = RowState{0, 0, 0, 0};
+                }
                 const uint32_t id = ent[e].id >> 1;
+                const bool neg = ent[e].id & 1u;
                 P->row_var[e] = int32_t(id / 3);
-                P->row_coef[e] = (ent[e].id & 1u) ? -1 : 1;
+                P->row_coef[e] = neg ? -1 : 1;
                 row_ent[e] = int32_t(id % 3);
-                elem_row[id] = r;
+                elem_row[id] = int32_t(r);
+                elem_coef[id] = P->row_coef[e];
+                ++(neg ? rs[r].nn : rs[r].np);
             }
         }
     });
@@ -559,6 +599,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
             int64_t tot = 0;
             for (int c = 0; c < nth; ++c) tot += cnt[c][t];
             if (tot == 0) { *err = "a triangle has no matching element"; return DISCO_ERR_INFEASIBLE; }
+            rs[size_t(row0 + t)] = RowState{1, int32_t(tot), 0, 0};
             P->row_ptr.push_back(run);
             for (int c = 0; c < nth; ++c) {
                 off[c][t] = run;
@@ -586,91 +627,114 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     const int64_t nr = P->nrows;
 
     tr.mark("projection rows");
-    // ---- presolve: saturated rows force all their free variables, to a fixpoint. Rounds
-    // are bulk-synchronous (decide on a snapshot, apply, recount the touched rows), so the
-    // result is the unique arc-consistent closure whatever the thread count.
-    std::vector<int32_t> res(P->rhs.begin(), P->rhs.end());
-    pod_vector<int32_t> npos(static_cast<size_t>(nr)), nneg(static_cast<size_t>(nr));
+    // ---- presolve: saturated rows force all their free variables, to a fixpoint. Rows and
+    // variables are split into contiguous ranges, one per thread, and each thread alone
+    // writes the state of its ranges. A round is bulk-synchronous: (1) the owners of the
+    // frontier rows decide on the counts of the previous round and send every forced value
+    // to the variable's owner; (2) variable owners fix the variables (a second, different
+    // value is a conflict) and send (row, coefficient, value) to the owners of the
+    // variable's rows; (3) row owners update the free counts and the residual and queue each
+    // updated row once for the next round. The fixed values are the unique arc-consistent
+    // closure whatever the thread count.
     P->fixed.assign(size_t(nv), -1);
-    auto recount = [&](int64_t r) {
-        int32_t rs = P->rhs[r], np = 0, nn = 0;
-        for (int64_t e = P->row_ptr[r]; e < P->row_ptr[r + 1]; ++e) {
-            const int8_t f = P->fixed[P->row_var[e]];
-            if (f < 0) (P->row_coef[e] > 0 ? np : nn)++;
-            else rs -= P->row_coef[e] * f;
-        }
-        res[r] = rs;
-        npos[r] = np;
-        nneg[r] = nn;
-    };
     {
-        // nothing is fixed yet: the counts are the coefficient counts; every row is in round 1
-        std::vector<std::vector<int64_t>> first(nth);
-        parallel_chunks(nr, nth, [&](int c, int64_t lo, int64_t hi) {
-            for (int64_t r = lo; r < hi; ++r) {
-                int32_t np = 0, nn = 0;
-                for (int64_t e = P->row_ptr[r]; e < P->row_ptr[r + 1]; ++e) (P->row_coef[e] > 0 ? np : nn)++;
-                npos[r] = np;
-                nneg[r] = nn;
-                // only saturated or violated rows can act
-                if (res[r] == np || res[r] == -nn || res[r] > np || res[r] < -nn) first[c].push_back(r);
-            }
+        const int nt = nth;
+        // owner of row r / variable v: table lookup by blocks of 4096
+        auto owners = [&](int64_t n) {
+            std::vector<uint8_t> tab(size_t((n >> 12) + 1));
+            for (size_t b = 0; b < tab.size(); ++b) tab[b] = uint8_t(std::min<int64_t>(nt - 1, (int64_t(b) << 12) * nt / n));
+            return tab;
+        };
+        if (nt > 255) { *err = "too many host threads"; return DISCO_ERR_INVALID_ARG; }
+        const std::vector<uint8_t> row_owner = owners(nr), var_owner = owners(nv);
+        auto row_lo = [&](int t) {  // first row owned by t (block granular, matches the table)
+            int64_t b = 0;
+            while (b < int64_t(row_owner.size()) && row_owner[b] < t) ++b;
+            return std::min<int64_t>(nr, b << 12);
+        };
+        std::vector<std::vector<int32_t>> frontier(nt);
+        parallel_chunks(nt, nt, [&](int t, int64_t, int64_t) {
+            // nothing is fixed yet: only saturated or violated rows can act in round 1
+            for (int64_t r = row_lo(t), r1 = row_lo(t + 1); r < r1; ++r)
+                if (rs[r].res >= rs[r].np || rs[r].res <= -rs[r].nn) frontier[t].push_back(int32_t(r));
         });
-        std::vector<int64_t> frontier;
-        for (auto& x : first) frontier.insert(frontier.end(), x.begin(), x.end());
-        std::vector<uint8_t> touched(static_cast<size_t>(nr), 0);
-        std::atomic<int> bad{0};
-        while (!frontier.empty() && !bad.load()) {
-            // decide on the snapshot
-            std::vector<std::vector<std::pair<int32_t, int8_t>>> prop(nth);
-            parallel_chunks(int64_t(frontier.size()), nth, [&](int c, int64_t lo, int64_t hi) {
-                for (int64_t k = lo; k < hi; ++k) {
-                    const int64_t r = frontier[k];
-                    if (res[r] > npos[r] || res[r] < -nneg[r]) { bad = 1; return; }
-                    if (npos[r] + nneg[r] == 0) continue;
+        struct Upd {
+            int32_t row;
+            int32_t code;  // bit 0: value, bit 1: coefficient > 0
+        };
+        std::vector<std::vector<std::vector<std::pair<int32_t, int8_t>>>> force(nt, std::vector<std::vector<std::pair<int32_t, int8_t>>>(nt));
+        std::vector<std::vector<std::vector<Upd>>> upd(nt, std::vector<std::vector<Upd>>(nt));
+        std::vector<int> bad(nt, 0);
+        auto any = [&](auto pred) {
+            for (int t = 0; t < nt; ++t)
+                if (pred(t)) return true;
+            return false;
+        };
+        while (any([&](int t) { return !frontier[t].empty(); })) {
+            // (1) decide
+            parallel_chunks(nt, nt, [&](int t, int64_t, int64_t) {
+                for (auto& b : force[t]) b.clear();
+                for (const int32_t r : frontier[t]) {
+                    RowState& q = rs[r];
+                    q.queued = 0;
+                    if (q.res > q.np || q.res < -q.nn) { bad[t] = 1; return; }
+                    if (q.np + q.nn == 0) continue;
                     int up;
-                    if (res[r] == npos[r]) up = 1;
-                    else if (res[r] == -nneg[r]) up = 0;
+                    if (q.res == q.np) up = 1;
+                    else if (q.res == -q.nn) up = 0;
                     else continue;
                     for (int64_t e = P->row_ptr[r]; e < P->row_ptr[r + 1]; ++e) {
                         const int32_t v = P->row_var[e];
-                        if (P->fixed[v] < 0) prop[c].emplace_back(v, int8_t(P->row_coef[e] > 0 ? up : 1 - up));
+                        if (P->fixed[v] < 0)
+                            force[t][var_owner[size_t(v) >> 12]].emplace_back(v, int8_t(P->row_coef[e] > 0 ? up : 1 - up));
                     }
                 }
             });
-            if (bad.load()) break;
-            // apply: first writer wins, a different value is a conflict; mark the touched rows
-            parallel_chunks(nth, nth, [&](int c, int64_t, int64_t) {
-                for (auto [v, val] : prop[c]) {
-                    int8_t expect = -1;
-                    if (__atomic_compare_exchange_n(&P->fixed[v], &expect, val, false, __ATOMIC_RELAXED,
-                                                    __ATOMIC_RELAXED)) {
-                        for (int q = 0; q < 3; ++q) touched[elem_row[3 * int64_t(v) + q]] = 1;
-                        for (int side = 0; side < 2; ++side)
-                            if (proj_row[size_t(2) * v + side] >= 0) touched[proj_row[size_t(2) * v + side]] = 1;
-                    } else if (expect != val) {
-                        bad = 1;
-                    }
-                }
-            });
-            if (bad.load()) break;
-            // the touched rows, in row order, are recounted and form the next frontier
-            std::vector<std::vector<int64_t>> next(nth);
-            parallel_chunks(nr, nth, [&](int c, int64_t lo, int64_t hi) {
-                for (int64_t r = lo; r < hi; ++r)
-                    if (touched[r]) {
-                        touched[r] = 0;
-                        recount(r);
-                        next[c].push_back(r);
+            if (any([&](int t) { return bad[t] != 0; })) break;
+            // (2) fix
+            parallel_chunks(nt, nt, [&](int u, int64_t, int64_t) {
+                for (auto& b : upd[u]) b.clear();
+                for (int t = 0; t < nt; ++t)
+                    for (auto [v, val] : force[t][u]) {
+                        const int8_t f = P->fixed[v];
+                        if (f == val) continue;
+                        if (f >= 0) { bad[u] = 1; return; }
+                        P->fixed[v] = val;
+                        for (int q = 0; q < 3; ++q) {
+                            const int32_t r = elem_row[3 * int64_t(v) + q];
+                            upd[u][row_owner[size_t(r) >> 12]].push_back(Upd{r, val | (elem_coef[3 * int64_t(v) + q] > 0 ? 2 : 0)});
+                        }
+                        for (int side = 0; side < 2; ++side) {
+                            const int32_t r = proj_row[size_t(2) * v + side];
+                            if (r >= 0) upd[u][row_owner[size_t(r) >> 12]].push_back(Upd{r, val | 2});
+                        }
                     }
             });
-            frontier.clear();
-            for (auto& x : next) frontier.insert(frontier.end(), x.begin(), x.end());
+            if (any([&](int t) { return bad[t] != 0; })) break;
+            // (3) update the rows, queue each once
+            parallel_chunks(nt, nt, [&](int t, int64_t, int64_t) {
+                frontier[t].clear();
+                for (int u = 0; u < nt; ++u)
+                    for (const Upd& m : upd[u][t]) {
+                        RowState& q = rs[m.row];
+                        if (m.code & 2) {
+                            --q.np;
+                            q.res -= m.code & 1;
+                        } else {
+                            --q.nn;
+                            q.res += m.code & 1;
+                        }
+                        if (!q.queued) {
+                            q.queued = 1;
+                            frontier[t].push_back(m.row);
+                        }
+                    }
+            });
         }
-        if (bad.load()) { *err = "presolve: a row has no solution"; return DISCO_ERR_INFEASIBLE; }
+        if (any([&](int t) { return bad[t] != 0; })) { *err = "presolve: a row has no solution"; return DISCO_ERR_INFEASIBLE; }
     }
     for (int64_t r = 0; r < nr; ++r)
-        if (npos[r] + nneg[r] == 0 && res[r] != 0) { *err = "presolve: violated row"; return DISCO_ERR_INFEASIBLE; }
+        if (rs[r].np + rs[r].nn == 0 && rs[r].res != 0) { *err = "presolve: violated row"; return DISCO_ERR_INFEASIBLE; }
     tr.mark("presolve");
     P->constant = 0.0;
     std::vector<int32_t> internal(size_t(nv), -1);
@@ -723,7 +787,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                 }
                 const int n = int(fv.size());
                 if (n == 0) continue;
-                const int rr = res[r];
+                const int rr = rs[r].res;
                 int ptot = 0, qtot = 0;
                 for (int8_t cf : fc) (cf > 0 ? ptot : qtot)++;
                 lo.assign(n + 1, 0);
