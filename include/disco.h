@@ -74,7 +74,14 @@ typedef struct {
     int32_t split_max_segments; /* [8] at most this many segments per row when splitting (0 = no
                                  cap): a one-hot chain carries cost information across one cut
                                  per half-pass, so very long rows are cut into longer segments */
-    int32_t reserved[6];
+    int32_t graph_iters;      /* [10] dual iterations captured once into a CUDA graph and replayed
+                                 as a block; 0 = one launch per half-pass and width class. If the
+                                 stream cannot be captured the library launches plainly. */
+    int32_t autotune;         /* [1] time the launch geometries of the half-pass kernels on the
+                                 first dual iterations and keep the fastest; every geometry gives
+                                 bit-identical results, so the trial iterations count as normal
+                                 iterations. 0 = the default geometry. */
+    int32_t reserved[4];
 } disco_opts;
 
 typedef struct {
@@ -94,7 +101,9 @@ typedef struct {
     double build_ms;          /* host time of disco_build */
     int64_t bytes_per_iter;   /* algorithmic bytes of one iteration (two half-passes) */
     double upload_ms;         /* disco_build time after the host compiler: device store, upload */
-    int64_t reserved[4];
+    int64_t launch_geometry;  /* warps per block of the half-pass kernels (chosen by the autotuner
+                                 or the default) */
+    int64_t reserved[3];
 } disco_info_t;
 
 typedef struct disco_handle disco_handle;

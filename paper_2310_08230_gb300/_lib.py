@@ -36,7 +36,8 @@ class disco_opts(ctypes.Structure):
         ("perturb_delta0", ctypes.c_float), ("perturb_growth", ctypes.c_float), ("tie_tau", ctypes.c_float),
         ("propagate_limit", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
         ("host_threads", ctypes.c_int32), ("split_max_segments", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 6),
+        ("graph_iters", ctypes.c_int32), ("autotune", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 
@@ -46,7 +47,8 @@ class disco_info_t(ctypes.Structure):
         "ntiles", "device_bytes", "iterations")] + [("constant", ctypes.c_double), ("build_ms", ctypes.c_double),
                                                    ("bytes_per_iter", ctypes.c_int64),
                                                    ("upload_ms", ctypes.c_double),
-                                                   ("reserved", ctypes.c_int64 * 4)]
+                                                   ("launch_geometry", ctypes.c_int64),
+                                                   ("reserved", ctypes.c_int64 * 3)]
 
 
 V, P, I32, I64, D, F = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_float

@@ -127,7 +127,12 @@ struct disco_handle {
     int64_t nelems() const { return elem_base.back(); }
     bool has_b = false;
     std::vector<void*> allocations;
-    cudaGraphExec_t iter_graph = nullptr;
+    int geometry = 2;              // warps per block of the fused MMA half-passes
+    bool tuned = false;            // autotuner done (or off)
+    cudaGraphExec_t iter_graph = nullptr;  // opts.graph_iters iterations, replayed as a block
+    int graph_cur = 0;             // averaging-buffer parity the graph was captured at
+    int64_t graph_launches = 0;    // kernels in one replay
+    bool graph_failed = false;     // the stream could not be captured: launch plainly
 
     template <class T>
     int alloc(T** p, int64_t n) {
@@ -166,7 +171,7 @@ struct disco_handle {
 
     // One pass over every width class (a half-pass flips the averaging buffers).
     int pass(Pass p) {
-        for (const WidthClass& c : classes) CK(launch_pass(p, c.W, args(c), stream));
+        for (const WidthClass& c : classes) CK(launch_pass(p, c.W, args(c), stream, geometry));
         if (p == Pass::FwdMMA || p == Pass::BwdMMA || p == Pass::FwdMMARound || p == Pass::BwdMMARound) cur ^= 1;
         return DISCO_OK;
     }
@@ -210,6 +215,8 @@ int width_class(int w) {
 }
 
 int upload(disco_handle* h) {
+    Trace tr;
+    tr.scope = "upload";
     const int64_t ni = h->n_inst();
     const int nth = host_threads(h->opts);
     h->var_base.assign(size_t(ni) + 1, 0);
@@ -224,63 +231,70 @@ int upload(disco_handle* h) {
     h->nint = h->var_base[ni];
     if (h->nint >= (int64_t(1) << 32) - 1) return fail(DISCO_ERR_INVALID_ARG, "build: too many variables");
     // ---- tiles: per instance, segments grouped by width class, longest first; a tile never
-    // mixes instances (its bound sum belongs to one instance)
+    // mixes instances (its bound sum belongs to one instance). Counting sorts by (class,
+    // length), then the tiles by (launch group, length): both stable.
     struct TileSeg {
         int32_t inst;
         int64_t seg;
     };
+    auto class_index = [](int W) { return W <= 2 ? 0 : W <= 4 ? 1 : W <= 6 ? 2 : W <= 8 ? 3 : W <= 16 ? 4 : 5; };
     std::vector<TileInfo> tiles;
-    std::vector<std::vector<TileSeg>> tile_segs;
-    std::vector<int32_t> tile_inst;
+    std::vector<int64_t> tile_first;  // first entry of the tile's segments in `order`
+    std::vector<int32_t> tile_count, tile_inst;
+    std::vector<TileSeg> order;
+    int maxL = 1;
+    for (int64_t i = 0; i < ni; ++i) maxL = std::max(maxL, h->plans[i].max_layers);
     for (int64_t i = 0; i < ni; ++i) {
         const Plan& P = h->plans[i];
         const int64_t nseg = int64_t(P.segs.size());
-        std::vector<int64_t> order(nseg);
-        std::iota(order.begin(), order.end(), 0);
-        std::vector<uint8_t> wcls(static_cast<size_t>(nseg));
-        for (int64_t k = 0; k < nseg; ++k) wcls[k] = uint8_t(width_class(P.segs[k].max_width));
-        std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
-            if (wcls[x] != wcls[y]) return wcls[x] < wcls[y];
-            return P.segs[x].n_layers > P.segs[y].n_layers;
-        });
+        std::vector<int64_t> cnt(size_t(6) * (maxL + 1) + 1, 0);
+        auto key = [&](const Segment& sg) {  // class ascending, length descending
+            return size_t(class_index(width_class(sg.max_width))) * (maxL + 1) + size_t(maxL - sg.n_layers);
+        };
+        for (const Segment& sg : P.segs) ++cnt[key(sg) + 1];
+        for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
+        const size_t o0 = order.size();
+        order.resize(o0 + size_t(nseg));
+        for (int64_t k = 0; k < nseg; ++k) order[o0 + size_t(cnt[key(P.segs[k])]++)] = TileSeg{int32_t(i), k};
         for (int64_t k = 0; k < nseg;) {
-            const int W = wcls[order[k]];
-            std::vector<TileSeg> ts;
-            int L = 0;
-            for (int q = 0; q < 32 && k < nseg && wcls[order[k]] == W; ++q, ++k) {
-                ts.push_back(TileSeg{int32_t(i), order[k]});
-                L = std::max(L, P.segs[order[k]].n_layers);
-            }
+            const int W = width_class(P.segs[order[o0 + k].seg].max_width);
+            const int64_t first = int64_t(o0) + k;
+            const int L = P.segs[order[o0 + k].seg].n_layers;
+            int q = 0;
+            while (q < 32 && k < nseg && width_class(P.segs[order[o0 + k].seg].max_width) == W) ++q, ++k;
             tiles.push_back(TileInfo{0, 0, L, W});
-            tile_segs.push_back(std::move(ts));
+            tile_first.push_back(first);
+            tile_count.push_back(q);
             tile_inst.push_back(int32_t(i));
         }
     }
-    // classes 2, 4, 6, 8 share one launch, longest tiles first; 16 and 32 launch on their own
-    std::vector<size_t> tord(tiles.size());
-    std::iota(tord.begin(), tord.end(), size_t(0));
-    std::stable_sort(tord.begin(), tord.end(), [&](size_t x, size_t y) {
-        const int gx = tiles[x].W <= 8 ? 0 : tiles[x].W, gy = tiles[y].W <= 8 ? 0 : tiles[y].W;
-        if (gx != gy) return gx < gy;
-        return tiles[x].L > tiles[y].L;
-    });
+    // classes up to kFusedMaxW share one launch, longest tiles first; wider ones launch on their own
     {
-        std::vector<TileInfo> t2;
-        std::vector<std::vector<TileSeg>> s2;
-        std::vector<int32_t> i2;
-        for (size_t k : tord) {
-            t2.push_back(tiles[k]);
-            s2.push_back(std::move(tile_segs[k]));
-            i2.push_back(tile_inst[k]);
+        auto group_index = [](int W) { return W <= kFusedMaxW ? 0 : W <= 8 ? 1 : W <= 16 ? 2 : 3; };
+        std::vector<int64_t> cnt(size_t(4) * (maxL + 1) + 1, 0);
+        auto key = [&](const TileInfo& t) { return size_t(group_index(t.W)) * (maxL + 1) + size_t(maxL - t.L); };
+        for (const TileInfo& t : tiles) ++cnt[key(t) + 1];
+        for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
+        std::vector<size_t> perm(tiles.size());
+        for (size_t t = 0; t < tiles.size(); ++t) perm[size_t(cnt[key(tiles[t])]++)] = t;
+        std::vector<TileInfo> t2(tiles.size());
+        std::vector<int64_t> f2(tiles.size());
+        std::vector<int32_t> c2(tiles.size()), i2(tiles.size());
+        for (size_t k = 0; k < perm.size(); ++k) {
+            t2[k] = tiles[perm[k]];
+            f2[k] = tile_first[perm[k]];
+            c2[k] = tile_count[perm[k]];
+            i2[k] = tile_inst[perm[k]];
         }
         tiles.swap(t2);
-        tile_segs.swap(s2);
+        tile_first.swap(f2);
+        tile_count.swap(c2);
         tile_inst.swap(i2);
     }
     h->classes.clear();
     int64_t slot_base = 0, node_base = 0;
     for (size_t t = 0; t < tiles.size(); ++t) {
-        const int group = tiles[t].W <= 8 ? 0 : tiles[t].W;
+        const int group = tiles[t].W <= kFusedMaxW ? 0 : tiles[t].W;
         if (h->classes.empty() || h->classes.back().W != group) h->classes.push_back(WidthClass{group, int(t), int(t)});
         h->classes.back().tile_end = int(t) + 1;
         tiles[t].slot_base = slot_base;
@@ -301,6 +315,7 @@ int upload(disco_handle* h) {
         for (size_t t = 0; t < tiles.size(); ++t) inst_tiles[pos[tile_inst[t]]++] = int32_t(t);
     }
     const int64_t nslots = h->nslots();
+    tr.mark("tile order");
 
     pod_vector<uint32_t> hvar(slot_base), hdesc(slot_base);
     pod_vector<float> hlam(slot_base), hlam_lo(slot_base);
@@ -312,10 +327,11 @@ int upload(disco_handle* h) {
             std::fill(hdesc.begin() + b0, hdesc.begin() + b1, 0u);
             std::fill(hlam.begin() + b0, hlam.begin() + b1, 0.0f);
             std::fill(hlam_lo.begin() + b0, hlam_lo.begin() + b1, 0.0f);
-            for (size_t lane = 0; lane < tile_segs[t].size(); ++lane) {
-                const int32_t i = tile_segs[t][lane].inst;
+            for (int lane = 0; lane < tile_count[t]; ++lane) {
+                const TileSeg& ts = order[size_t(tile_first[t] + lane)];
+                const int32_t i = ts.inst;
                 const Plan& P = h->plans[i];
-                const Segment& sg = P.segs[tile_segs[t][lane].seg];
+                const Segment& sg = P.segs[ts.seg];
                 const uint32_t vb = uint32_t(h->var_base[i]);
                 const int64_t cb = h->slot_base[i];
                 for (int l = 0; l < sg.n_layers; ++l) {
@@ -338,6 +354,7 @@ int upload(disco_handle* h) {
         std::fill(var_inst.begin() + h->var_base[i], var_inst.begin() + h->var_base[i + 1], int32_t(i));
         consts[i] = h->plans[i].constant;
     }
+    tr.mark("tile layout");
     int rc;
     if ((rc = h->alloc(&h->tiles, h->ntiles))) return rc;
     if ((rc = h->alloc(&h->var, slot_base))) return rc;
@@ -366,6 +383,7 @@ int upload(disco_handle* h) {
     if ((rc = h->alloc(&h->var_inst, h->nint))) return rc;
     CK(cudaMallocHost(&h->h_counters, size_t(4 * std::max<int64_t>(ni, 1)) * sizeof(int)));
     CK(cudaMallocHost(&h->h_scalar, size_t(std::max<int64_t>(ni, 1)) * sizeof(double)));
+    tr.mark("allocations");
     cudaStream_t s = h->stream;
     if ((rc = copy_in(h->tiles, tiles.data(), tiles.size() * sizeof(TileInfo), s))) return rc;
     if ((rc = copy_in(h->var, hvar.data(), hvar.size() * 4, s))) return rc;
@@ -384,6 +402,7 @@ int upload(disco_handle* h) {
     CK(cudaMemsetAsync(h->acc[1], 0, size_t(h->nint) * kAccStride * 4, s));
     CK(cudaMemsetAsync(h->state, 0, size_t(h->nint), s));
     CK(cudaStreamSynchronize(s));
+    tr.mark("copies");
     return DISCO_OK;
 }
 
@@ -395,14 +414,112 @@ int reset_b(disco_handle* h) {
     return DISCO_OK;
 }
 
+int plain_iteration(disco_handle* h) {
+    int rc;
+    if ((rc = h->pass(Pass::FwdMMA))) return rc;
+    if ((rc = h->pass(Pass::BwdMMA))) return rc;
+    ++h->iterations;
+    return DISCO_OK;
+}
+
+// Launch-geometry autotuner: every geometry runs the same per-lane arithmetic on the same
+// tiles, so the results do not depend on the choice and the timed iterations are ordinary
+// iterations. Each geometry runs kTrials iterations, timed with events on the handle's
+// stream; the fastest single iteration wins.
+constexpr int kGeometries[3] = {1, 2, 4};
+constexpr int kTrials = 2;
+
+int autotune(disco_handle* h, int* used) {
+    cudaEvent_t ev[2];
+    CK(cudaEventCreate(&ev[0]));
+    CK(cudaEventCreate(&ev[1]));
+    float best = 1e30f;
+    int best_g = h->geometry, rc = DISCO_OK;
+    for (int t = 0; t < kTrials && !rc; ++t)
+        for (int g : kGeometries) {
+            h->geometry = g;
+            cudaEventRecord(ev[0], h->stream);
+            if ((rc = plain_iteration(h))) break;
+            cudaEventRecord(ev[1], h->stream);
+            float ms = 0.0f;
+            if (cudaEventSynchronize(ev[1]) != cudaSuccess || cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess) {
+                rc = fail(DISCO_ERR_CUDA, "autotune: event timing failed");
+                break;
+            }
+            *used += 1;
+            if (ms < best) {
+                best = ms;
+                best_g = g;
+            }
+        }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    h->geometry = best_g;
+    h->tuned = true;
+    return rc;
+}
+
+// Captures opts.graph_iters iterations into one executable graph (kernels only).
+int capture_iterations(disco_handle* h) {
+    const int G = h->opts.graph_iters;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        h->graph_failed = true;
+        return DISCO_OK;
+    }
+    const int64_t before = g_launches.load();
+    const int cur0 = h->cur;
+    int rc = DISCO_OK;
+    for (int t = 0; t < G && !rc; ++t) {
+        rc = h->pass(Pass::FwdMMA);
+        if (!rc) rc = h->pass(Pass::BwdMMA);
+    }
+    const cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    const int64_t captured = g_launches.load() - before;
+    g_launches.fetch_sub(captured);  // recorded, not run
+    h->cur = cur0;
+    if (rc || e != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        h->graph_failed = true;
+        return DISCO_OK;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&h->iter_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        h->iter_graph = nullptr;
+        h->graph_failed = true;
+        return DISCO_OK;
+    }
+    h->graph_cur = cur0;
+    h->graph_launches = captured;
+    return DISCO_OK;
+}
+
 int run_iterations(disco_handle* h, int iters) {
     int rc;
     if (!h->has_b && (rc = reset_b(h))) return rc;
-    for (int t = 0; t < iters; ++t) {
-        if ((rc = h->pass(Pass::FwdMMA))) return rc;
-        if ((rc = h->pass(Pass::BwdMMA))) return rc;
-        ++h->iterations;
+    int t = 0;
+    if (!h->tuned && h->opts.autotune && iters >= kTrials * 3) {
+        int used = 0;
+        if ((rc = autotune(h, &used))) return rc;
+        t += used;
     }
+    const int G = h->opts.graph_iters;
+    if (G > 0 && !h->graph_failed && iters - t >= G) {
+        if (!h->iter_graph && (h->tuned || !h->opts.autotune) && (rc = capture_iterations(h))) return rc;
+        if (h->iter_graph && h->cur == h->graph_cur) {
+            for (; iters - t >= G; t += G) {
+                CK(cudaGraphLaunch(h->iter_graph, h->stream));
+                g_launches.fetch_add(h->graph_launches, std::memory_order_relaxed);
+                h->iterations += G;
+            }
+        }
+    }
+    for (; t < iters; ++t)
+        if ((rc = plain_iteration(h))) return rc;
     return DISCO_OK;
 }
 
@@ -460,6 +577,8 @@ int disco_default_opts(disco_opts* o) {
     o->stream = nullptr;
     o->host_threads = 0;
     o->split_max_segments = 8;
+    o->graph_iters = 10;
+    o->autotune = 1;
     return DISCO_OK;
 }
 
@@ -562,7 +681,8 @@ int build_handle(int32_t n, const disco_mesh* X, const disco_mesh* Y, const floa
         if (!X[i].T || !Y[i].T || !d[i]) return fail(DISCO_ERR_INVALID_ARG, "build: null mesh or cost array");
     disco_opts o;
     if (opts) o = *opts; else disco_default_opts(&o);
-    if (!(o.omega > 0.0f && o.omega <= 1.0f) || o.split_chunk < 0 || o.split_max_segments < 0 || o.lb_every < 1)
+    if (!(o.omega > 0.0f && o.omega <= 1.0f) || o.split_chunk < 0 || o.split_max_segments < 0 || o.lb_every < 1 ||
+        o.graph_iters < 0)
         return fail(DISCO_ERR_INVALID_ARG, "build: bad options");
     std::unique_ptr<disco_handle> h(new disco_handle());
     h->device = o.device;
@@ -949,6 +1069,7 @@ int disco_info(disco_handle* h, disco_info_t* info) {
     info->device_bytes = h->device_bytes;
     info->iterations = h->iterations;
     info->upload_ms = h->upload_ms;
+    info->launch_geometry = h->geometry;
     // per iteration: 8 B per node and 20 B per slot per half-pass, 8 B per variable for the averaging
     info->bytes_per_iter = 2 * (8 * info->nnodes + 20 * info->nslots + 8 * (info->nvars_free + info->nvars_aux));
     return DISCO_OK;

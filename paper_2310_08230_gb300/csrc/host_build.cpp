@@ -330,18 +330,6 @@ struct RowChunk {
     int rc = 0;
 };
 
-// Phase timer: with DISCO_TRACE set in the environment, each phase's wall time goes to stderr.
-struct Trace {
-    bool on = std::getenv("DISCO_TRACE") != nullptr;
-    std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
-    void mark(const char* phase) {
-        if (!on) return;
-        const auto n = std::chrono::steady_clock::now();
-        std::fprintf(stderr, "disco build %-22s %8.2f ms\n", phase, std::chrono::duration<double, std::milli>(n - t).count());
-        t = n;
-    }
-};
-
 }  // namespace
 
 int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8_t* mask, int split_chunk,

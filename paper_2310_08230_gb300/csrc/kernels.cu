@@ -28,6 +28,8 @@ namespace {
 
 constexpr float BIG = 1e30f;
 constexpr int kWarpsPerBlock = 2;
+// Resident warps per SM the fused half-pass kernels are compiled for (caps their registers).
+constexpr int kFusedWarpsPerSM = 24;
 
 struct Desc {
     int w, wn, d0, d1, one, rank, deg;
@@ -330,19 +332,20 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward(KArgs a) {
     forward_tile<W, MODE>(a, tile, ti, smem + (threadIdx.x >> 5) * ring_floats<W>());
 }
 
-// Width classes 2, 4, 6 and 8 in one launch (tiles ordered longest first), so that short
-// tiles fill the SMs around the long ones; every warp's ring is sized for width 8.
-template <int MODE>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward_fused(KArgs a) {
+// Width classes 2, 4 and 6 in one launch (tiles ordered longest first), so that short tiles
+// fill the SMs around the long ones; every warp's ring is sized for width kFusedMaxW.
+// WPB warps (tiles) per block; every geometry computes the same results.
+template <int MODE, int WPB>
+__global__ void __launch_bounds__(WPB * 32, kFusedWarpsPerSM / WPB) k_forward_fused(KArgs a) {
+    static_assert(kFusedMaxW == 6, "fused dispatch covers widths 2, 4, 6");
     extern __shared__ float smem[];
-    const int tile = a.tile0 + int(blockIdx.x) * kWarpsPerBlock + int(threadIdx.x >> 5);
+    const int tile = a.tile0 + int(blockIdx.x) * WPB + int(threadIdx.x >> 5);
     if (tile >= a.tile_end) return;
     const TileInfo ti = a.tiles[tile];
-    float* ring = smem + (threadIdx.x >> 5) * ring_floats<8>();
+    float* ring = smem + (threadIdx.x >> 5) * ring_floats<kFusedMaxW>();
     if (ti.W == 2) forward_tile<2, MODE>(a, tile, ti, ring);
     else if (ti.W == 4) forward_tile<4, MODE>(a, tile, ti, ring);
-    else if (ti.W == 6) forward_tile<6, MODE>(a, tile, ti, ring);
-    else forward_tile<8, MODE>(a, tile, ti, ring);
+    else forward_tile<6, MODE>(a, tile, ti, ring);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -462,17 +465,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_backward(KArgs a) {
     backward_tile<W, MODE>(a, ti, smem + (threadIdx.x >> 5) * ring_floats<W>());
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_backward_fused(KArgs a) {
+template <int MODE, int WPB>
+__global__ void __launch_bounds__(WPB * 32, kFusedWarpsPerSM / WPB) k_backward_fused(KArgs a) {
     extern __shared__ float smem[];
-    const int tile = a.tile0 + int(blockIdx.x) * kWarpsPerBlock + int(threadIdx.x >> 5);
+    const int tile = a.tile0 + int(blockIdx.x) * WPB + int(threadIdx.x >> 5);
     if (tile >= a.tile_end) return;
     const TileInfo ti = a.tiles[tile];
-    float* ring = smem + (threadIdx.x >> 5) * ring_floats<8>();
+    float* ring = smem + (threadIdx.x >> 5) * ring_floats<kFusedMaxW>();
     if (ti.W == 2) backward_tile<2, MODE>(a, ti, ring);
     else if (ti.W == 4) backward_tile<4, MODE>(a, ti, ring);
-    else if (ti.W == 6) backward_tile<6, MODE>(a, ti, ring);
-    else backward_tile<8, MODE>(a, ti, ring);
+    else backward_tile<6, MODE>(a, ti, ring);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -516,22 +518,45 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_supports(KArgs a) {
     }
 }
 
-cudaError_t launch_fused(Pass pass, const KArgs& a, cudaStream_t s) {
+template <int WPB>
+cudaError_t launch_fused_g(Pass pass, const KArgs& a, cudaStream_t s) {
     const int n = a.tile_end - a.tile0;
     if (n <= 0) return cudaSuccess;
-    const dim3 grid((n + kWarpsPerBlock - 1) / kWarpsPerBlock), block(kWarpsPerBlock * 32);
-    const size_t sm = size_t(kWarpsPerBlock) * ring_floats<8>() * sizeof(float);
+    const dim3 grid((n + WPB - 1) / WPB), block(WPB * 32);
+    const size_t sm = size_t(WPB) * ring_floats<kFusedMaxW>() * sizeof(float);
     switch (pass) {
-        case Pass::FwdMMA: k_forward_fused<0><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
-        case Pass::FwdMMARound: k_forward_fused<1><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
-        case Pass::Lb: k_forward_fused<2><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
-        case Pass::FwdMM: k_forward_fused<3><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
-        case Pass::BwdMMA: k_backward_fused<0><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
-        case Pass::BwdMMARound: k_backward_fused<1><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
-        case Pass::BwdMM: k_backward_fused<2><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
-        case Pass::BwdReset: k_backward_fused<3><<<grid, block, sm, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
-        case Pass::Supports: k_supports<8><<<grid, block, 0, s>>>(a); g_launches.fetch_add(1, std::memory_order_relaxed); break;
+        case Pass::FwdMMA: k_forward_fused<0, WPB><<<grid, block, sm, s>>>(a); break;
+        case Pass::BwdMMA: k_backward_fused<0, WPB><<<grid, block, sm, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
     }
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused(Pass pass, const KArgs& a, cudaStream_t s, int geometry) {
+    const int n = a.tile_end - a.tile0;
+    if (n <= 0) return cudaSuccess;
+    if (pass == Pass::FwdMMA || pass == Pass::BwdMMA) {
+        switch (geometry) {
+            case 1: return launch_fused_g<1>(pass, a, s);
+            case 4: return launch_fused_g<4>(pass, a, s);
+            default: return launch_fused_g<2>(pass, a, s);
+        }
+    }
+    constexpr int WPB = kWarpsPerBlock;
+    const dim3 grid((n + WPB - 1) / WPB), block(WPB * 32);
+    const size_t sm = size_t(WPB) * ring_floats<kFusedMaxW>() * sizeof(float);
+    switch (pass) {
+        case Pass::FwdMMARound: k_forward_fused<1, WPB><<<grid, block, sm, s>>>(a); break;
+        case Pass::Lb: k_forward_fused<2, WPB><<<grid, block, sm, s>>>(a); break;
+        case Pass::FwdMM: k_forward_fused<3, WPB><<<grid, block, sm, s>>>(a); break;
+        case Pass::BwdMMARound: k_backward_fused<1, WPB><<<grid, block, sm, s>>>(a); break;
+        case Pass::BwdMM: k_backward_fused<2, WPB><<<grid, block, sm, s>>>(a); break;
+        case Pass::BwdReset: k_backward_fused<3, WPB><<<grid, block, sm, s>>>(a); break;
+        case Pass::Supports: k_supports<kFusedMaxW><<<grid, block, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 
@@ -790,11 +815,9 @@ inline int grid_for(int64_t n, int block) {
 
 }  // namespace
 
-cudaError_t launch_pass(Pass pass, int W, const KArgs& a, cudaStream_t s) {
+cudaError_t launch_pass(Pass pass, int W, const KArgs& a, cudaStream_t s, int geometry) {
     switch (W) {
-        case 0: return launch_fused(pass, a, s);
-        case 2: return launch_w<2>(pass, a, s);
-        case 4: return launch_w<4>(pass, a, s);
+        case 0: return launch_fused(pass, a, s, geometry);
         case 8: return launch_w<8>(pass, a, s);
         case 16: return launch_w<16>(pass, a, s);
         case 32: return launch_w<32>(pass, a, s);

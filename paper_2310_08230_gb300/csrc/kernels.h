@@ -26,6 +26,9 @@ struct TileInfo {
 
 constexpr uint32_t kNoVar = 0xFFFFFFFFu;
 constexpr int kAccStride = 8;  // floats per variable in the averaging tables
+// Width classes up to kFusedMaxW share one launch (launch_pass with W = 0); wider classes
+// launch on their own.
+constexpr int kFusedMaxW = 6;
 enum : uint8_t { kFree = 0, kFix0 = 1, kFix1 = 2 };
 
 struct KArgs {
@@ -60,9 +63,11 @@ enum class Pass {
     Supports     // reachability under fixings, writes per-slot value supports
 };
 
-// Launches `pass` over the tiles [a.tile0, a.tile_end) of width class W (2, 4, 8, 16, 32);
-// W = 0: tiles of classes 2, 4, 6 and 8 mixed in one launch (each tile carries its class).
-cudaError_t launch_pass(Pass pass, int W, const KArgs& a, cudaStream_t s);
+// Launches `pass` over the tiles [a.tile0, a.tile_end) of width class W (8, 16, 32);
+// W = 0: tiles of classes 2, 4 and 6 mixed in one launch (each tile carries its class).
+// `geometry` (1, 2 or 4 warps per block) applies to the fused MMA half-passes; all
+// geometries give identical results.
+cudaError_t launch_pass(Pass pass, int W, const KArgs& a, cudaStream_t s, int geometry = 2);
 
 cudaError_t launch_sum_tiles(const double* tile_sum, int64_t n, double add, double* out, cudaStream_t s);
 cudaError_t launch_sum_instances(const double* tile_sum, const int32_t* ptr, const int32_t* tiles, const double* add,

@@ -2,7 +2,10 @@
 // store in disco.cu. See host_build.cpp for the passages each step follows.
 #pragma once
 
+#include <chrono>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <memory>
 #include <new>
 #include <string>
@@ -49,6 +52,20 @@ inline void parallel_chunks(int64_t n, int nch, F body) {
     }
     for (auto& th : pool) th.join();
 }
+
+// Phase timer: with DISCO_TRACE set in the environment, each phase's wall time goes to stderr.
+struct Trace {
+    const char* scope = "build";
+    bool on = std::getenv("DISCO_TRACE") != nullptr;
+    std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+    void mark(const char* phase) {
+        if (!on) return;
+        const auto n = std::chrono::steady_clock::now();
+        std::fprintf(stderr, "disco %-6s %-22s %8.2f ms\n", scope, phase,
+                     std::chrono::duration<double, std::milli>(n - t).count());
+        t = n;
+    }
+};
 
 // Widest BDD layer the device kernels accept (node states held in registers).
 constexpr int kMaxWidth = 32;

@@ -141,6 +141,34 @@ def test_state_roundtrip_and_dual_feasibility(torch):
     s2.close()
 
 
+@pytest.mark.parametrize("which,chunk", [("config1", 0), ("config2", 16)])
+def test_graph_replay_and_launch_geometries_are_bit_identical(torch, which, chunk):
+    """Plain launches with the default geometry, graph replay, and the autotuner (which runs
+    its trial iterations in every geometry) give bit-identical dual states."""
+    from paper_2310_08230_gb300 import _lib as L
+
+    inst, prob, d, allowed, fixed, dec = _oracle(which, chunk)
+    states = []
+    for kw in (dict(graph_iters=0, autotune=0), dict(graph_iters=10, autotune=0), dict(graph_iters=7, autotune=1)):
+        s = _solver(inst, d, allowed, split_chunk=chunk, **kw)
+        n0 = L.lib().disco_kernel_launches()
+        s.dual(6)   # autotune trials when enabled
+        s.dual(33)  # graph blocks plus a plain remainder
+        launched = L.lib().disco_kernel_launches() - n0
+        info = s.info()
+        assert info["iterations"] == 39
+        assert info["launch_geometry"] in (1, 2, 4)
+        assert launched >= 2 * 39  # every replayed kernel is counted
+        lam, pend = s.get_state()
+        states.append((lam, pend, s.lower_bound(), s.min_marginals()))
+        s.close()
+    for lam, pend, lb, mm in states[1:]:
+        np.testing.assert_array_equal(lam, states[0][0])
+        np.testing.assert_array_equal(pend, states[0][1])
+        assert lb == states[0][2]
+        np.testing.assert_array_equal(mm, states[0][3])
+
+
 def test_bound_is_monotone_and_below_primal(torch):
     inst, prob, d, allowed, fixed, dec = _oracle("config2", 0)
     s = _solver(inst, d, allowed)
