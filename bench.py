@@ -274,9 +274,98 @@ def gpu_arm(args):
     }
     if not args.no_batched:
         line["batched"] = batched_vs_single(torch)
+    if not args.no_differentiated:
+        line["differentiated"] = differentiated(torch)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line), flush=True)
+
+
+def differentiated(torch, n_pairs: int = 8, iters: int = 50, every: int = 10, fd_dirs: int = 2,
+                   eps: float = 1e-3) -> dict:
+    """Learned costs through the solver: 8 pairs of 1280-triangle icospheres, raw 128-d
+    features -> 2-layer MLP (128-256-64, ReLU) -> squared distances -> top-16 candidates
+    (held fixed) -> bound after 50 iterations; its gradient w.r.t. the MLP parameters by the
+    adjoint kernels (checkpoint every 10 iterations) against central differences."""
+    from paper_2310_08230_gb300.api import Solver, candidates
+    from paper_2310_08230_gb300.autograd import dual_bounds
+    from synth import instances as I
+
+    insts = I.config5(n_pairs)
+    params = [torch.tensor(p, device="cuda", requires_grad=True) for p in I.mlp_params()]
+    FX = [torch.from_numpy(i.FX).cuda() for i in insts]
+    FY = [torch.from_numpy(i.FY).cuda() for i in insts]
+    meshes = [(i.X.T, i.Y.T) for i in insts]
+
+    def mlp(F, ps):
+        W1, b1, W2, b2 = ps
+        return torch.relu(F @ W1.T + b1) @ W2.T + b2
+
+    def costs(ps):
+        out = []
+        for fx, fy in zip(FX, FY):
+            a, b = mlp(fx, ps), mlp(fy, ps)
+            out.append(((a[:, None, :] - b[None, :, :]) ** 2).sum(-1))
+        return out
+
+    with torch.no_grad():
+        masks = [candidates(d, 16, i.X.T, i.Y.T) for d, i in zip(costs(params), insts)]
+
+    def bounds_plain(ps):
+        with torch.no_grad():
+            ds = costs(ps)
+            s = Solver.batch([(TX, TY, d, m) for d, (TX, TY), m in zip(ds, meshes, masks)], normalize_costs=0)
+            s.dual(iters)
+            lbs = s.lower_bounds()
+            s.close()
+        return lbs
+
+    bounds_plain(params)  # warm-up (build caches, autotuner paths)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lbs = dual_bounds(costs(params), meshes, masks, iters, every, normalize_costs=0)
+    loss = lbs.sum()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    grads = [p.grad.detach().clone() for p in params]
+    # the plain single-instance path on the same pairs (no recording, no gradient)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    with torch.no_grad():
+        ds = costs(params)
+        plain = []
+        for d, (TX, TY), m in zip(ds, meshes, masks):
+            s = Solver(TX, TY, d, m, normalize_costs=0)
+            s.dual(iters)
+            plain.append(s.lower_bound())
+            s.close()
+    torch.cuda.synchronize()
+    t4 = time.perf_counter()
+    # central differences along random parameter directions
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    checks = []
+    for _ in range(fd_dirs):
+        v = [torch.randn(p.shape, device="cuda", generator=gen) for p in params]
+        nrm = torch.sqrt(sum((x * x).sum() for x in v))
+        v = [x / nrm for x in v]
+        with torch.no_grad():
+            up = bounds_plain([p + eps * x for p, x in zip(params, v)]).sum()
+            dn = bounds_plain([p - eps * x for p, x in zip(params, v)]).sum()
+        fd = (up - dn) / (2 * eps)
+        an = float(sum((g * x).sum() for g, x in zip(grads, v)))
+        checks.append({"fd": float(fd), "adjoint": an, "rel_err": abs(float(fd) - an) / max(abs(an), 1e-12)})
+    return {
+        "pairs": n_pairs, "iters": iters, "checkpoint_every": every, "mlp": "128-256-64 relu",
+        "params": int(sum(p.numel() for p in params)),
+        "bound_sum": float(loss), "plain_bound_sum": float(np.sum(plain)),
+        "fwd_ms": (t1 - t0) * 1e3, "bwd_ms": (t2 - t1) * 1e3,
+        "plain_one_by_one_ms": (t4 - t3) * 1e3,
+        "fd_eps": eps, "fd_checks": checks,
+        "note": "times include the host compiler; fd = central differences of the plain batched solve, masks fixed",
+    }
 
 
 def batched_vs_single(torch, iters: int = 300, n_pairs: int = 64, split_chunk: int = 32) -> dict:
@@ -443,6 +532,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-differentiated", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

@@ -81,7 +81,10 @@ typedef struct {
                                  first dual iterations and keep the fastest; every geometry gives
                                  bit-identical results, so the trial iterations count as normal
                                  iterations. 0 = the default geometry. */
-    int32_t reserved[4];
+    int32_t normalize_costs;  /* [1] divide the element costs by the largest one (c in [0, 1]);
+                                 0 = raw means of the three pair costs (then the bound is linear
+                                 in the pair costs' scale) */
+    int32_t reserved[3];
 } disco_opts;
 
 typedef struct {
@@ -243,6 +246,29 @@ int disco_set_state(disco_handle *h, const float *lam, int64_t n, const float *p
 
 /* Problem and store statistics. */
 int disco_info(disco_handle *h, disco_info_t *info);
+
+/* Differentiation of the dual bound (the bound after T iterations of Eq. D's first-order
+ * method, Alg. 1 "MMA", is a piecewise linear function of the costs; this gives its gradient
+ * wherever it is differentiable, and a subgradient choice at ties).
+ *
+ * disco_record: restarts the dual at lambda^0 = c / |J| (pend = 0, b from one backward
+ * pass), runs `iters` iterations (as disco_dual would) and keeps a copy of the dual state
+ * every `checkpoint_every` iterations on the device (lambda, the averaging sectors and the
+ * backward node costs: about 8 B per slot + 32 B per variable + 4 B per node each).
+ * Errors: DISCO_ERR_INVALID_ARG for iters < 0 or checkpoint_every < 1, DISCO_ERR_OOM. */
+int disco_record(disco_handle *h, int32_t iters, int32_t checkpoint_every);
+
+/* d(bound after the recorded iterations) / d(pair costs), by reverse mode through the
+ * recorded iterations: every block of checkpoint_every iterations is replayed from its
+ * checkpoint recording each half-pass's inputs (2 * checkpoint_every copies of the state),
+ * then each half-pass is recomputed and reversed by an adjoint kernel. Out: for every
+ * instance nvx * nvy floats (row-major, the layout of disco_build's pair costs),
+ * concatenated over a batch; host or device pointer, n >= that count. The bound includes
+ * the presolve constant (gradient 1 for elements fixed to 1) and, with normalize_costs,
+ * the dependence on the largest element cost. The candidate mask and presolve are held
+ * fixed. The handle's state is left at the recorded final state. Synchronises.
+ * Errors: DISCO_ERR_INVALID_ARG (no record, output too small), DISCO_ERR_OOM. */
+int disco_grad(disco_handle *h, float *dlb_dpair_costs, int64_t n);
 
 /* Releases the handle (NULL is allowed). A handle built on a caller's stream must be freed
  * before that stream is destroyed (its device memory is returned on that stream). */

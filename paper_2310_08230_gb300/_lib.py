@@ -36,8 +36,8 @@ class disco_opts(ctypes.Structure):
         ("perturb_delta0", ctypes.c_float), ("perturb_growth", ctypes.c_float), ("tie_tau", ctypes.c_float),
         ("propagate_limit", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
         ("host_threads", ctypes.c_int32), ("split_max_segments", ctypes.c_int32),
-        ("graph_iters", ctypes.c_int32), ("autotune", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("graph_iters", ctypes.c_int32), ("autotune", ctypes.c_int32), ("normalize_costs", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -80,6 +80,8 @@ SIGNATURES = {
     "disco_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "disco_last_error": (ctypes.c_char_p, []),
     "disco_kernel_launches": (ctypes.c_int64, []),
+    "disco_record": (ctypes.c_int, [P, I32, I32]),
+    "disco_grad": (ctypes.c_int, [P, P, I64]),
 }
 
 _lib = None

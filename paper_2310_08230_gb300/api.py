@@ -93,6 +93,7 @@ class Solver:
                                     None if allowed is None else _ptr(allowed), ctypes.byref(self.opts),
                                     ctypes.byref(h)), "disco_build")
         self.h = h
+        self._sizes = [(nvx, nvy)]
 
     # -------------------------------------------------------------------------------
     def info(self) -> dict:
@@ -147,6 +148,23 @@ class Solver:
                                         None if pp is None else pp.ctypes.data, 0 if pp is None else pp.shape[0]),
                 "disco_set_state")
 
+    def record(self, iters: int, checkpoint_every: int = 10) -> None:
+        """Restart at lambda^0 and run `iters` iterations keeping checkpoints for grad()."""
+        L.check(L.lib().disco_record(self.h, int(iters), int(checkpoint_every)), "disco_record")
+
+    def grad(self, out=None):
+        """d(bound after the recorded iterations) / d(pair costs): (nvx, nvy) per instance,
+        concatenated (float32; NumPy array, or `out`, a host or device buffer)."""
+        n = self.pair_cost_count()
+        if out is None:
+            out = np.empty(n, np.float32)
+        L.check(L.lib().disco_grad(self.h, _ptr(out), int(out.numel() if hasattr(out, "numel") else out.size)),
+                "disco_grad")
+        return out
+
+    def pair_cost_count(self) -> int:
+        return sum(a * b for a, b in self._sizes)
+
     @classmethod
     def batch(cls, pairs, **opts) -> "Solver":
         """One handle over several pairs: ``pairs`` = [(TX, TY, d, allowed_or_None), ...]."""
@@ -176,6 +194,7 @@ class Solver:
                                           ctypes.byref(h)), "disco_build_batch")
         self.h = h
         self._keep = keep
+        self._sizes = [(int(p[2].shape[0]), int(p[2].shape[1])) for p in pairs]
         return self
 
     def batch_size(self) -> int:

@@ -97,6 +97,8 @@ struct disco_handle {
     uint32_t* desc = nullptr;
     float* lam = nullptr;
     float* lam_lo = nullptr;
+    float* lam0 = nullptr;         // lambda^0 (high / low), the start of disco_record
+    float* lam0_lo = nullptr;
     float* F = nullptr;
     float* B = nullptr;
     float* acc[2] = {nullptr, nullptr};
@@ -133,6 +135,22 @@ struct disco_handle {
     int graph_cur = 0;             // averaging-buffer parity the graph was captured at
     int64_t graph_launches = 0;    // kernels in one replay
     bool graph_failed = false;     // the stream could not be captured: launch plainly
+    // ---- differentiation (disco_record / disco_grad)
+    struct Snap {  // the dual state at an iteration boundary, or the inputs of one half-pass
+        float* lam = nullptr;
+        float* lam_lo = nullptr;
+        float* acc = nullptr;      // averaging sectors the next pass reads
+        float* nodes = nullptr;    // node costs of the other direction
+        int cur = 0;               // which averaging buffer they belong to
+    };
+    std::vector<Snap> checkpoints, tape;
+    Snap final_state;
+    int32_t rec_iters = -1, rec_every = 0;
+    float* lbar = nullptr;         // adjoint per slot
+    float* mub[2] = {nullptr, nullptr};  // adjoint sectors of the deferred means
+    float* Fbar = nullptr;         // adjoints of the stored node costs
+    float* Bbar = nullptr;
+    float* cbar = nullptr;         // adjoint per internal variable
 
     template <class T>
     int alloc(T** p, int64_t n) {
@@ -361,6 +379,8 @@ int upload(disco_handle* h) {
     if ((rc = h->alloc(&h->desc, slot_base))) return rc;
     if ((rc = h->alloc(&h->lam, slot_base))) return rc;
     if ((rc = h->alloc(&h->lam_lo, slot_base))) return rc;
+    if ((rc = h->alloc(&h->lam0, slot_base))) return rc;
+    if ((rc = h->alloc(&h->lam0_lo, slot_base))) return rc;
     if ((rc = h->alloc(&h->F, node_base))) return rc;
     if ((rc = h->alloc(&h->B, node_base))) return rc;
     if ((rc = h->alloc(&h->acc[0], h->nint * kAccStride))) return rc;
@@ -390,6 +410,8 @@ int upload(disco_handle* h) {
     if ((rc = copy_in(h->desc, hdesc.data(), hdesc.size() * 4, s))) return rc;
     if ((rc = copy_in(h->lam, hlam.data(), hlam.size() * 4, s))) return rc;
     if ((rc = copy_in(h->lam_lo, hlam_lo.data(), hlam_lo.size() * 4, s))) return rc;
+    CK(cudaMemcpyAsync(h->lam0, h->lam, size_t(slot_base) * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(h->lam0_lo, h->lam_lo, size_t(slot_base) * 4, cudaMemcpyDeviceToDevice, s));
     if ((rc = copy_in(h->canon_pos, canon.data(), canon.size() * 8, s))) return rc;
     if ((rc = copy_in(h->deg, deg.data(), deg.size(), s))) return rc;
     if ((rc = copy_in(h->var_inst, var_inst.data(), var_inst.size() * 4, s))) return rc;
@@ -579,6 +601,7 @@ int disco_default_opts(disco_opts* o) {
     o->split_max_segments = 8;
     o->graph_iters = 10;
     o->autotune = 1;
+    o->normalize_costs = 1;
     return DISCO_OK;
 }
 
@@ -714,8 +737,7 @@ int build_handle(int32_t n, const disco_mesh* X, const disco_mesh* Y, const floa
         for (int64_t i = i0; i < i1; ++i)
             rcs[i] = build_plan(MeshIn{X[i].nv, X[i].nt, X[i].T}, MeshIn{Y[i].nv, Y[i].nt, Y[i].T}, hd[i].data(),
                                 (allowed && allowed[i]) ? ha[i].data() : nullptr, o.split_chunk, o.split_max_segments,
-                                inner, &h->plans[i],
-                                &errs[i]);
+                                inner, &h->plans[i], &errs[i], o.normalize_costs != 0);
     });
     for (int32_t i = 0; i < n; ++i)
         if (rcs[i]) return fail(rcs[i], "build: instance " + std::to_string(i) + ": " + errs[i]);
@@ -1073,6 +1095,209 @@ int disco_info(disco_handle* h, disco_info_t* info) {
     // per iteration: 8 B per node and 20 B per slot per half-pass, 8 B per variable for the averaging
     info->bytes_per_iter = 2 * (8 * info->nnodes + 20 * info->nslots + 8 * (info->nvars_free + info->nvars_aux));
     return DISCO_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Differentiation: the bound after T iterations from lambda^0 = c / |J| as a function of the
+// pair costs. disco_record runs the iterations keeping a checkpoint every few iterations;
+// disco_grad replays each block from its checkpoint recording every half-pass's inputs,
+// then walks the passes backwards: each is recomputed by its normal kernel (bit-identical
+// mins) and reversed by its adjoint kernel (adjoint.cu).
+namespace {
+
+using Snap = disco_handle::Snap;
+
+int alloc_snap(disco_handle* h, Snap* s) {
+    if (s->lam) return DISCO_OK;
+    int rc;
+    if ((rc = h->alloc(&s->lam, h->nslots_tile))) return rc;
+    if ((rc = h->alloc(&s->lam_lo, h->nslots_tile))) return rc;
+    if ((rc = h->alloc(&s->acc, h->nint * kAccStride))) return rc;
+    if ((rc = h->alloc(&s->nodes, h->nnodes_tile))) return rc;
+    return DISCO_OK;
+}
+
+int d2d(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s));
+    return DISCO_OK;
+}
+
+// Saves lambda, the averaging sectors the next pass reads and the given node costs.
+int save_snap(disco_handle* h, Snap* s, const float* nodes) {
+    int rc;
+    const size_t ns = size_t(h->nslots_tile) * 4, na = size_t(h->nint) * kAccStride * 4, nn = size_t(h->nnodes_tile) * 4;
+    if ((rc = d2d(s->lam, h->lam, ns, h->stream)) || (rc = d2d(s->lam_lo, h->lam_lo, ns, h->stream)) ||
+        (rc = d2d(s->acc, h->acc[h->cur], na, h->stream)) || (rc = d2d(s->nodes, nodes, nn, h->stream)))
+        return rc;
+    s->cur = h->cur;
+    return DISCO_OK;
+}
+
+int load_snap(disco_handle* h, const Snap& s, float* nodes) {
+    int rc;
+    const size_t ns = size_t(h->nslots_tile) * 4, na = size_t(h->nint) * kAccStride * 4, nn = size_t(h->nnodes_tile) * 4;
+    if ((rc = d2d(h->lam, s.lam, ns, h->stream)) || (rc = d2d(h->lam_lo, s.lam_lo, ns, h->stream)) ||
+        (rc = d2d(h->acc[s.cur], s.acc, na, h->stream)) || (rc = d2d(nodes, s.nodes, nn, h->stream)))
+        return rc;
+    h->cur = s.cur;
+    return DISCO_OK;
+}
+
+AdjArgs adj_args(disco_handle* h) {
+    AdjArgs a{};
+    a.tiles = h->tiles;
+    a.ntiles = int32_t(h->ntiles);
+    a.var = h->var;
+    a.desc = h->desc;
+    a.lbar = h->lbar;
+    a.omega = h->opts.omega;
+    return a;
+}
+
+int64_t pair_cost_count(const disco_handle* h) {
+    int64_t n = 0;
+    for (const Plan& P : h->plans) n += int64_t(P.nvx) * P.nvy;
+    return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+int disco_record(disco_handle* h, int32_t iters, int32_t checkpoint_every) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (iters < 0 || checkpoint_every < 1) return fail(DISCO_ERR_INVALID_ARG, "record: iters < 0 or checkpoint_every < 1");
+    const int nck = std::max(1, (iters + checkpoint_every - 1) / checkpoint_every);
+    h->checkpoints.resize(size_t(std::max<size_t>(h->checkpoints.size(), size_t(nck))));
+    for (int k = 0; k < nck; ++k)
+        if ((rc = alloc_snap(h, &h->checkpoints[k]))) return rc;
+    cudaStream_t s = h->stream;
+    const size_t ns = size_t(h->nslots_tile) * 4;
+    if ((rc = d2d(h->lam, h->lam0, ns, s)) || (rc = d2d(h->lam_lo, h->lam0_lo, ns, s))) return rc;
+    CK(cudaMemsetAsync(h->acc[0], 0, size_t(h->nint) * kAccStride * 4, s));
+    CK(cudaMemsetAsync(h->acc[1], 0, size_t(h->nint) * kAccStride * 4, s));
+    CK(cudaMemsetAsync(h->state, 0, size_t(h->nint), s));
+    h->cur = 0;
+    h->iterations = 0;
+    if ((rc = reset_b(h))) return rc;
+    for (int k = 0; k < nck; ++k) {
+        if ((rc = save_snap(h, &h->checkpoints[k], h->B))) return rc;
+        const int n = std::min(checkpoint_every, iters - k * checkpoint_every);
+        if (n > 0 && (rc = run_iterations(h, n))) return rc;
+    }
+    h->rec_iters = iters;
+    h->rec_every = checkpoint_every;
+    CK(cudaStreamSynchronize(s));
+    return DISCO_OK;
+}
+
+int disco_grad(disco_handle* h, float* dlb_dpair_costs, int64_t n) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (h->rec_iters < 0) return fail(DISCO_ERR_INVALID_ARG, "grad: call disco_record first");
+    const int64_t need = pair_cost_count(h);
+    if (!dlb_dpair_costs || n < need) return fail(DISCO_ERR_INVALID_ARG, "grad: output too small");
+    const int T = h->rec_iters, G = h->rec_every;
+    const int nck = std::max(1, (T + G - 1) / G);
+    if (h->tape.size() < size_t(2 * G)) h->tape.resize(size_t(2 * G));
+    for (int e = 0; e < std::min(2 * G, 2 * T); ++e)
+        if ((rc = alloc_snap(h, &h->tape[e]))) return rc;
+    if ((rc = alloc_snap(h, &h->final_state))) return rc;
+    if (!h->lbar) {
+        if ((rc = h->alloc(&h->lbar, h->nslots_tile)) || (rc = h->alloc(&h->mub[0], h->nint * kAccStride)) ||
+            (rc = h->alloc(&h->mub[1], h->nint * kAccStride)) || (rc = h->alloc(&h->Fbar, h->nnodes_tile)) ||
+            (rc = h->alloc(&h->Bbar, h->nnodes_tile)) || (rc = h->alloc(&h->cbar, h->nint)))
+            return rc;
+    }
+    cudaStream_t s = h->stream;
+    if ((rc = save_snap(h, &h->final_state, h->B))) return rc;
+    CK(cudaMemsetAsync(h->lbar, 0, size_t(h->nslots_tile) * 4, s));
+    CK(cudaMemsetAsync(h->Fbar, 0, size_t(h->nnodes_tile) * 4, s));
+    CK(cudaMemsetAsync(h->Bbar, 0, size_t(h->nnodes_tile) * 4, s));
+    // the bound: forward min-sum on lambda + pend (recompute its node costs, then reverse)
+    if ((rc = h->pass(Pass::FwdMM))) return rc;
+    {
+        AdjArgs a = adj_args(h);
+        a.lam_in = h->lam;
+        a.lam_in_lo = h->lam_lo;
+        a.acc_in = h->acc[h->cur];
+        a.own = h->F;
+        a.mubar_out = h->mub[0];
+        CK(launch_adjoint(Adj::Bound, a, s));
+    }
+    int nx = 0;  // mub[nx]: adjoint of the deferred means the pass being reversed produced
+    for (int k = nck - 1; k >= 0; --k) {
+        if ((rc = load_snap(h, h->checkpoints[k], h->B))) return rc;
+        const int nit = std::min(G, T - k * G);
+        for (int t = 0; t < nit; ++t)
+            for (int dir = 0; dir < 2; ++dir) {
+                if ((rc = save_snap(h, &h->tape[2 * t + dir], dir == 0 ? h->B : h->F))) return rc;
+                if ((rc = h->pass(dir == 0 ? Pass::FwdMMA : Pass::BwdMMA))) return rc;
+            }
+        for (int e = 2 * nit - 1; e >= 0; --e) {
+            const Snap& tp = h->tape[e];
+            const bool fwd = (e % 2) == 0;
+            if ((rc = load_snap(h, tp, fwd ? h->B : h->F))) return rc;
+            if ((rc = h->pass(fwd ? Pass::FwdMMA : Pass::BwdMMA))) return rc;  // recompute
+            AdjArgs a = adj_args(h);
+            a.lam_in = tp.lam;
+            a.lam_in_lo = tp.lam_lo;
+            a.acc_in = tp.acc;
+            a.other = tp.nodes;
+            a.own = fwd ? h->F : h->B;
+            a.own_bar = fwd ? h->Fbar : h->Bbar;
+            a.other_bar = fwd ? h->Bbar : h->Fbar;
+            a.mubar_next = h->mub[nx];
+            a.mubar_out = h->mub[nx ^ 1];
+            CK(launch_adjoint(fwd ? Adj::Fwd : Adj::Bwd, a, s));
+            nx ^= 1;
+        }
+    }
+    // the initial backward min-sum on lambda^0
+    {
+        const Snap& c0 = h->checkpoints[0];
+        if ((rc = load_snap(h, c0, h->B))) return rc;
+        if ((rc = h->pass(Pass::BwdReset))) return rc;
+        AdjArgs a = adj_args(h);
+        a.lam_in = c0.lam;
+        a.lam_in_lo = c0.lam_lo;
+        a.acc_in = c0.acc;
+        a.own = h->B;
+        a.own_bar = h->Bbar;
+        CK(launch_adjoint(Adj::Reset, a, s));
+    }
+    CK(launch_adj_cost(h->var, h->desc, h->nslots_tile, h->lbar, h->deg, h->nint, h->mub[nx ^ 1], h->cbar, s));
+    if ((rc = load_snap(h, h->final_state, h->B))) return rc;
+    h->has_b = true;
+    std::vector<float> cb(static_cast<size_t>(h->nint));
+    CK(cudaMemcpyAsync(cb.data(), h->cbar, cb.size() * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // chain rule to the pair costs: c_e = (mean of e's three pair costs) / scale
+    std::vector<float> g(static_cast<size_t>(need), 0.0f);
+    int64_t off = 0;
+    for (size_t i = 0; i < h->plans.size(); ++i) {
+        const Plan& P = h->plans[i];
+        std::vector<double> ge(static_cast<size_t>(P.nvars), 0.0);
+        for (int64_t u = 0; u < P.n_free; ++u) ge[size_t(P.free_orig[u])] = cb[size_t(h->var_base[i] + u)];
+        double cc = 0.0;
+        for (int64_t e = 0; e < P.nvars; ++e) {
+            if (P.fixed[e] == 1) ge[e] = 1.0;
+            cc += ge[e] * P.cost[e];
+        }
+        std::vector<double> gp(static_cast<size_t>(P.nvx) * P.nvy, 0.0);
+        for (int64_t e = 0; e < P.nvars; ++e) {
+            double gr = ge[e] / P.cost_scale;
+            if (e == P.cost_scale_elem) gr -= cc / P.cost_scale;
+            if (gr == 0.0) continue;
+            for (int v = 0; v < 3; ++v) gp[size_t(P.vm[3 * e + v]) * P.nvy + P.vn[3 * e + v]] += gr / 3.0;
+        }
+        for (size_t q = 0; q < gp.size(); ++q) g[size_t(off) + q] = float(gp[q]);
+        off += int64_t(P.nvx) * P.nvy;
+    }
+    return write_out(dlb_dpair_costs, g.data(), g.size() * 4, s);
 }
 
 void disco_free(disco_handle* h) {

@@ -333,7 +333,7 @@ struct RowChunk {
 }  // namespace
 
 int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8_t* mask, int split_chunk,
-               int split_max_segments, int threads, Plan* P, std::string* err) {
+               int split_max_segments, int threads, Plan* P, std::string* err, bool normalize) {
     auto t0 = std::chrono::steady_clock::now();
     Trace tr;
     if (threads <= 0) threads = std::max(1u, std::thread::hardware_concurrency());
@@ -411,9 +411,16 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         for (int c = 0; c < nth; ++c)
             if (bad[c]) { *err = "pair costs must be finite and >= 0"; return DISCO_ERR_INVALID_ARG; }
         const double cmax = *std::max_element(cmaxs.begin(), cmaxs.end());
-        if (cmax > 0) parallel_chunks(nv, nth, [&](int, int64_t lo, int64_t hi) {
-            for (int64_t i = lo; i < hi; ++i) P->cost[i] /= cmax;
-        });
+        P->cost_scale = 1.0;
+        P->cost_scale_elem = -1;
+        if (normalize && cmax > 0) {
+            P->cost_scale = cmax;
+            for (int64_t i = 0; i < nv; ++i)
+                if (P->cost[i] == cmax) { P->cost_scale_elem = i; break; }
+            parallel_chunks(nv, nth, [&](int, int64_t lo, int64_t hi) {
+                for (int64_t i = lo; i < hi; ++i) P->cost[i] /= cmax;
+            });
+        }
     }
 
     tr.mark("costs");

@@ -51,6 +51,43 @@ struct KArgs {
     uint8_t* sup_var;                // kAccStride per variable
 };
 
+// Arguments of the adjoint kernels (adjoint.cu). A pass's inputs come from the tape (the
+// values the pass read when it ran), its own-direction node costs from a recomputation by
+// the normal kernel; adjoints: lbar per slot (in: of lambda after the pass; out: of lambda
+// before it), mubar per variable and rank (sectors like the averaging tables; next = the
+// adjoint of the deferred means this pass produced, out = of those it read), node-array
+// adjoints own_bar (of the costs this pass stored, read) and other_bar (of the costs it read
+// from the previous pass, written).
+struct AdjArgs {
+    const TileInfo* tiles;
+    int32_t ntiles;
+    const uint32_t* var;
+    const uint32_t* desc;
+    const float* lam_in;
+    const float* lam_in_lo;
+    const float* acc_in;
+    const float* other;     // node costs the pass read (B forward, F backward)
+    const float* own;       // node costs the pass stored (recomputed)
+    const float* own_bar;   // adjoint of `own` (from the following pass); may be null = 0
+    float* other_bar;       // adjoint of `other` (for the preceding pass)
+    float* lbar;
+    const float* mubar_next;
+    float* mubar_out;
+    float omega;
+};
+
+enum class Adj {
+    Fwd,    // forward MMA half-pass
+    Bwd,    // backward MMA half-pass
+    Bound,  // final bound: forward min-sum on lambda + pend (lbar, mubar_out written)
+    Reset,  // initial backward min-sum on lambda (lbar accumulated)
+};
+
+cudaError_t launch_adjoint(Adj kind, const AdjArgs& a, cudaStream_t s);
+// cbar[v] = (sum over v's slots of lbar) / deg[v], via a rank-sector table (tab).
+cudaError_t launch_adj_cost(const uint32_t* var, const uint32_t* desc, int64_t nslots, const float* lbar,
+                            const uint8_t* deg, int64_t nint, float* tab, float* cbar, cudaStream_t s);
+
 enum class Pass {
     FwdMMA,      // forward half-pass with updates, stores F
     BwdMMA,      // backward half-pass with updates, stores B

@@ -98,7 +98,9 @@ struct Plan {
     int32_t nvx = 0, nvy = 0;
     int64_t nvars = 0, nrows = 0, n_closed = 0, n_projx = 0, n_projy = 0;
     pod_vector<int32_t> vm, vn;         // 3 per variable: X / Y vertex of each corner
-    pod_vector<double> cost;            // normalised c_p per variable
+    pod_vector<double> cost;            // c_p per variable (normalised unless disabled)
+    double cost_scale = 1.0;            // c_p = (mean of its pair costs) / cost_scale
+    int64_t cost_scale_elem = -1;       // the element whose raw cost is cost_scale (normalised)
     pod_vector<int64_t> row_ptr;        // rows: closedness, X projection, Y projection
     pod_vector<int32_t> row_var;
     pod_vector<int8_t> row_coef;
@@ -127,7 +129,10 @@ struct MeshIn {
 };
 
 // Returns 0 or a negative DISCO_ERR_* code (err receives a message).
+// normalize: divide the element costs by the largest one (c in [0, 1]); otherwise the
+// element costs are the raw means of their three pair costs.
 int build_plan(const MeshIn& X, const MeshIn& Y, const float* d, const uint8_t* allowed,
-               int split_chunk, int split_max_segments, int threads, Plan* out, std::string* err);
+               int split_chunk, int split_max_segments, int threads, Plan* out, std::string* err,
+               bool normalize = true);
 
 }  // namespace disco

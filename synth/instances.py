@@ -117,4 +117,27 @@ def config4(n_pairs: int = 64) -> list[Instance]:
     return out
 
 
+def config5(n_pairs: int = 8, subdiv: int = 3) -> list[Instance]:
+    """Pairs for the differentiated solve: icosphere X (subdivision 3: 1280 triangles)
+    against a deformed, relabelled copy; raw 128-d N(0, 1) features (Y: permuted + N(0,
+    0.05^2)) that a learned map turns into costs; top-16 candidates; 50 iterations."""
+    out = []
+    for p in range(n_pairs):
+        rng = _rng(5 ^ p)
+        X = M.icosphere(subdiv)
+        Y, FX, FY, perm = make_pair(X, rng, 128, 0.05, deform=True)
+        out.append(Instance(f"diff{p}-{X.nt}T-top16", X, Y, FX, FY, perm, 16, 50))
+    return out
+
+
+def mlp_params(seed: int = 5, sizes=(128, 256, 64)) -> list[np.ndarray]:
+    """Seeded weights of the 2-layer feature MLP (W1, b1, W2, b2; N(0, 1/fan_in), zero bias)."""
+    rng = _rng(1000 + seed)
+    out = []
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        out.append((rng.standard_normal((b, a)) / np.sqrt(a)).astype(np.float32))
+        out.append(np.zeros(b, np.float32))
+    return out
+
+
 CONFIGS = {"config1": config1, "config2": config2, "config3": config3, "tet": tet}
