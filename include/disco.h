@@ -84,7 +84,10 @@ typedef struct {
     int32_t normalize_costs;  /* [1] divide the element costs by the largest one (c in [0, 1]);
                                  0 = raw means of the three pair costs (then the bound is linear
                                  in the pair costs' scale) */
-    int32_t reserved[3];
+    int32_t qn_memory;        /* [0] disco_converge interleaves quasi-Newton steps (Alg. 1) with
+                                 its lb_every MMA iterations, keeping this many L-BFGS pairs;
+                                 0 = MMA only */
+    int32_t reserved[2];
 } disco_opts;
 
 typedef struct {
@@ -211,6 +214,17 @@ int disco_primal_batch(disco_handle *h, uint8_t *x_out, int64_t nvars, double *c
 /* Runs `iters` dual iterations (forward + backward half-pass of deferred min-marginal
  * averaging, Alg. 1 "MMA"). Asynchronous on the handle's stream. */
 int disco_dual(disco_handle *h, int32_t iters);
+
+/* Runs `calls` executions of the quasi-Newton powered iteration (Alg. 1): move the deferred
+ * means into lambda; subgradient g = per BDD the minimising assignment (per slot 1 iff its
+ * min-marginal difference is negative, App. A.5); direction H g by the L-BFGS two-loop
+ * recursion (Alg. 5) over the stored pairs, projected so that every variable's entries sum
+ * to 0 (Alg. 1, dual feasibility); step size by FindStepSize (Alg. 6, bound evaluations,
+ * the step is taken only if it raises the bound); then `mma_iters` MMA iterations; then
+ * the pair (s, y) enters the memory if s^T y >= 1e-8 (Alg. 4). Memory size: opts.qn_memory,
+ * or 5 if that is 0. The bound never decreases. Synchronises (the step search reads
+ * bounds on the host). Errors: DISCO_ERR_INVALID_ARG for negative counts, DISCO_ERR_OOM. */
+int disco_dual_qn(disco_handle *h, int32_t calls, int32_t mma_iters);
 
 /* Lower bound E(lambda + pend) + presolve constant of Eq. D, FP64 sum. Synchronises. */
 int disco_lower_bound(disco_handle *h, double *lb);

@@ -37,7 +37,7 @@ class disco_opts(ctypes.Structure):
         ("propagate_limit", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
         ("host_threads", ctypes.c_int32), ("split_max_segments", ctypes.c_int32),
         ("graph_iters", ctypes.c_int32), ("autotune", ctypes.c_int32), ("normalize_costs", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("qn_memory", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
     ]
 
 
@@ -82,6 +82,7 @@ SIGNATURES = {
     "disco_kernel_launches": (ctypes.c_int64, []),
     "disco_record": (ctypes.c_int, [P, I32, I32]),
     "disco_grad": (ctypes.c_int, [P, P, I64]),
+    "disco_dual_qn": (ctypes.c_int, [P, I32, I32]),
 }
 
 _lib = None

@@ -104,6 +104,10 @@ class Solver:
     def dual(self, iters: int) -> None:
         L.check(L.lib().disco_dual(self.h, int(iters)), "disco_dual")
 
+    def dual_qn(self, calls: int, mma_iters: int = 20) -> None:
+        """`calls` quasi-Newton powered iterations (Alg. 1), each with `mma_iters` MMA iterations."""
+        L.check(L.lib().disco_dual_qn(self.h, int(calls), int(mma_iters)), "disco_dual_qn")
+
     def lower_bound(self) -> float:
         lb = ctypes.c_double()
         L.check(L.lib().disco_lower_bound(self.h, ctypes.byref(lb)), "disco_lower_bound")

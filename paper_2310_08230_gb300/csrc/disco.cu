@@ -151,6 +151,24 @@ struct disco_handle {
     float* Fbar = nullptr;         // adjoints of the stored node costs
     float* Bbar = nullptr;
     float* cbar = nullptr;         // adjoint per internal variable
+    // ---- quasi-Newton steps (Alg. 1 with Alg. 4-6)
+    int qn_m = 0;                  // L-BFGS memory
+    float* qn_g = nullptr;         // subgradient at the start of a call
+    float* qn_g2 = nullptr;        // subgradient after its MMA iterations
+    float* qn_d = nullptr;         // direction
+    float* qn_old = nullptr;       // lambda at the start of a call (high / low)
+    float* qn_old_lo = nullptr;
+    float* qn_tr = nullptr;        // trial lambda + gamma d
+    float* qn_tr_lo = nullptr;
+    float* qn_tab = nullptr;       // rank sectors for the projection
+    std::vector<float*> qn_S, qn_Y;  // m + 1 buffers; qn_order lists the stored pairs, oldest first
+    std::vector<int> qn_order;
+    std::vector<double> qn_sy, qn_yy;
+    int qn_spare = 0;
+    double* qn_part = nullptr;     // per-block dot partials (device) and their pinned copy
+    double* qn_hpart = nullptr;
+    double qn_gamma = 1e-3, qn_dmin = 0.0, qn_Estart = 0.0;
+    int64_t qn_calls = 0;
 
     template <class T>
     int alloc(T** p, int64_t n) {
@@ -200,6 +218,7 @@ struct disco_handle {
         if (stream) cudaStreamSynchronize(stream);
         if (h_counters) cudaFreeHost(h_counters);
         if (h_scalar) cudaFreeHost(h_scalar);
+        if (qn_hpart) cudaFreeHost(qn_hpart);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -765,6 +784,154 @@ void fill_info(const Plan& P, disco_info_t* info) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------------------
+// Quasi-Newton powered MMA (Alg. 1; L-BFGS memory Alg. 4, direction Alg. 5, step size
+// Alg. 6). Readings, shared with the FP64 oracle: textbook L-BFGS on -E (y = g_k - g_{k+1},
+// curvature test s^T y >= eps), the second loop's beta uses the running direction,
+// FindStepSize starts from E_init = E(lambda), Delta_min = 1e-6 (E after the first call -
+// E at its start) and 0 during the first call; the step is taken only if it raised the
+// bound; eps = 1e-8, growth 1.1, shrink 0.8, K = 5 (the paper's values); first step 1e-3.
+namespace {
+
+constexpr double kQnEps = 1e-8, kQnGrow = 1.1, kQnShrink = 0.8;
+constexpr int kQnK = 5;
+
+int qn_init(disco_handle* h, int m) {
+    if (h->qn_g) return DISCO_OK;
+    h->qn_m = std::max(1, m);
+    const int64_t n = h->nslots_tile;
+    int rc;
+    for (float** p : {&h->qn_g, &h->qn_g2, &h->qn_d, &h->qn_old, &h->qn_old_lo, &h->qn_tr, &h->qn_tr_lo})
+        if ((rc = h->alloc(p, n))) return rc;
+    if ((rc = h->alloc(&h->qn_tab, h->nint * kAccStride))) return rc;
+    h->qn_S.assign(size_t(h->qn_m) + 1, nullptr);
+    h->qn_Y.assign(size_t(h->qn_m) + 1, nullptr);
+    for (int k = 0; k <= h->qn_m; ++k)
+        if ((rc = h->alloc(&h->qn_S[k], n)) || (rc = h->alloc(&h->qn_Y[k], n))) return rc;
+    h->qn_sy.assign(size_t(h->qn_m) + 1, 0.0);
+    h->qn_yy.assign(size_t(h->qn_m) + 1, 0.0);
+    h->qn_order.clear();
+    h->qn_spare = 0;
+    if ((rc = h->alloc(&h->qn_part, qn_dot_blocks()))) return rc;
+    CK(cudaMallocHost(&h->qn_hpart, size_t(qn_dot_blocks()) * sizeof(double)));
+    return DISCO_OK;
+}
+
+int qn_dot(disco_handle* h, const float* a, const float* b, double* out) {
+    CK(launch_qn_dot(a, b, h->nslots_tile, h->qn_part, h->stream));
+    CK(cudaMemcpyAsync(h->qn_hpart, h->qn_part, size_t(qn_dot_blocks()) * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    double x = 0.0;
+    for (int k = 0; k < qn_dot_blocks(); ++k) x += h->qn_hpart[k];
+    *out = x;
+    return DISCO_OK;
+}
+
+// Per slot: 1 iff every minimising assignment of its BDD (on lambda + pend) sets the variable.
+int qn_subgradient(disco_handle* h, float* g) {
+    int rc;
+    if ((rc = h->pass(Pass::FwdMM))) return rc;
+    if ((rc = h->pass(Pass::BwdMM))) return rc;
+    CK(launch_qn_sign(h->mm_slot, h->var, h->nslots_tile, g, h->stream));
+    return DISCO_OK;
+}
+
+// E(lambda + gamma d) + constant (pend is 0 during the step search).
+int qn_trial(disco_handle* h, double gamma, double* e) {
+    CK(launch_qn_step(h->lam, h->lam_lo, h->qn_d, float(gamma), h->var, h->nslots_tile, h->qn_tr, h->qn_tr_lo,
+                      h->stream));
+    std::swap(h->lam, h->qn_tr);
+    std::swap(h->lam_lo, h->qn_tr_lo);
+    const int rc = lower_bound(h, e);
+    std::swap(h->lam, h->qn_tr);
+    std::swap(h->lam_lo, h->qn_tr_lo);
+    return rc;
+}
+
+int qn_call(disco_handle* h, int mma_iters) {
+    int rc;
+    cudaStream_t s = h->stream;
+    const int64_t n = h->nslots_tile;
+    if ((rc = qn_init(h, h->opts.qn_memory > 0 ? h->opts.qn_memory : 5))) return rc;
+    // lambda <- lambda + pend
+    CK(launch_flush(h->var, h->desc, n, h->acc[h->cur], h->lam, h->lam_lo, s));
+    CK(cudaMemsetAsync(h->acc[h->cur], 0, size_t(h->nint) * kAccStride * 4, s));
+    double E0;
+    if ((rc = lower_bound(h, &E0))) return rc;
+    if (h->qn_calls == 0) h->qn_Estart = E0;
+    if ((rc = qn_subgradient(h, h->qn_g))) return rc;
+    // d = H g (two loops), then the dual-feasible projection
+    CK(cudaMemcpyAsync(h->qn_d, h->qn_g, size_t(n) * 4, cudaMemcpyDeviceToDevice, s));
+    const int np = int(h->qn_order.size());
+    std::vector<double> alpha(size_t(np), 0.0);
+    for (int k = np - 1; k >= 0; --k) {
+        const int b = h->qn_order[k];
+        double sd;
+        if ((rc = qn_dot(h, h->qn_S[b], h->qn_d, &sd))) return rc;
+        alpha[k] = sd / h->qn_sy[b];
+        CK(launch_qn_axpy(h->qn_d, float(-alpha[k]), h->qn_Y[b], n, s));
+    }
+    if (np > 0) {
+        const int b = h->qn_order.back();
+        CK(launch_qn_scale(h->qn_d, float(h->qn_sy[b] / h->qn_yy[b]), n, s));
+    }
+    for (int k = 0; k < np; ++k) {
+        const int b = h->qn_order[k];
+        double yd;
+        if ((rc = qn_dot(h, h->qn_Y[b], h->qn_d, &yd))) return rc;
+        CK(launch_qn_axpy(h->qn_d, float(alpha[k] - yd / h->qn_sy[b]), h->qn_S[b], n, s));
+    }
+    CK(launch_qn_project(h->qn_d, h->var, h->desc, n, h->qn_tab, s));
+    // step size (Alg. 6)
+    CK(cudaMemcpyAsync(h->qn_old, h->lam, size_t(n) * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(h->qn_old_lo, h->lam_lo, size_t(n) * 4, cudaMemcpyDeviceToDevice, s));
+    double gamma = h->qn_gamma, gm = gamma, Em, e;
+    if ((rc = qn_trial(h, gamma, &Em))) return rc;
+    e = Em;
+    for (int t = 0; t < kQnK; ++t) {
+        gamma *= e <= E0 ? kQnShrink : kQnGrow;
+        if ((rc = qn_trial(h, gamma, &e))) return rc;
+        if (e >= Em) {
+            gm = gamma;
+            Em = e;
+        }
+        if (e - E0 >= h->qn_dmin) break;
+    }
+    if (Em > E0) CK(launch_qn_step(h->lam, h->lam_lo, h->qn_d, float(gm), h->var, n, h->lam, h->lam_lo, s));
+    h->qn_gamma = gm;
+    h->has_b = false;
+    if ((rc = run_iterations(h, mma_iters))) return rc;
+    // L-BFGS memory (Alg. 4): s = lambda_new - lambda_old, y = g_old - g_new
+    if ((rc = qn_subgradient(h, h->qn_g2))) return rc;
+    const int b = h->qn_spare;
+    CK(launch_qn_delta(h->lam, h->lam_lo, h->acc[h->cur], h->qn_old, h->qn_old_lo, h->var, h->desc, n, h->qn_S[b], s));
+    CK(launch_qn_sub(h->qn_g, h->qn_g2, n, h->qn_Y[b], s));
+    double sy, yy;
+    if ((rc = qn_dot(h, h->qn_S[b], h->qn_Y[b], &sy))) return rc;
+    if (sy >= kQnEps) {
+        if ((rc = qn_dot(h, h->qn_Y[b], h->qn_Y[b], &yy))) return rc;
+        h->qn_sy[b] = sy;
+        h->qn_yy[b] = yy;
+        h->qn_order.push_back(b);
+        if (int(h->qn_order.size()) > h->qn_m) {
+            h->qn_spare = h->qn_order.front();
+            h->qn_order.erase(h->qn_order.begin());
+        } else {
+            h->qn_spare = int(h->qn_order.size());  // buffers 0..m are used in order at first
+        }
+    }
+    ++h->qn_calls;
+    if (h->qn_calls == 1) {
+        double lb;
+        if ((rc = lower_bound(h, &lb))) return rc;
+        h->qn_dmin = 1e-6 * (lb - h->qn_Estart);
+    }
+    return DISCO_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int disco_build(const disco_mesh* X, const disco_mesh* Y, const float* d, const uint8_t* allowed, const disco_opts* opts,
@@ -847,6 +1014,15 @@ int disco_dual(disco_handle* h, int32_t iters) {
     return run_iterations(h, iters);
 }
 
+int disco_dual_qn(disco_handle* h, int32_t calls, int32_t mma_iters) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (calls < 0 || mma_iters < 0) return fail(DISCO_ERR_INVALID_ARG, "dual_qn: calls < 0 or mma_iters < 0");
+    for (int c = 0; c < calls; ++c)
+        if ((rc = qn_call(h, mma_iters))) return rc;
+    return DISCO_OK;
+}
+
 int disco_lower_bound(disco_handle* h, double* lb) {
     int rc = check_handle(h);
     if (rc) return rc;
@@ -864,7 +1040,7 @@ int disco_converge(disco_handle* h, int32_t max_iters, int32_t* iters_done, doub
     bool converged = false;
     while (done < max_iters) {
         const int n = std::min(h->opts.lb_every, max_iters - done);
-        if ((rc = run_iterations(h, n))) return rc;
+        if ((rc = h->opts.qn_memory > 0 ? qn_call(h, n) : run_iterations(h, n))) return rc;
         done += n;
         if ((rc = lower_bound(h, &lb))) return rc;
         if (std::fabs(lb - prev) < h->opts.conv_rel_tol * std::max(std::fabs(lb), 1e-300)) {
@@ -1213,6 +1389,13 @@ int disco_grad(disco_handle* h, float* dlb_dpair_costs, int64_t n) {
             return rc;
     }
     cudaStream_t s = h->stream;
+    Trace tr;
+    tr.scope = "grad";
+    auto mark = [&](const char* what) {
+        if (tr.on) cudaStreamSynchronize(s);
+        tr.mark(what);
+    };
+    mark("setup");
     if ((rc = save_snap(h, &h->final_state, h->B))) return rc;
     CK(cudaMemsetAsync(h->lbar, 0, size_t(h->nslots_tile) * 4, s));
     CK(cudaMemsetAsync(h->Fbar, 0, size_t(h->nnodes_tile) * 4, s));
@@ -1228,6 +1411,7 @@ int disco_grad(disco_handle* h, float* dlb_dpair_costs, int64_t n) {
         a.mubar_out = h->mub[0];
         CK(launch_adjoint(Adj::Bound, a, s));
     }
+    mark("bound adjoint");
     int nx = 0;  // mub[nx]: adjoint of the deferred means the pass being reversed produced
     for (int k = nck - 1; k >= 0; --k) {
         if ((rc = load_snap(h, h->checkpoints[k], h->B))) return rc;
@@ -1237,6 +1421,7 @@ int disco_grad(disco_handle* h, float* dlb_dpair_costs, int64_t n) {
                 if ((rc = save_snap(h, &h->tape[2 * t + dir], dir == 0 ? h->B : h->F))) return rc;
                 if ((rc = h->pass(dir == 0 ? Pass::FwdMMA : Pass::BwdMMA))) return rc;
             }
+        mark("block replay");
         for (int e = 2 * nit - 1; e >= 0; --e) {
             const Snap& tp = h->tape[e];
             const bool fwd = (e % 2) == 0;
@@ -1255,6 +1440,7 @@ int disco_grad(disco_handle* h, float* dlb_dpair_costs, int64_t n) {
             CK(launch_adjoint(fwd ? Adj::Fwd : Adj::Bwd, a, s));
             nx ^= 1;
         }
+        mark("block reverse");
     }
     // the initial backward min-sum on lambda^0
     {
@@ -1275,11 +1461,16 @@ int disco_grad(disco_handle* h, float* dlb_dpair_costs, int64_t n) {
     std::vector<float> cb(static_cast<size_t>(h->nint));
     CK(cudaMemcpyAsync(cb.data(), h->cbar, cb.size() * 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    mark("reset adjoint, costs");
     // chain rule to the pair costs: c_e = (mean of e's three pair costs) / scale
     std::vector<float> g(static_cast<size_t>(need), 0.0f);
-    int64_t off = 0;
-    for (size_t i = 0; i < h->plans.size(); ++i) {
+    std::vector<int64_t> offs(h->plans.size() + 1, 0);
+    for (size_t i = 0; i < h->plans.size(); ++i) offs[i + 1] = offs[i] + int64_t(h->plans[i].nvx) * h->plans[i].nvy;
+    parallel_chunks(int64_t(h->plans.size()), std::min<int>(host_threads(h->opts), int(h->plans.size())),
+                    [&](int, int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; ++i) {
         const Plan& P = h->plans[i];
+        const int64_t off = offs[i];
         std::vector<double> ge(static_cast<size_t>(P.nvars), 0.0);
         for (int64_t u = 0; u < P.n_free; ++u) ge[size_t(P.free_orig[u])] = cb[size_t(h->var_base[i] + u)];
         double cc = 0.0;
@@ -1295,9 +1486,12 @@ int disco_grad(disco_handle* h, float* dlb_dpair_costs, int64_t n) {
             for (int v = 0; v < 3; ++v) gp[size_t(P.vm[3 * e + v]) * P.nvy + P.vn[3 * e + v]] += gr / 3.0;
         }
         for (size_t q = 0; q < gp.size(); ++q) g[size_t(off) + q] = float(gp[q]);
-        off += int64_t(P.nvx) * P.nvy;
     }
-    return write_out(dlb_dpair_costs, g.data(), g.size() * 4, s);
+    });
+    mark("chain to pair costs");
+    rc = write_out(dlb_dpair_costs, g.data(), g.size() * 4, s);
+    mark("output");
+    return rc;
 }
 
 void disco_free(disco_handle* h) {

@@ -88,6 +88,21 @@ cudaError_t launch_adjoint(Adj kind, const AdjArgs& a, cudaStream_t s);
 cudaError_t launch_adj_cost(const uint32_t* var, const uint32_t* desc, int64_t nslots, const float* lbar,
                             const uint8_t* deg, int64_t nint, float* tab, float* cbar, cudaStream_t s);
 
+// Quasi-Newton vector kernels (qn.cu); n = slots in tile layout.
+cudaError_t launch_qn_sign(const float* mm, const uint32_t* var, int64_t n, float* g, cudaStream_t s);
+int qn_dot_blocks();
+cudaError_t launch_qn_dot(const float* a, const float* b, int64_t n, double* partial, cudaStream_t s);
+cudaError_t launch_qn_axpy(float* y, float a, const float* x, int64_t n, cudaStream_t s);
+cudaError_t launch_qn_scale(float* x, float a, int64_t n, cudaStream_t s);
+cudaError_t launch_qn_sub(const float* a, const float* b, int64_t n, float* out, cudaStream_t s);
+cudaError_t launch_qn_project(float* x, const uint32_t* var, const uint32_t* desc, int64_t n, float* tab,
+                              cudaStream_t s);
+cudaError_t launch_qn_step(const float* lam, const float* lam_lo, const float* d, float gamma, const uint32_t* var,
+                           int64_t n, float* out, float* out_lo, cudaStream_t s);
+cudaError_t launch_qn_delta(const float* lam, const float* lam_lo, const float* acc, const float* old,
+                            const float* old_lo, const uint32_t* var, const uint32_t* desc, int64_t n, float* s_out,
+                            cudaStream_t s);
+
 enum class Pass {
     FwdMMA,      // forward half-pass with updates, stores F
     BwdMMA,      // backward half-pass with updates, stores B

@@ -148,5 +148,5 @@ def test_autograd_function_matches_solver(torch):
     w = torch.tensor([2.0, -0.5], dtype=torch.float64, device="cuda")
     (lbs * w).sum().backward()
     for k, (lb, g) in enumerate(refs):
-        assert float(lbs[k]) == pytest.approx(lb, rel=1e-12)
+        assert float(lbs[k].detach()) == pytest.approx(lb, rel=1e-12)
         np.testing.assert_allclose(costs[k].grad.cpu().numpy(), float(w[k]) * g, rtol=1e-6, atol=1e-12)
