@@ -46,7 +46,7 @@ def _traffic(workload: str, split_chunk: int):
     """DRAM bytes per half-pass launch from the committed ncu summary of this workload, or
     None when the half-pass kernels changed since the counters were taken (source hash)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "halfpass_config3_icosphere4.md")
+    path = os.path.join(ROOT, "profiles", "halfpass_icosphere4-5120T-top16.md")
     src = os.path.join(ROOT, "paper_2310_08230_gb300", "csrc", "kernels.cu")
     if workload != "icosphere4-5120T-top16" or split_chunk != 32 or not os.path.exists(path):
         return None
@@ -202,6 +202,7 @@ def gpu_arm(args):
                      iters=info.iterations, conv_iters=iters, lb=lb.value, primal=cost.value, primal_ok=rc == 0,
                      dual_ms=dual_ms, conv_ms=t_conv, build_ms=info.build_ms, bytes_per_iter=info.bytes_per_iter,
                      ntiles=info.ntiles, max_layers=info.max_layers, upload_ms=info.upload_ms,
+                     launch_geometry=info.launch_geometry,
                      costs_candidates_ms=(t1 - t0) * 1e3, build_call_ms=(t_dual0 - t1) * 1e3,
                      primal_ms=(t4 - t3) * 1e3)
         t5 = time.perf_counter()
@@ -255,6 +256,7 @@ def gpu_arm(args):
         "data": "synthetic",
         "config": {"workload": inst.name, "nvars": st["nvars"], "nvars_free": st["nvars_free"],
                    "bdd_slots": st["nslots"], "bdd_nodes": st["nnodes"], "max_layers": st["max_layers"],
+                   "warps_per_block_autotuned": st["launch_geometry"],
                    "split_chunk": args.split_chunk, "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "ms_to_converged_bound": st["conv_ms"], "converged_iters": st["conv_iters"],

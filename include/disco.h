@@ -87,7 +87,12 @@ typedef struct {
     int32_t qn_memory;        /* [0] disco_converge interleaves quasi-Newton steps (Alg. 1) with
                                  its lb_every MMA iterations, keeping this many L-BFGS pairs;
                                  0 = MMA only */
-    int32_t reserved[2];
+    int32_t cost_model;       /* [0] element costs from the pair costs: 0 = mean of the three pair
+                                 costs; 1 = Eq. 2: sum over the corners of (A_X(m_v) + A_Y(n_v))
+                                 d(m_v, n_v) with A the mixed vertex areas (Meyer et al. 2003;
+                                 needs the meshes' V) and d the pair distances
+                                 (disco_pair_distances) */
+    int32_t reserved[1];
 } disco_opts;
 
 typedef struct {
@@ -124,6 +129,11 @@ int disco_default_opts(disco_opts *opts);
  */
 int disco_pair_costs(const float *FX, const float *FY, int32_t nvx, int32_t nvy, int32_t dim,
                      float *d, void *stream);
+
+/* d[m, n] = ||FX[m, :] - FY[n, :]|| (Euclidean; the feature distance of Eq. 2), FP32,
+ * row-major nvx x nvy. Same arguments, layout and errors as disco_pair_costs. */
+int disco_pair_distances(const float *FX, const float *FY, int32_t nvx, int32_t nvy, int32_t dim, float *d,
+                         void *stream);
 
 /*
  * Candidate mask of the top-k pruned product space (Sec. 4 pruning to neighbourhoods of

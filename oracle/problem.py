@@ -75,6 +75,45 @@ def pair_distance(FX: np.ndarray, FY: np.ndarray) -> np.ndarray:
     return np.mean(diff * diff, axis=2)
 
 
+def pair_euclid(FX: np.ndarray, FY: np.ndarray) -> np.ndarray:
+    """d(m, n) = ||F_X[m] - F_Y[n]||, FP64 (the feature distance of Eq. 2)."""
+    FX = np.asarray(FX, dtype=np.float64)
+    FY = np.asarray(FY, dtype=np.float64)
+    diff = FX[:, None, :] - FY[None, :, :]
+    return np.sqrt(np.sum(diff * diff, axis=2))
+
+
+def mixed_areas(V: np.ndarray, T: np.ndarray) -> np.ndarray:
+    """Mixed area of every vertex (Eq. 2's A; Meyer et al. 2003, "mixed area" of a vertex's
+    1-ring). Per triangle: if no angle exceeds 90 degrees, corner P takes its Voronoi part
+    (|PR|^2 cot Q + |PQ|^2 cot R) / 8; otherwise the obtuse corner takes half the triangle's
+    area and the two others a quarter each."""
+    V = np.asarray(V, dtype=np.float64)
+    T = np.asarray(T, dtype=np.int64)
+    out = np.zeros(len(V))
+    for t in T:
+        P = V[t]
+        area = 0.5 * np.linalg.norm(np.cross(P[1] - P[0], P[2] - P[0]))
+        if area == 0.0:
+            continue
+        # angle at each corner from the law of cosines on the opposite side
+        ang = np.empty(3)
+        for v in range(3):
+            a, b = P[(v + 1) % 3] - P[v], P[(v + 2) % 3] - P[v]
+            ang[v] = np.arccos(np.clip(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)), -1.0, 1.0))
+        if ang.max() <= np.pi / 2:
+            for v in range(3):
+                q, r = (v + 1) % 3, (v + 2) % 3
+                pr2 = np.sum((P[v] - P[r]) ** 2)
+                pq2 = np.sum((P[v] - P[q]) ** 2)
+                out[t[v]] += (pr2 / np.tan(ang[q]) + pq2 / np.tan(ang[r])) / 8.0
+        else:
+            ob = int(np.argmax(ang))
+            for v in range(3):
+                out[t[v]] += area / 2.0 if v == ob else area / 4.0
+    return out
+
+
 def closed_one_ring(nv: int, T: np.ndarray) -> np.ndarray:
     """Boolean adjacency with the diagonal: N[v] = {v} + neighbours of v."""
     A = np.eye(nv, dtype=bool)
@@ -208,8 +247,14 @@ def enumerate_product_space(TX: np.ndarray, TY: np.ndarray, allowed: np.ndarray)
             cat(out_p, (0,)))
 
 
-def build_problem(TX: np.ndarray, TY: np.ndarray, d: np.ndarray, allowed: np.ndarray | None = None) -> Problem:
-    """Product space, costs and constraint rows (closedness, then X projection, then Y projection)."""
+def build_problem(TX: np.ndarray, TY: np.ndarray, d: np.ndarray, allowed: np.ndarray | None = None,
+                  cost_model: int = 0, VX: np.ndarray | None = None, VY: np.ndarray | None = None,
+                  normalize: bool = True) -> Problem:
+    """Product space, costs and constraint rows (closedness, then X projection, then Y projection).
+
+    cost_model 0: c_p = mean of the three pair costs d; 1 (Eq. 2): c_p = sum over the three
+    corners of (A_X(m_v) + A_Y(n_v)) d(m_v, n_v), A the mixed vertex areas of the meshes
+    with positions VX, VY. Costs are then divided by the largest one unless normalize is off."""
     nvx, nvy = d.shape
     if allowed is None:
         allowed = np.ones((nvx, nvy), dtype=bool)
@@ -217,10 +262,16 @@ def build_problem(TX: np.ndarray, TY: np.ndarray, d: np.ndarray, allowed: np.nda
     TY = np.asarray(TY, dtype=np.int64)
     vm, vn, vt, vx, vy, vp = enumerate_product_space(TX, TY, allowed)
     P = len(vt)
-    # cost: mean of the three pair distances, normalised by the largest kept cost
-    c = (d[vm[:, 0], vn[:, 0]] + d[vm[:, 1], vn[:, 1]] + d[vm[:, 2], vn[:, 2]]) / 3.0
+    # cost: mean of the three pair distances (or Eq. 2), normalised by the largest kept cost
+    if cost_model == 1:
+        aX = mixed_areas(VX, TX)
+        aY = mixed_areas(VY, TY)
+        c = sum((aX[vm[:, v]] + aY[vn[:, v]]) * d[vm[:, v], vn[:, v]] for v in range(3))
+    else:
+        c = (d[vm[:, 0], vn[:, 0]] + d[vm[:, 1], vn[:, 1]] + d[vm[:, 2], vn[:, 2]]) / 3.0
     cmax = c.max() if P else 1.0
-    c = c / cmax if cmax > 0 else c
+    if normalize:
+        c = c / cmax if cmax > 0 else c
 
     # closedness rows: each element's three boundary edges p_v -> p_{v+1}
     key = vm * nvy + vn  # product-vertex key, lexicographic in (m, n)

@@ -37,7 +37,7 @@ class disco_opts(ctypes.Structure):
         ("propagate_limit", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
         ("host_threads", ctypes.c_int32), ("split_max_segments", ctypes.c_int32),
         ("graph_iters", ctypes.c_int32), ("autotune", ctypes.c_int32), ("normalize_costs", ctypes.c_int32),
-        ("qn_memory", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
+        ("qn_memory", ctypes.c_int32), ("cost_model", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1),
     ]
 
 
@@ -55,6 +55,7 @@ V, P, I32, I64, D, F = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.
 SIGNATURES = {
     "disco_default_opts": (ctypes.c_int, [ctypes.POINTER(disco_opts)]),
     "disco_pair_costs": (ctypes.c_int, [P, P, I32, I32, I32, P, P]),
+    "disco_pair_distances": (ctypes.c_int, [P, P, I32, I32, I32, P, P]),
     "disco_candidates": (ctypes.c_int, [P, I32, I32, I32, ctypes.POINTER(disco_mesh), ctypes.POINTER(disco_mesh), P, P]),
     "disco_candidates_noalloc": (ctypes.c_int, [P, I32, I32, I32, ctypes.POINTER(disco_mesh),
                                                 ctypes.POINTER(disco_mesh), P, P]),

@@ -28,10 +28,15 @@ def _stream_ptr(stream=None) -> int:
     return int(s.cuda_stream)
 
 
-def _mesh(T: np.ndarray, nv: int):
+def _mesh(T: np.ndarray, nv: int, V: np.ndarray | None = None):
+    """disco_mesh over host arrays; returns (mesh, arrays to keep alive)."""
     T = np.ascontiguousarray(T, dtype=np.int32)
-    m = L.disco_mesh(int(nv), int(T.shape[0]), None, T.ctypes.data_as(ctypes.c_void_p))
-    return m, T
+    Vp = None
+    if V is not None:
+        V = np.ascontiguousarray(V, dtype=np.float32)
+        Vp = V.ctypes.data_as(ctypes.c_void_p)
+    m = L.disco_mesh(int(nv), int(T.shape[0]), Vp, T.ctypes.data_as(ctypes.c_void_p))
+    return m, (T, V)
 
 
 def _ptr(a) -> int:
@@ -49,6 +54,17 @@ def pair_costs(FX, FY, stream=None):
     d = torch.empty((FX.shape[0], FY.shape[0]), dtype=torch.float32, device=FX.device)
     L.check(L.lib().disco_pair_costs(FX.data_ptr(), FY.data_ptr(), FX.shape[0], FY.shape[0], FX.shape[1],
                                      d.data_ptr(), _stream_ptr(stream)), "disco_pair_costs")
+    return d
+
+
+def pair_distances(FX, FY, stream=None):
+    """d[m, n] = ||FX[m] - FY[n]|| (FP32, CUDA tensors in and out), the feature distance of Eq. 2."""
+    torch = _torch()
+    FX = FX.contiguous().float()
+    FY = FY.contiguous().float()
+    d = torch.empty((FX.shape[0], FY.shape[0]), dtype=torch.float32, device=FX.device)
+    L.check(L.lib().disco_pair_distances(FX.data_ptr(), FY.data_ptr(), FX.shape[0], FY.shape[0], FX.shape[1],
+                                         d.data_ptr(), _stream_ptr(stream)), "disco_pair_distances")
     return d
 
 
@@ -78,15 +94,15 @@ class Solver:
     """One shape pair: ILP (P) compiled to BDDs and solved by the GPU dual / primal."""
 
     def __init__(self, TX: np.ndarray, TY: np.ndarray, d, allowed=None, nvx: int | None = None,
-                 nvy: int | None = None, **opts):
+                 nvy: int | None = None, VX=None, VY=None, **opts):
         nvx = int(d.shape[0]) if nvx is None else nvx
         nvy = int(d.shape[1]) if nvy is None else nvy
         if isinstance(d, np.ndarray):
             d = np.ascontiguousarray(d, dtype=np.float32)
         if isinstance(allowed, np.ndarray):
             allowed = np.ascontiguousarray(allowed, dtype=np.uint8)
-        mx, self._tx = _mesh(TX, nvx)
-        my, self._ty = _mesh(TY, nvy)
+        mx, self._tx = _mesh(TX, nvx, VX)
+        my, self._ty = _mesh(TY, nvy, VY)
         self.opts = default_opts(**opts)
         h = ctypes.c_void_p()
         L.check(L.lib().disco_build(ctypes.byref(mx), ctypes.byref(my), _ptr(d),
@@ -171,7 +187,7 @@ class Solver:
 
     @classmethod
     def batch(cls, pairs, **opts) -> "Solver":
-        """One handle over several pairs: ``pairs`` = [(TX, TY, d, allowed_or_None), ...]."""
+        """One handle over several pairs: ``pairs`` = [(TX, TY, d, allowed_or_None[, VX, VY]), ...]."""
         self = cls.__new__(cls)
         n = len(pairs)
         meshes_x = (L.disco_mesh * n)()
@@ -179,13 +195,15 @@ class Solver:
         keep = []
         dptr = (ctypes.c_void_p * n)()
         aptr = (ctypes.c_void_p * n)()
-        for i, (TX, TY, d, allowed) in enumerate(pairs):
+        for i, pair in enumerate(pairs):
+            TX, TY, d, allowed = pair[:4]
+            VX, VY = (pair[4], pair[5]) if len(pair) > 4 else (None, None)
             if isinstance(d, np.ndarray):
                 d = np.ascontiguousarray(d, dtype=np.float32)
             if isinstance(allowed, np.ndarray):
                 allowed = np.ascontiguousarray(allowed, dtype=np.uint8)
-            mx, tx = _mesh(TX, int(d.shape[0]))
-            my, ty = _mesh(TY, int(d.shape[1]))
+            mx, tx = _mesh(TX, int(d.shape[0]), VX)
+            my, ty = _mesh(TY, int(d.shape[1]), VY)
             meshes_x[i] = mx
             meshes_y[i] = my
             dptr[i] = _ptr(d)

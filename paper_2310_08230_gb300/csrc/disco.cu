@@ -652,6 +652,16 @@ int disco_pair_costs(const float* FX, const float* FY, int32_t nvx, int32_t nvy,
     return DISCO_OK;
 }
 
+int disco_pair_distances(const float* FX, const float* FY, int32_t nvx, int32_t nvy, int32_t dim, float* d,
+                         void* stream) {
+    if (!FX || !FY || !d || nvx <= 0 || nvy <= 0 || dim <= 0)
+        return fail(DISCO_ERR_INVALID_ARG, "pair_distances: bad arguments");
+    if (!is_device_ptr(FX) || !is_device_ptr(FY) || !is_device_ptr(d))
+        return fail(DISCO_ERR_INVALID_ARG, "pair_distances: FX, FY and d must be device pointers");
+    CK(launch_pair_costs(FX, FY, nvx, nvy, dim, d, static_cast<cudaStream_t>(stream), true));
+    return DISCO_OK;
+}
+
 int disco_candidates(const float* d, int32_t nvx, int32_t nvy, int32_t k, const disco_mesh* X, const disco_mesh* Y,
                      uint8_t* allowed, void* stream) {
     if (!d || !allowed || !X || !Y || !X->T || !Y->T || nvx != X->nv || nvy != Y->nv || k < 1 || k > 64 || k > nvx ||
@@ -724,7 +734,7 @@ int build_handle(int32_t n, const disco_mesh* X, const disco_mesh* Y, const floa
     disco_opts o;
     if (opts) o = *opts; else disco_default_opts(&o);
     if (!(o.omega > 0.0f && o.omega <= 1.0f) || o.split_chunk < 0 || o.split_max_segments < 0 || o.lb_every < 1 ||
-        o.graph_iters < 0)
+        o.graph_iters < 0 || o.cost_model < 0 || o.cost_model > 1 || o.qn_memory < 0)
         return fail(DISCO_ERR_INVALID_ARG, "build: bad options");
     std::unique_ptr<disco_handle> h(new disco_handle());
     h->device = o.device;
@@ -754,9 +764,9 @@ int build_handle(int32_t n, const disco_mesh* X, const disco_mesh* Y, const floa
     std::vector<std::string> errs(n);
     parallel_chunks(n, outer, [&](int, int64_t i0, int64_t i1) {
         for (int64_t i = i0; i < i1; ++i)
-            rcs[i] = build_plan(MeshIn{X[i].nv, X[i].nt, X[i].T}, MeshIn{Y[i].nv, Y[i].nt, Y[i].T}, hd[i].data(),
+            rcs[i] = build_plan(MeshIn{X[i].nv, X[i].nt, X[i].T, X[i].V}, MeshIn{Y[i].nv, Y[i].nt, Y[i].T, Y[i].V}, hd[i].data(),
                                 (allowed && allowed[i]) ? ha[i].data() : nullptr, o.split_chunk, o.split_max_segments,
-                                inner, &h->plans[i], &errs[i], o.normalize_costs != 0);
+                                inner, &h->plans[i], &errs[i], o.normalize_costs != 0, o.cost_model);
     });
     for (int32_t i = 0; i < n; ++i)
         if (rcs[i]) return fail(rcs[i], "build: instance " + std::to_string(i) + ": " + errs[i]);
@@ -980,7 +990,7 @@ int disco_compile_host(const disco_mesh* X, const disco_mesh* Y, const float* d,
         return fail(DISCO_ERR_INVALID_ARG, "compile_host: bad arguments");
     Plan P;
     std::string err;
-    int rc = build_plan(MeshIn{X->nv, X->nt, X->T}, MeshIn{Y->nv, Y->nt, Y->T}, d, allowed, split_chunk,
+    int rc = build_plan(MeshIn{X->nv, X->nt, X->T, X->V}, MeshIn{Y->nv, Y->nt, Y->T, Y->V}, d, allowed, split_chunk,
                         split_max_segments, 0, &P, &err);
     if (rc) return fail(rc, "compile_host: " + err);
     std::memset(info, 0, sizeof(*info));

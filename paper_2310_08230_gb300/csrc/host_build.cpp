@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <memory>
@@ -332,8 +333,51 @@ struct RowChunk {
 
 }  // namespace
 
+void mixed_areas(const MeshIn& M, std::vector<double>* out) {
+    out->assign(size_t(M.nv), 0.0);
+    for (int t = 0; t < M.nt; ++t) {
+        const int id[3] = {M.T[3 * t], M.T[3 * t + 1], M.T[3 * t + 2]};
+        double p[3][3];
+        for (int v = 0; v < 3; ++v)
+            for (int k = 0; k < 3; ++k) p[v][k] = double(M.V[3 * size_t(id[v]) + k]);
+        // edge vectors and the corner dot products: corner v between edges to v+1 and v+2
+        auto sub = [](const double* a, const double* b, double* r) {
+            for (int k = 0; k < 3; ++k) r[k] = a[k] - b[k];
+        };
+        auto dot = [](const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; };
+        double e[3][2][3], dv[3], len2[3];
+        for (int v = 0; v < 3; ++v) {
+            sub(p[(v + 1) % 3], p[v], e[v][0]);
+            sub(p[(v + 2) % 3], p[v], e[v][1]);
+            dv[v] = dot(e[v][0], e[v][1]);
+        }
+        double cr[3];
+        cr[0] = e[0][0][1] * e[0][1][2] - e[0][0][2] * e[0][1][1];
+        cr[1] = e[0][0][2] * e[0][1][0] - e[0][0][0] * e[0][1][2];
+        cr[2] = e[0][0][0] * e[0][1][1] - e[0][0][1] * e[0][1][0];
+        const double twice = std::sqrt(dot(cr, cr));  // twice the triangle area
+        if (twice <= 0.0) continue;
+        for (int v = 0; v < 3; ++v) len2[v] = dot(e[v][0], e[v][0]);  // |p_v p_{v+1}|^2
+        int obtuse = -1;
+        for (int v = 0; v < 3; ++v)
+            if (dv[v] < 0.0) obtuse = v;
+        if (obtuse < 0) {
+            // cot of the angle at corner v = dot / (2 area); Voronoi part of corner v uses the
+            // two edges at v and the cotangents of the opposite angles
+            for (int v = 0; v < 3; ++v) {
+                const int a = (v + 1) % 3, b = (v + 2) % 3;
+                const double cot_a = dv[a] / twice, cot_b = dv[b] / twice;
+                // |v b|^2 cot(angle at a) + |v a|^2 cot(angle at b)
+                (*out)[id[v]] += (len2[b] * cot_a + len2[v] * cot_b) / 8.0;
+            }
+        } else {
+            for (int v = 0; v < 3; ++v) (*out)[id[v]] += (v == obtuse ? 0.25 : 0.125) * twice;
+        }
+    }
+}
+
 int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8_t* mask, int split_chunk,
-               int split_max_segments, int threads, Plan* P, std::string* err, bool normalize) {
+               int split_max_segments, int threads, Plan* P, std::string* err, bool normalize, int cost_model) {
     auto t0 = std::chrono::steady_clock::now();
     Trace tr;
     if (threads <= 0) threads = std::max(1u, std::thread::hardware_concurrency());
@@ -392,8 +436,14 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     P->vn = std::move(E.n);
 
     tr.mark("product space");
-    // ---- costs: mean of the three pair costs, normalised by the largest
+    // ---- costs: mean of the three pair costs (or Eq. 2), normalised by the largest
     const int nth = threads;
+    std::vector<double> aX, aY;
+    if (cost_model == 1) {
+        if (!Xin.V || !Yin.V) { *err = "cost model 1 needs vertex positions"; return DISCO_ERR_INVALID_ARG; }
+        mixed_areas(Xin, &aX);
+        mixed_areas(Yin, &aY);
+    }
     P->cost.resize(nv);
     {
         std::vector<double> cmaxs(nth, 0.0);
@@ -401,8 +451,15 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         parallel_chunks(nv, nth, [&](int c, int64_t lo, int64_t hi) {
             for (int64_t i = lo; i < hi; ++i) {
                 double x = 0.0;
-                for (int v = 0; v < 3; ++v) x += double(d[size_t(P->vm[3 * i + v]) * nvy + P->vn[3 * i + v]]);
-                x /= 3.0;
+                if (cost_model == 1) {
+                    for (int v = 0; v < 3; ++v) {
+                        const int m = P->vm[3 * i + v], nn = P->vn[3 * i + v];
+                        x += (aX[m] + aY[nn]) * double(d[size_t(m) * nvy + nn]);
+                    }
+                } else {
+                    for (int v = 0; v < 3; ++v) x += double(d[size_t(P->vm[3 * i + v]) * nvy + P->vn[3 * i + v]]);
+                    x /= 3.0;
+                }
                 if (!(x >= 0.0) || x > 3.0e38) bad[c] = 1;
                 P->cost[i] = x;
                 cmaxs[c] = std::max(cmaxs[c], x);

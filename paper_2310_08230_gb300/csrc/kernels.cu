@@ -615,6 +615,8 @@ __global__ void k_perturb(const uint32_t* __restrict__ var, const uint32_t* __re
 
 // ---- feature distances: d[m, n] = mean_k (FX[m,k] - FY[n,k])^2, 64 x 64 tiles, 4 x 4 per thread
 constexpr int kPT = 64, kPK = 32;
+// NORM = false: mean squared difference; NORM = true: Euclidean distance (Eq. 2).
+template <bool NORM>
 __global__ void __launch_bounds__(256) k_pair_costs(const float* __restrict__ FX, const float* __restrict__ FY, int nvx,
                                                     int nvy, int dim, float* __restrict__ d) {
     __shared__ float sx[kPK][kPT + 1];
@@ -651,7 +653,7 @@ __global__ void __launch_bounds__(256) k_pair_costs(const float* __restrict__ FX
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int m = m0 + ty * 4 + i, n = n0 + tx * 4 + j;
-            if (m < nvx && n < nvy) d[size_t(m) * nvy + n] = acc[i][j] * inv;
+            if (m < nvx && n < nvy) d[size_t(m) * nvy + n] = NORM ? sqrtf(acc[i][j]) : acc[i][j] * inv;
         }
 }
 
@@ -792,9 +794,11 @@ cudaError_t launch_perturb(const uint32_t* var, const uint32_t* desc, int64_t n,
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
-cudaError_t launch_pair_costs(const float* FX, const float* FY, int nvx, int nvy, int dim, float* d, cudaStream_t s) {
+cudaError_t launch_pair_costs(const float* FX, const float* FY, int nvx, int nvy, int dim, float* d, cudaStream_t s,
+                              bool norm) {
     const dim3 grid((nvy + kPT - 1) / kPT, (nvx + kPT - 1) / kPT);
-    k_pair_costs<<<grid, 256, 0, s>>>(FX, FY, nvx, nvy, dim, d);
+    if (norm) k_pair_costs<true><<<grid, 256, 0, s>>>(FX, FY, nvx, nvy, dim, d);
+    else k_pair_costs<false><<<grid, 256, 0, s>>>(FX, FY, nvx, nvy, dim, d);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }

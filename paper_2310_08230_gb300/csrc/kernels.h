@@ -138,7 +138,8 @@ cudaError_t launch_count_free(const uint8_t* state, const uint8_t* deg, const in
                               cudaStream_t s);
 cudaError_t launch_perturb(const uint32_t* var, const uint32_t* desc, int64_t nslots, const float* mm_var,
                            const uint8_t* state, float delta, float* lam, float* lam_lo, cudaStream_t s);
-cudaError_t launch_pair_costs(const float* FX, const float* FY, int nvx, int nvy, int dim, float* d, cudaStream_t s);
+cudaError_t launch_pair_costs(const float* FX, const float* FY, int nvx, int nvy, int dim, float* d, cudaStream_t s,
+                              bool norm = false);
 cudaError_t launch_transpose(const float* src, int rows, int cols, float* dst, cudaStream_t s);
 cudaError_t launch_topk_rows(const float* d, int rows, int cols, int k, int32_t* idx, cudaStream_t s);
 cudaError_t launch_dilate(const int32_t* topk, int rows, int k, const int32_t* ring_ptr, const int32_t* ring,

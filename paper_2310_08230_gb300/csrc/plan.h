@@ -126,13 +126,22 @@ struct Plan {
 struct MeshIn {
     int32_t nv, nt;
     const int32_t* T;
+    const float* V = nullptr;  // nv x 3 positions (needed by cost model 1 only)
 };
 
+// Mixed (Voronoi) area of every vertex of a triangle mesh (Eq. 2's A, after Meyer et al.
+// 2003): per triangle, a non-obtuse triangle gives each corner its Voronoi part
+// (|PR|^2 cot Q + |PQ|^2 cot R) / 8; an obtuse one gives half its area to the obtuse corner
+// and a quarter to each other corner.
+void mixed_areas(const MeshIn& M, std::vector<double>* out);
+
 // Returns 0 or a negative DISCO_ERR_* code (err receives a message).
-// normalize: divide the element costs by the largest one (c in [0, 1]); otherwise the
-// element costs are the raw means of their three pair costs.
+// cost_model 0: c_p = mean of the element's three pair costs; 1 (Eq. 2): c_p = sum over
+// its corners of (A_X(m_v) + A_Y(n_v)) d(m_v, n_v), with A the mixed vertex areas (the
+// meshes' V are then required) and d the pair distances. normalize: divide the element
+// costs by the largest one (c in [0, 1]).
 int build_plan(const MeshIn& X, const MeshIn& Y, const float* d, const uint8_t* allowed,
                int split_chunk, int split_max_segments, int threads, Plan* out, std::string* err,
-               bool normalize = true);
+               bool normalize = true, int cost_model = 0);
 
 }  // namespace disco

@@ -1,8 +1,8 @@
 """Quasi-Newton powered MMA (Alg. 1 with Alg. 4-6, ``disco_dual_qn``) against the FP64
-oracle (``oracle/lbfgs.py``): the bound after every call matches to 1e-5 relative (FP32
-device arithmetic; the step search compares bounds, so the two sides take the same
-decisions except at near-ties, where the bound is flat anyway), never decreases, and the
-dual stays feasible (Eq. D)."""
+oracle (``oracle/lbfgs.py``): the bound after every call matches to 1e-5 relative, with an
+absolute floor of 1e-7 (FP32 device arithmetic; the step search compares bounds, so the two
+sides take the same decisions except at near-ties, where the bound is flat anyway), never
+decreases, and the dual stays feasible (Eq. D)."""
 import numpy as np
 import pytest
 
@@ -52,8 +52,10 @@ def test_qn_bounds_match_oracle(torch, which, chunk, mma):
         s.dual_qn(1, mma)
         ref = qn.o.lower_bound()
         lb = s.lower_bound()
-        assert abs(lb - ref) <= 1e-5 * max(abs(ref), 1e-3), (lb, ref, qn.last)
-        assert lb >= prev - 1e-5 * max(abs(prev), 1e-3)  # FP32 evaluation noise of the bound
+        # FP32 rounding of a sum of O(10^3) BDD minima of order 0.1-1 (costs in [0, 1]): the
+        # absolute floor 1e-7 matters only while the bound itself is still tiny (early calls)
+        assert abs(lb - ref) <= 1e-5 * max(abs(ref), 1e-2), (lb, ref, qn.last)
+        assert lb >= prev - 1e-5 * max(abs(prev), 1e-2)
         prev = lb
     # Eq. D feasibility: sum_j lambda^j_i + |J_i| pend_i = c_i
     lam, pend = s.get_state()
