@@ -236,6 +236,25 @@ int disco_dual(disco_handle *h, int32_t iters);
  * bounds on the host). Errors: DISCO_ERR_INVALID_ARG for negative counts, DISCO_ERR_OOM. */
 int disco_dual_qn(disco_handle *h, int32_t calls, int32_t mma_iters);
 
+/* Point map of a matching (triangle matching -> vertex pairs): the distinct vertex pairs
+ * (m, n) at the corners of the elements set to 1 in x (x as written by disco_primal, one byte
+ * per element of a single-instance handle), sorted by (m, n), written as pairs[2k] = m,
+ * pairs[2k+1] = n (host pointer). *count receives the number of pairs; if it exceeds
+ * `capacity` nothing is written and DISCO_ERR_INVALID_ARG is returned. */
+int disco_point_map(disco_handle *h, const uint8_t *x, int64_t nvars, int32_t *pairs, int64_t capacity,
+                    int64_t *count);
+
+/* Coarse-to-fine candidate mask (Sec. 4, coarse-to-fine: fine matchings are kept near the
+ * coarse solution): allowed[m', n'] = 1 iff some coarse pair (m, n) of `pairs` (npairs pairs,
+ * layout of disco_point_map) has m' within `rings` edges of fine vertex c2f_x[m] on the fine
+ * mesh X and n' within `rings` edges of c2f_y[n] on the fine mesh Y. c2f_x / c2f_y map coarse
+ * vertex ids to fine ones (host arrays, lengths ncx / ncy). Out: Xf->nv * Yf->nv bytes,
+ * row-major, host or device pointer. Host computation; synchronises. Errors:
+ * DISCO_ERR_INVALID_ARG (ids out of range, rings < 0). */
+int disco_candidates_coarse_to_fine(const int32_t *pairs, int64_t npairs, const int32_t *c2f_x, int32_t ncx,
+                                    const int32_t *c2f_y, int32_t ncy, int32_t rings, const disco_mesh *Xf,
+                                    const disco_mesh *Yf, uint8_t *allowed);
+
 /* Lower bound E(lambda + pend) + presolve constant of Eq. D, FP64 sum. Synchronises. */
 int disco_lower_bound(disco_handle *h, double *lb);
 

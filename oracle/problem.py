@@ -376,3 +376,32 @@ def make_problem(inst, topk="inst") -> tuple[Problem, np.ndarray, np.ndarray]:
     else:
         allowed = candidate_pairs(d, k, inst.X.T, inst.Y.T)
     return build_problem(inst.X.T, inst.Y.T, d, allowed), d, allowed
+
+
+def point_map(prob: Problem, x: np.ndarray) -> np.ndarray:
+    """Vertex pairs (m, n), sorted, at the corners of the elements set in x (the point-wise
+    correspondence of a triangle matching)."""
+    sel = np.asarray(x).astype(bool)
+    pairs = np.stack([prob.vm[sel].ravel(), prob.vn[sel].ravel()], axis=1)
+    return np.unique(pairs, axis=0) if len(pairs) else np.zeros((0, 2), np.int64)
+
+
+def coarse_to_fine_candidates(pairs: np.ndarray, c2f_x: np.ndarray, c2f_y: np.ndarray, rings: int,
+                              TX: np.ndarray, nvx: int, TY: np.ndarray, nvy: int) -> np.ndarray:
+    """Fine pairs (m', n') with m' within `rings` edges of c2f_x[m] and n' within `rings` edges
+    of c2f_y[n] for some coarse pair (m, n) (Sec. 4, coarse-to-fine). Boolean matrix powers of
+    the closed 1-ring adjacency give the within-r relation."""
+    def within(nv, T):
+        A = closed_one_ring(nv, T).astype(np.float64)
+        R = np.eye(nv)
+        for _ in range(rings):
+            R = ((R @ A) > 0).astype(np.float64)
+        return R
+
+    RX = within(nvx, TX)
+    RY = within(nvy, TY)
+    S = np.zeros((nvx, nvy))
+    for m, n in np.asarray(pairs).reshape(-1, 2):
+        S[c2f_x[m], c2f_y[n]] = 1.0
+    return (RX.T @ S @ RY) > 0
+

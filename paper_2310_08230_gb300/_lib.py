@@ -84,6 +84,9 @@ SIGNATURES = {
     "disco_record": (ctypes.c_int, [P, I32, I32]),
     "disco_grad": (ctypes.c_int, [P, P, I64]),
     "disco_dual_qn": (ctypes.c_int, [P, I32, I32]),
+    "disco_point_map": (ctypes.c_int, [P, P, I64, P, I64, ctypes.POINTER(ctypes.c_int64)]),
+    "disco_candidates_coarse_to_fine": (ctypes.c_int, [P, I64, P, I32, P, I32, I32, ctypes.POINTER(disco_mesh),
+                                                       ctypes.POINTER(disco_mesh), P]),
 }
 
 _lib = None

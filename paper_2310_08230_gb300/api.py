@@ -80,6 +80,22 @@ def candidates(d, k: int, TX: np.ndarray, TY: np.ndarray, stream=None):
     return allowed
 
 
+def candidates_coarse_to_fine(pairs: np.ndarray, c2f_x: np.ndarray, c2f_y: np.ndarray, rings: int,
+                              TX: np.ndarray, nvx: int, TY: np.ndarray, nvy: int) -> np.ndarray:
+    """Fine candidate mask (uint8, nvx x nvy) around the coarse vertex pairs `pairs` (k x 2):
+    pairs within `rings` edges, on both fine meshes, of a coarse match mapped by c2f_x / c2f_y."""
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    cx = np.ascontiguousarray(c2f_x, dtype=np.int32)
+    cy = np.ascontiguousarray(c2f_y, dtype=np.int32)
+    mx, kx = _mesh(TX, nvx)
+    my, ky = _mesh(TY, nvy)
+    out = np.zeros((nvx, nvy), np.uint8)
+    L.check(L.lib().disco_candidates_coarse_to_fine(pairs.ctypes.data, pairs.shape[0], cx.ctypes.data, cx.shape[0],
+                                                    cy.ctypes.data, cy.shape[0], int(rings), ctypes.byref(mx),
+                                                    ctypes.byref(my), out.ctypes.data), "disco_candidates_coarse_to_fine")
+    return out
+
+
 def default_opts(**kw) -> L.disco_opts:
     o = L.disco_opts()
     L.check(L.lib().disco_default_opts(ctypes.byref(o)), "disco_default_opts")
@@ -152,6 +168,16 @@ class Solver:
         if rc not in (L.DISCO_OK, L.DISCO_ERR_PRIMAL_FAILED):
             L.check(rc, "disco_primal")
         return x, c.value, rc == L.DISCO_OK
+
+    def point_map(self, x: np.ndarray) -> np.ndarray:
+        """Vertex pairs (k x 2, sorted) at the corners of the matching elements set in x."""
+        x = np.ascontiguousarray(x, dtype=np.uint8)
+        n = ctypes.c_int64()
+        cap = 3 * int(x.sum()) + 1
+        out = np.zeros((cap, 2), np.int32)
+        L.check(L.lib().disco_point_map(self.h, x.ctypes.data, x.shape[0], out.ctypes.data, cap, ctypes.byref(n)),
+                "disco_point_map")
+        return out[: n.value].copy()
 
     def get_state(self) -> tuple[np.ndarray, np.ndarray]:
         inf = self.info()

@@ -983,6 +983,87 @@ int disco_instance_info(disco_handle* h, int32_t i, disco_info_t* info) {
     return DISCO_OK;
 }
 
+int disco_point_map(disco_handle* h, const uint8_t* x, int64_t nvars, int32_t* pairs, int64_t capacity,
+                    int64_t* count) {
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (h->n_inst() != 1 || !x || !count || nvars < h->plans[0].nvars)
+        return fail(DISCO_ERR_INVALID_ARG, "point_map: single-instance handle and a full x required");
+    const Plan& P = h->plans[0];
+    std::vector<int64_t> keys;
+    for (int64_t e = 0; e < P.nvars; ++e)
+        if (x[e])
+            for (int v = 0; v < 3; ++v) keys.push_back(int64_t(P.vm[3 * e + v]) * P.nvy + P.vn[3 * e + v]);
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    *count = int64_t(keys.size());
+    if (int64_t(keys.size()) > capacity || (!pairs && !keys.empty()))
+        return fail(DISCO_ERR_INVALID_ARG, "point_map: capacity too small");
+    for (size_t k = 0; k < keys.size(); ++k) {
+        pairs[2 * k] = int32_t(keys[k] / P.nvy);
+        pairs[2 * k + 1] = int32_t(keys[k] % P.nvy);
+    }
+    return DISCO_OK;
+}
+
+int disco_candidates_coarse_to_fine(const int32_t* pairs, int64_t npairs, const int32_t* c2f_x, int32_t ncx,
+                                    const int32_t* c2f_y, int32_t ncy, int32_t rings, const disco_mesh* Xf,
+                                    const disco_mesh* Yf, uint8_t* allowed) {
+    if (!Xf || !Yf || !Xf->T || !Yf->T || !allowed || !c2f_x || !c2f_y || rings < 0 || npairs < 0 ||
+        (npairs > 0 && !pairs))
+        return fail(DISCO_ERR_INVALID_ARG, "coarse_to_fine: bad arguments");
+    const int nx = Xf->nv, ny = Yf->nv;
+    for (int32_t i = 0; i < ncx; ++i)
+        if (c2f_x[i] < 0 || c2f_x[i] >= nx) return fail(DISCO_ERR_INVALID_ARG, "coarse_to_fine: c2f_x out of range");
+    for (int32_t i = 0; i < ncy; ++i)
+        if (c2f_y[i] < 0 || c2f_y[i] >= ny) return fail(DISCO_ERR_INVALID_ARG, "coarse_to_fine: c2f_y out of range");
+    // vertices within `rings` edges of every seed vertex, by breadth-first search on each mesh
+    auto adjacency = [](const disco_mesh* M, std::vector<std::vector<int32_t>>* adj) {
+        adj->assign(size_t(M->nv), {});
+        for (int t = 0; t < M->nt; ++t)
+            for (int v = 0; v < 3; ++v) {
+                const int32_t a = M->T[3 * t + v], b = M->T[3 * t + (v + 1) % 3];
+                if (a < 0 || a >= M->nv || b < 0 || b >= M->nv) return false;
+                (*adj)[a].push_back(b);
+                (*adj)[b].push_back(a);
+            }
+        return true;
+    };
+    std::vector<std::vector<int32_t>> ax, ay;
+    if (!adjacency(Xf, &ax) || !adjacency(Yf, &ay)) return fail(DISCO_ERR_INVALID_ARG, "coarse_to_fine: bad mesh");
+    auto ball = [rings](const std::vector<std::vector<int32_t>>& adj, int32_t src, std::vector<int32_t>* out,
+                        std::vector<int32_t>* dist) {
+        out->assign(1, src);
+        (*dist)[src] = 0;
+        for (size_t q = 0; q < out->size(); ++q) {
+            const int32_t u = (*out)[q];
+            if ((*dist)[u] == rings) continue;
+            for (int32_t w : adj[u])
+                if ((*dist)[w] < 0) {
+                    (*dist)[w] = (*dist)[u] + 1;
+                    out->push_back(w);
+                }
+        }
+        for (int32_t u : *out) (*dist)[u] = -1;
+    };
+    std::vector<uint8_t> mask(size_t(nx) * ny, 0);
+    std::vector<int32_t> dx(size_t(nx), -1), dy(size_t(ny), -1), bx, by;
+    for (int64_t k = 0; k < npairs; ++k) {
+        const int32_t m = pairs[2 * k], n = pairs[2 * k + 1];
+        if (m < 0 || m >= ncx || n < 0 || n >= ncy) return fail(DISCO_ERR_INVALID_ARG, "coarse_to_fine: pair out of range");
+        ball(ax, c2f_x[m], &bx, &dx);
+        ball(ay, c2f_y[n], &by, &dy);
+        for (int32_t a : bx)
+            for (int32_t b : by) mask[size_t(a) * ny + b] = 1;
+    }
+    if (is_device_ptr(allowed)) {
+        CK(cudaMemcpy(allowed, mask.data(), mask.size(), cudaMemcpyHostToDevice));
+    } else {
+        std::memcpy(allowed, mask.data(), mask.size());
+    }
+    return DISCO_OK;
+}
+
 int disco_compile_host(const disco_mesh* X, const disco_mesh* Y, const float* d, const uint8_t* allowed,
                        int32_t split_chunk, int32_t split_max_segments, disco_info_t* info, int32_t* slot_var,
                        int32_t* slot_width, int64_t nslots, int8_t* fixed, int64_t nvars) {

@@ -130,6 +130,34 @@ def config5(n_pairs: int = 8, subdiv: int = 3) -> list[Instance]:
     return out
 
 
+def coarse_fine_pair(subdiv: int = 2, dim: int = 16, feat_noise: float = 0.05, seed: int = 6):
+    """An icosphere pair at two resolutions for coarse-to-fine solving.
+
+    The fine pair is X_f = icosphere(subdiv) against a deformed, relabelled copy Y_f. The
+    coarse pair uses the vertices of icosphere(subdiv - 1), which are the first vertices of
+    X_f, on both sides (Y_c relabelled again). Returns (coarse, fine, c2f_x, c2f_y) with
+    c2f_* mapping coarse vertex ids to fine ones; features of a coarse vertex are those of its
+    fine vertex."""
+    rng = _rng(seed)
+    Xf = M.icosphere(subdiv)
+    Yf, FXf, FYf, perm = make_pair(Xf, rng, dim, feat_noise, deform=True)
+    Xc0 = M.icosphere(subdiv - 1)
+    nc = Xc0.nv
+    q = rng.permutation(nc).astype(np.int64)  # coarse Y id of X vertex j
+    c2f_x = np.arange(nc, dtype=np.int32)
+    c2f_y = np.empty(nc, np.int32)
+    c2f_y[q] = perm[:nc]
+    VYc = np.empty((nc, 3), np.float32)
+    VYc[q] = Yf.V[perm[:nc]]
+    Yc = M.Mesh(VYc, q[Xc0.T.astype(np.int64)].astype(np.int32))
+    Xc = M.Mesh(Xf.V[:nc].copy(), Xc0.T)
+    FYc = np.empty((nc, dim), np.float32)
+    FYc[q] = FYf[perm[:nc]]
+    coarse = Instance(f"coarse-{Xc.nt}T", Xc, Yc, FXf[:nc].copy(), FYc, q, None, 100)
+    fine = Instance(f"fine-{Xf.nt}T", Xf, Yf, FXf, FYf, perm, None, 100)
+    return coarse, fine, c2f_x, c2f_y
+
+
 def mlp_params(seed: int = 5, sizes=(128, 256, 64)) -> list[np.ndarray]:
     """Seeded weights of the 2-layer feature MLP (W1, b1, W2, b2; N(0, 1/fan_in), zero bias)."""
     rng = _rng(1000 + seed)
