@@ -242,13 +242,14 @@ int to_host(const T* src, size_t n, std::vector<T>* out) {
     return DISCO_OK;
 }
 
+// Register widths of the tile classes: a segment goes to the narrowest class that holds its
+// widest layer (per-layer work grows with the class width, not with the layer's width).
+constexpr int kWidthClasses[] = {2, 4, 6, 8, 16, 32};
+
 int width_class(int w) {
-    if (w <= 2) return 2;
-    if (w <= 4) return 4;
-    if (w <= 6) return 6;
-    if (w <= 8) return 8;
-    if (w <= 16) return 16;
-    return 32;
+    for (int c : kWidthClasses)
+        if (w <= c) return c;
+    return kMaxWidth;
 }
 
 int upload(disco_handle* h) {
@@ -274,7 +275,7 @@ int upload(disco_handle* h) {
         int32_t inst;
         int64_t seg;
     };
-    auto class_index = [](int W) { return W <= 2 ? 0 : W <= 4 ? 1 : W <= 6 ? 2 : W <= 8 ? 3 : W <= 16 ? 4 : 5; };
+    auto class_index = [](int W) { return W; };  // classes are at most 32 wide
     std::vector<TileInfo> tiles;
     std::vector<int64_t> tile_first;  // first entry of the tile's segments in `order`
     std::vector<int32_t> tile_count, tile_inst;
@@ -284,7 +285,7 @@ int upload(disco_handle* h) {
     for (int64_t i = 0; i < ni; ++i) {
         const Plan& P = h->plans[i];
         const int64_t nseg = int64_t(P.segs.size());
-        std::vector<int64_t> cnt(size_t(6) * (maxL + 1) + 1, 0);
+        std::vector<int64_t> cnt(size_t(kMaxWidth + 1) * (maxL + 1) + 1, 0);
         auto key = [&](const Segment& sg) {  // class ascending, length descending
             return size_t(class_index(width_class(sg.max_width))) * (maxL + 1) + size_t(maxL - sg.n_layers);
         };

@@ -2,7 +2,12 @@
 // store in disco.cu. See host_build.cpp for the passages each step follows.
 #pragma once
 
+#include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -38,18 +43,105 @@ struct uninit_alloc : std::allocator<T> {
 template <class T>
 using pod_vector = std::vector<T, uninit_alloc<T>>;
 
-// Runs body(chunk, lo, hi) over [0, n) split into `nch` contiguous chunks on threads.
+// Persistent worker threads for parallel_chunks (creating and joining threads for every
+// parallel phase costs tens of microseconds per thread on many-core hosts). One job at a
+// time; its tasks are taken dynamically by the workers and the calling thread. A worker
+// checks into a job under the lock and out when it finds no task left; the caller returns
+// only when every task has finished and every worker that checked in has checked out, so no
+// worker ever touches a finished job.
+class WorkerPool {
+public:
+    static WorkerPool& get() {
+        static WorkerPool pool(int(std::max(2u, std::thread::hardware_concurrency())) - 1);
+        return pool;
+    }
+    // Runs f(0 .. n-1); false (nothing run) if the pool is busy or called from a worker.
+    bool try_run(int n, const std::function<void(int)>& f) {
+        if (in_worker() || !busy_.try_lock()) return false;
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            job_ = &f;
+            njobs_ = n;
+            next_.store(0);
+            remaining_ = n;
+            ++gen_;
+        }
+        cv_.notify_all();
+        run_tasks(f, n);
+        {
+            std::unique_lock<std::mutex> lk(mu_);
+            done_.wait(lk, [&] { return remaining_ == 0 && active_ == 0; });
+            job_ = nullptr;
+        }
+        busy_.unlock();
+        return true;
+    }
+    ~WorkerPool() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto& t : threads_) t.join();
+    }
+
+private:
+    explicit WorkerPool(int nthreads) {
+        for (int i = 0; i < nthreads; ++i)
+            threads_.emplace_back([this] {
+                in_worker() = true;
+                uint64_t seen = 0;
+                for (;;) {
+                    const std::function<void(int)>* f = nullptr;
+                    int n = 0;
+                    {
+                        std::unique_lock<std::mutex> lk(mu_);
+                        cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+                        if (stop_) return;
+                        seen = gen_;
+                        if (!job_) continue;
+                        f = job_;
+                        n = njobs_;
+                        ++active_;  // check in
+                    }
+                    run_tasks(*f, n);
+                    std::lock_guard<std::mutex> lk(mu_);
+                    if (--active_ == 0 && remaining_ == 0) done_.notify_all();  // check out
+                }
+            });
+    }
+    static bool& in_worker() {
+        static thread_local bool flag = false;
+        return flag;
+    }
+    void run_tasks(const std::function<void(int)>& f, int n) {
+        for (int i; (i = next_.fetch_add(1)) < n;) {
+            f(i);
+            std::lock_guard<std::mutex> lk(mu_);
+            if (--remaining_ == 0 && active_ == 0) done_.notify_all();
+        }
+    }
+    std::vector<std::thread> threads_;
+    std::mutex mu_, busy_;
+    std::condition_variable cv_, done_;
+    const std::function<void(int)>* job_ = nullptr;
+    int njobs_ = 0, remaining_ = 0, active_ = 0;
+    std::atomic<int> next_{0};
+    uint64_t gen_ = 0;
+    bool stop_ = false;
+};
+
+// Runs body(chunk, lo, hi) over [0, n) split into `nch` contiguous chunks in parallel.
 template <class F>
 inline void parallel_chunks(int64_t n, int nch, F body) {
     if (nch <= 1 || n < 2) {
         body(0, int64_t(0), n);
         return;
     }
+    const std::function<void(int)> task = [&](int c) { body(c, n * c / nch, n * (c + 1) / nch); };
+    if (WorkerPool::get().try_run(nch, task)) return;
     std::vector<std::thread> pool;
-    for (int c = 0; c < nch; ++c) {
-        const int64_t lo = n * c / nch, hi = n * (c + 1) / nch;
-        pool.emplace_back([&body, c, lo, hi] { body(c, lo, hi); });
-    }
+    for (int c = 0; c < nch; ++c) pool.emplace_back([&task, c] { task(c); });
     for (auto& th : pool) th.join();
 }
 

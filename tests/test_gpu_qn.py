@@ -55,7 +55,8 @@ def test_qn_bounds_match_oracle(torch, which, chunk, mma):
         # FP32 rounding of a sum of O(10^3) BDD minima of order 0.1-1 (costs in [0, 1]): the
         # absolute floor 1e-7 matters only while the bound itself is still tiny (early calls)
         assert abs(lb - ref) <= 1e-5 * max(abs(ref), 1e-2), (lb, ref, qn.last)
-        assert lb >= prev - 1e-5 * max(abs(prev), 1e-2)
+        # both bounds lie within the parity tolerance of the oracle's non-decreasing sequence
+        assert lb >= prev - 2e-5 * max(abs(prev), 1e-2)
         prev = lb
     # Eq. D feasibility: sum_j lambda^j_i + |J_i| pend_i = c_i
     lam, pend = s.get_state()
