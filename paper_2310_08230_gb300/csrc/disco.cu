@@ -246,6 +246,14 @@ int to_host(const T* src, size_t n, std::vector<T>* out) {
 // widest layer (per-layer work grows with the class width, not with the layer's width).
 constexpr int kWidthClasses[] = {2, 4, 6, 8, 16, 32};
 
+// The fused kernels instantiate widths 2, 4 and 6; launch_pass has 8, 16 and 32.
+constexpr bool classes_have_kernels() {
+    for (int c : kWidthClasses)
+        if (c != 2 && c != 4 && c != 6 && c != 8 && c != 16 && c != 32) return false;
+    return true;
+}
+static_assert(classes_have_kernels(), "every width class needs a kernel instantiation");
+
 int width_class(int w) {
     for (int c : kWidthClasses)
         if (w <= c) return c;

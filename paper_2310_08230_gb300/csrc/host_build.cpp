@@ -722,7 +722,15 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                 if (pred(t)) return true;
             return false;
         };
+        tr.mark("presolve setup");
+        int rounds = 0;
         while (any([&](int t) { return !frontier[t].empty(); })) {
+            if (tr.on && rounds < 4) {
+                char what[32];
+                std::snprintf(what, sizeof(what), "presolve round %d", rounds);
+                tr.mark(what);
+            }
+            ++rounds;
             // (1) decide
             parallel_chunks(nt, nt, [&](int t, int64_t, int64_t) {
                 for (auto& b : force[t]) b.clear();

@@ -238,24 +238,20 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_forward(KArgs a) {
     forward_tile<W, MODE>(a, tile, ti, smem + (threadIdx.x >> 5) * ring_floats<W>());
 }
 
-// Width classes up to 6 in one launch (tiles ordered longest first), so that short tiles
+// Width classes 2, 4 and 6 in one launch (tiles ordered longest first), so that short tiles
 // fill the SMs around the long ones; every warp's ring is sized for width kFusedMaxW.
 // WPB warps (tiles) per block; every geometry computes the same results.
 template <int MODE, int WPB>
 __global__ void __launch_bounds__(WPB * 32, kFusedWarpsPerSM / WPB) k_forward_fused(KArgs a) {
-    static_assert(kFusedMaxW == 6, "fused dispatch covers widths 2 to 6");
+    static_assert(kFusedMaxW == 6, "fused dispatch covers widths 2, 4, 6");
     extern __shared__ float smem[];
     const int tile = a.tile0 + int(blockIdx.x) * WPB + int(threadIdx.x >> 5);
     if (tile >= a.tile_end) return;
     const TileInfo ti = a.tiles[tile];
     float* ring = smem + (threadIdx.x >> 5) * ring_floats<kFusedMaxW>();
-    switch (ti.W) {
-        case 2: forward_tile<2, MODE>(a, tile, ti, ring); break;
-        case 3: forward_tile<3, MODE>(a, tile, ti, ring); break;
-        case 4: forward_tile<4, MODE>(a, tile, ti, ring); break;
-        case 5: forward_tile<5, MODE>(a, tile, ti, ring); break;
-        default: forward_tile<6, MODE>(a, tile, ti, ring); break;
-    }
+    if (ti.W == 2) forward_tile<2, MODE>(a, tile, ti, ring);
+    else if (ti.W == 4) forward_tile<4, MODE>(a, tile, ti, ring);
+    else forward_tile<6, MODE>(a, tile, ti, ring);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -382,13 +378,9 @@ __global__ void __launch_bounds__(WPB * 32, kFusedWarpsPerSM / WPB) k_backward_f
     if (tile >= a.tile_end) return;
     const TileInfo ti = a.tiles[tile];
     float* ring = smem + (threadIdx.x >> 5) * ring_floats<kFusedMaxW>();
-    switch (ti.W) {
-        case 2: backward_tile<2, MODE>(a, ti, ring); break;
-        case 3: backward_tile<3, MODE>(a, ti, ring); break;
-        case 4: backward_tile<4, MODE>(a, ti, ring); break;
-        case 5: backward_tile<5, MODE>(a, ti, ring); break;
-        default: backward_tile<6, MODE>(a, ti, ring); break;
-    }
+    if (ti.W == 2) backward_tile<2, MODE>(a, ti, ring);
+    else if (ti.W == 4) backward_tile<4, MODE>(a, ti, ring);
+    else backward_tile<6, MODE>(a, ti, ring);
 }
 
 // ---------------------------------------------------------------------------------------
