@@ -125,6 +125,19 @@ def workload(name):
     raise ValueError(name)
 
 
+def replica_throughput(ms: float, updates_per_rank: float, world: int, device: str) -> tuple[float, float]:
+    """Replicas (one independent instance per rank, no data-path collective): the job's step
+    time is the slowest rank's, its throughput all ranks' updates over that time."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, updates_per_rank * world / (ms / 1e3)
+
+
 def gpu_arm(args):
     import torch
 
@@ -235,14 +248,9 @@ def gpu_arm(args):
             stats_all.append(st)
     launches = lib.disco_kernel_launches() - launches0  # whole timed region (all steps)
     e2e_times = [timed(True)[0] for _ in range(max(1, min(args.steps, 3)))]
-    ms = float(np.mean(times))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
     st = stats_all[-1]
     updates = 2.0 * st["nnodes"] * st["iters"]
-    value = updates * world / (ms / 1e3)
+    ms, value = replica_throughput(float(np.mean(times)), updates, world, "cuda")
     e2e_ms = float(np.mean(e2e_times))
     half_pass_ms = st["dual_ms"] / (2 * st["conv_iters"])
     alg_bytes = st["bytes_per_iter"] / 2.0
@@ -274,13 +282,14 @@ def gpu_arm(args):
                      "alg_bytes_per_launch": alg_bytes, "launch_ms": half_pass_ms, "peak_kind": kind},
         "clocks": clk.summary(),
     }
-    if not args.no_batched:
+    # the comparison sections and the CPU baseline run on single-GPU runs only
+    if world == 1 and not args.no_batched:
         line["batched"] = batched_vs_single(torch)
-    if not args.no_differentiated:
+    if world == 1 and not args.no_differentiated:
         line["differentiated"] = differentiated(torch)
-    if not args.no_quasi_newton:
+    if world == 1 and not args.no_quasi_newton:
         line["quasi_newton"] = quasi_newton_vs_mma(torch, inst, args.split_chunk)
-    if not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     print(json.dumps(line), flush=True)
 
