@@ -235,6 +235,8 @@ void enumerate(const MeshTopo& X, const MeshTopo& Y, const Allowed& A, int threa
                 break;
             }
             case 1: {  // type 1: X triangle t, Y edge e = (a < b), pattern p: corner v -> (t_v, pattern symbol)
+            // per edge at n0 the four candidate bits (m1, a), (m1, b), (m2, a), (m2, b) decide
+            // the three patterns that start at n0
             std::vector<int64_t> cand;
             for (int t = lo; t < hi; ++t) {
                 int m[3] = {TX[3 * t], TX[3 * t + 1], TX[3 * t + 2]};
@@ -243,8 +245,10 @@ void enumerate(const MeshTopo& X, const MeshTopo& Y, const Allowed& A, int threa
                     Y.edge_at.for_each(n0, [&](int e) {
                         const int ab[2] = {Y.edges[e].first, Y.edges[e].second};
                         const int role = ab[0] == n0 ? 0 : 1;  // patterns whose first corner is n0
+                        const bool b1[2] = {A(m[1], ab[0]), A(m[1], ab[1])};
+                        const bool b2[2] = {A(m[2], ab[0]), A(m[2], ab[1])};
                         for (int p = 0; p < 6; ++p)
-                            if (kEdgePattern[p][0] == role && A(m[1], ab[kEdgePattern[p][1]]) && A(m[2], ab[kEdgePattern[p][2]]))
+                            if (kEdgePattern[p][0] == role && b1[kEdgePattern[p][1]] && b2[kEdgePattern[p][2]])
                                 cand.push_back(int64_t(e) * 6 + p);
                     });
                 });
@@ -258,15 +262,22 @@ void enumerate(const MeshTopo& X, const MeshTopo& Y, const Allowed& A, int threa
                 break;
             }
             case 2: {  // type 2: X edge e = (a < b), Y triangle s, pattern p: corner v -> (pattern symbol, s_v)
+            // one walk over the candidate row of each end x0 of the edge; per Y triangle s at a
+            // candidate n0 = s_0 the four bits (a, s_1), (b, s_1), (a, s_2), (b, s_2) decide the
+            // three patterns that start with x0
             std::vector<int64_t> cand;
             for (int e = lo; e < hi; ++e) {
-                int ab[2] = {X.edges[e].first, X.edges[e].second};
+                const int ab[2] = {X.edges[e].first, X.edges[e].second};
                 cand.clear();
-                for (int p = 0; p < 6; ++p) {
-                    int x0 = ab[kEdgePattern[p][0]], x1 = ab[kEdgePattern[p][1]], x2 = ab[kEdgePattern[p][2]];
-                    A.row.for_each(x0, [&](int n0) {
+                for (int first = 0; first < 2; ++first) {
+                    A.row.for_each(ab[first], [&](int n0) {
                         Y.tri_at0.for_each(n0, [&](int s) {
-                            if (A(x1, TY[3 * s + 1]) && A(x2, TY[3 * s + 2])) cand.push_back(int64_t(s) * 6 + p);
+                            const int s1 = TY[3 * s + 1], s2 = TY[3 * s + 2];
+                            const bool b1[2] = {A(ab[0], s1), A(ab[1], s1)};
+                            const bool b2[2] = {A(ab[0], s2), A(ab[1], s2)};
+                            for (int p = 0; p < 6; ++p)
+                                if (kEdgePattern[p][0] == first && b1[kEdgePattern[p][1]] && b2[kEdgePattern[p][2]])
+                                    cand.push_back(int64_t(s) * 6 + p);
                         });
                     });
                 }
