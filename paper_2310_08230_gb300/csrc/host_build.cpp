@@ -332,9 +332,8 @@ struct EdgeEntry {
 
 // BDD segments of a contiguous range of rows, with auxiliary ids local to the range.
 struct RowChunk {
-    std::vector<int32_t> var;   // internal variable id; auxiliaries as -1 - local index
-    std::vector<int32_t> w, wn, d0, d1;
-    std::vector<uint8_t> one, rank;
+    pod_vector<int32_t> var;    // internal variable id; auxiliaries as -1 - local index
+    pod_vector<uint32_t> desc;  // packed layer descriptor (pack_desc)
     std::vector<Segment> segs;  // first_slot local to the chunk
     int64_t n_aux = 0, nodes = 0;
     int max_layers = 0, max_width = 0;
@@ -823,6 +822,15 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     // ---- BDD segments, compiled in parallel over row ranges; slot rank = which of the
     // variable's rows this is (closedness corner 0..2, then projection rows), so it is known
     // locally; auxiliaries get rank 0 in the left segment and 1 in the right one
+    // degree: every free element keeps all its rows (3 closedness + its projection rows); an
+    // auxiliary variable sits in two segments
+    std::vector<uint8_t> deg_free(static_cast<size_t>(P->n_free));
+    parallel_chunks(P->n_free, nth, [&](int, int64_t lo, int64_t hi) {
+        for (int64_t v = lo; v < hi; ++v) {
+            const int64_t i = P->free_orig[v];
+            deg_free[v] = uint8_t(3 + (proj_row[size_t(2) * i] >= 0) + (proj_row[size_t(2) * i + 1] >= 0));
+        }
+    });
     const int nrc = std::max(1, std::min<int>(nth * 8, int(nr / 1024) + 1));
     std::vector<RowChunk> chunks(nrc);
     parallel_chunks(nrc, nth, [&](int, int64_t c0, int64_t c1) {
@@ -834,12 +842,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
             const int64_t r0 = nr * c / nrc, r1 = nr * (c + 1) / nrc;
             auto add_slot = [&](int32_t var, int w, int wn, int d0, int d1, bool one, int rank) {
                 C.var.push_back(var);
-                C.w.push_back(w);
-                C.wn.push_back(wn);
-                C.d0.push_back(d0);
-                C.d1.push_back(d1);
-                C.one.push_back(one ? 1 : 0);
-                C.rank.push_back(uint8_t(rank));
+                C.desc.push_back(pack_desc(w, wn, d0, d1, one, rank, var < 0 ? 2 : deg_free[var]));
                 C.nodes += w;
             };
             for (int64_t r = r0; r < r1 && !C.rc; ++r) {
@@ -945,16 +948,8 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     P->slot_lam0.resize(size_t(ns));
     P->slot_lam0_lo.resize(size_t(ns));
     P->segs.resize(size_t(seg_off[nrc]));
-    P->deg.assign(size_t(nint), 0);
-    // degree: every free element keeps all its rows (3 closedness + its projection rows); an
-    // auxiliary variable sits in two segments
-    parallel_chunks(P->n_free, nth, [&](int, int64_t lo, int64_t hi) {
-        for (int64_t v = lo; v < hi; ++v) {
-            const int64_t i = P->free_orig[v];
-            P->deg[v] = uint8_t(3 + (proj_row[size_t(2) * i] >= 0) + (proj_row[size_t(2) * i + 1] >= 0));
-        }
-    });
-    for (int64_t v = P->n_free; v < nint; ++v) P->deg[v] = 2;
+    P->deg.assign(size_t(nint), 2);
+    std::copy(deg_free.begin(), deg_free.end(), P->deg.begin());
     parallel_chunks(nrc, nth, [&](int, int64_t c0, int64_t c1) {
         for (int64_t c = c0; c < c1; ++c) {
             const RowChunk& C = chunks[c];
@@ -964,7 +959,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                 if (v < 0) v = int32_t(P->n_free + aux_off[c] + (-1 - int64_t(v)));
                 const int dg = P->deg[v];
                 P->slot_var[so + i] = v;
-                P->slot_desc[so + i] = pack_desc(C.w[i], C.wn[i], C.d0[i], C.d1[i], C.one[i], C.rank[i], dg);
+                P->slot_desc[so + i] = C.desc[i];
                 const double l0 = v < P->n_free ? P->cost[P->free_orig[v]] / dg : 0.0;
                 P->slot_lam0[so + i] = float(l0);
                 P->slot_lam0_lo[so + i] = float(l0 - double(float(l0)));
