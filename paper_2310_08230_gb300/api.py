@@ -96,6 +96,35 @@ def candidates_coarse_to_fine(pairs: np.ndarray, c2f_x: np.ndarray, c2f_y: np.nd
     return out
 
 
+def solve_coarse_to_fine(levels, costs, rings: int = 1, iters: int = 100, **opts) -> list[dict]:
+    """Coarse-to-fine solving (Sec. 4): the coarsest level on its full product space, every
+    finer level on the candidates within `rings` edges of the previous level's matching.
+
+    levels: [(TX, TY, c2f_x, c2f_y)] from coarse to fine, c2f_* mapping a level's vertex ids
+    to the next level's (ignored at the finest); costs: per level the (nvx, nvy) pair costs.
+    Returns per level: bound, matching x, its cost, feasibility, the vertex pairs of the
+    matching and the candidate density used."""
+    out = []
+    allowed = None
+    for k, ((TX, TY, cx, cy), d) in enumerate(zip(levels, costs)):
+        nvx, nvy = int(d.shape[0]), int(d.shape[1])
+        s = Solver(TX, TY, d, allowed, **opts)
+        s.dual(iters)
+        lb = s.lower_bound()
+        x, cost, ok = s.primal()
+        pairs = s.point_map(x)
+        s.close()
+        out.append({"lower_bound": lb, "x": x, "cost": cost, "feasible": ok, "pairs": pairs,
+                    "density": 1.0 if allowed is None else float(np.mean(allowed))})
+        if not ok:
+            break
+        if k + 1 < len(levels):
+            nTX, nTY = levels[k + 1][0], levels[k + 1][1]
+            nd = costs[k + 1]
+            allowed = candidates_coarse_to_fine(pairs, cx, cy, rings, nTX, int(nd.shape[0]), nTY, int(nd.shape[1]))
+    return out
+
+
 def default_opts(**kw) -> L.disco_opts:
     o = L.disco_opts()
     L.check(L.lib().disco_default_opts(ctypes.byref(o)), "disco_default_opts")

@@ -158,6 +158,45 @@ def coarse_fine_pair(subdiv: int = 2, dim: int = 16, feat_noise: float = 0.05, s
     return coarse, fine, c2f_x, c2f_y
 
 
+def multilevel_pair(levels=(1, 2, 3), dim: int = 16, feat_noise: float = 0.05, seed: int = 7):
+    """An icosphere pair at several resolutions (subdivision levels), each level's vertices a
+    prefix of the next one's on X; Y is a deformed, relabelled copy at the finest level and
+    every coarser Y keeps the finest labels' relative order through a per-level relabelling.
+    Returns [(Instance, c2f_x, c2f_y)] from coarse to fine, c2f_* mapping the level's vertex ids
+    to the next level's (None for the finest)."""
+    rng = _rng(seed)
+    Xf = M.icosphere(levels[-1])
+    Yf, FXf, FYf, perm = make_pair(Xf, rng, dim, feat_noise, deform=True)
+    out, prev = [], None
+    for lv in levels:
+        X0 = M.icosphere(lv)
+        nc = X0.nv
+        q = rng.permutation(nc).astype(np.int64) if lv != levels[-1] else None
+        if q is None:  # finest level: the generated pair itself
+            inst, yfine = Instance(f"level{lv}-{Xf.nt}T", Xf, Yf, FXf, FYf, perm, None, 100), np.arange(Xf.nv)
+        else:
+            VY = np.empty((nc, 3), np.float32)
+            VY[q] = Yf.V[perm[:nc]]
+            FY = np.empty((nc, dim), np.float32)
+            FY[q] = FYf[perm[:nc]]
+            inst = Instance(f"level{lv}-{X0.nt}T", M.Mesh(Xf.V[:nc].copy(), X0.T), M.Mesh(VY, q[X0.T.astype(np.int64)].astype(np.int32)),
+                            FXf[:nc].copy(), FY, q, None, 100)
+            yfine = np.empty(nc, np.int64)
+            yfine[q] = perm[:nc]  # level Y id -> finest Y id
+        out.append([inst, yfine])
+    # maps to the next level: X ids are prefixes; Y ids through the finest labels
+    res = []
+    for i, (inst, yfine) in enumerate(out):
+        if i + 1 == len(out):
+            res.append((inst, None, None))
+            continue
+        nxt_inst, nxt_yfine = out[i + 1]
+        inv = np.full(int(nxt_yfine.max()) + 1, -1, np.int64)
+        inv[nxt_yfine] = np.arange(len(nxt_yfine))
+        res.append((inst, np.arange(inst.X.nv, dtype=np.int32), inv[yfine].astype(np.int32)))
+    return res
+
+
 def mlp_params(seed: int = 5, sizes=(128, 256, 64)) -> list[np.ndarray]:
     """Seeded weights of the 2-layer feature MLP (W1, b1, W2, b2; N(0, 1/fan_in), zero bias)."""
     rng = _rng(1000 + seed)

@@ -54,3 +54,20 @@ def test_coarse_to_fine(torch):
     hits = np.mean(fine.perm[pf[:, 0]] == pf[:, 1])
     assert hits > 0.9, hits
     sf.close()
+
+
+def test_three_levels(torch):
+    """80 -> 320 -> 1280 triangles, one ring of candidates around each level's matching:
+    every level's matching is feasible, the finest recovers the ground truth on most
+    vertices, and it is solved on a small fraction of its product space."""
+    from paper_2310_08230_gb300.api import solve_coarse_to_fine
+
+    levels = I.multilevel_pair()
+    costs = [P.pair_distance(inst.FX, inst.FY).astype(np.float32) for inst, _, _ in levels]
+    res = solve_coarse_to_fine([(inst.X.T, inst.Y.T, cx, cy) for inst, cx, cy in levels], costs, rings=1, iters=80)
+    assert len(res) == 3 and all(r["feasible"] for r in res)
+    fine = levels[-1][0]
+    pf = res[-1]["pairs"]
+    assert np.mean(fine.perm[pf[:, 0]] == pf[:, 1]) > 0.9
+    assert res[-1]["density"] < 0.05
+    assert all(r["lower_bound"] <= r["cost"] + 1e-6 * abs(r["cost"]) for r in res)
