@@ -190,7 +190,7 @@ int disco_compile_host(const disco_mesh *X, const disco_mesh *Y, const float *d,
                        int64_t nvars);
 
 /*
- * Batched build (BASELINE pattern "batching"; the paper solves one pair at a time): n
+ * Batched build (a serving pattern beside the plain solver; the paper solves one pair at a time): n
  * independent shape pairs in ONE handle and one device store, so that every half-pass of
  * every pair runs in the same kernel launches. X, Y: n meshes each (host); d[i], allowed[i]:
  * per pair as in disco_build (allowed may be NULL, or hold NULL entries). The pairs are

@@ -7,7 +7,7 @@ paper's dual (Sec. 3 pipeline figure, Sec. 4 "Methods"); agreement semantics of
 min-marginal signs, M^j_i > 0 means subproblem j prefers x_i = 0, all
 subproblems with the same sign "agree" (App. A.5).
 
-Reading (listed in the design doc). Round r = 0 .. R-1:
+Reading (the paper defers the heuristic to its citation). Round r = 0 .. R-1:
   1. flush the deferred mean into lambda; compute M on the BDDs restricted to the
      current fixings;
   2. every free variable whose M^j_i are all > tau is fixed to 0, all < -tau to 1;

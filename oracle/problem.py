@@ -12,7 +12,7 @@ Paper passages followed:
   the three vertex pairs, normalised to [0, 1] (Sec. 3.3, Eq. 2 variant);
 * pruning to neighbourhoods of vertex matches (Sec. 4 coarse-to-fine, App.).
 
-Readings where the paper is silent (each listed with its reason in the design doc):
+Readings where the paper is silent (each with its reason):
 * element enumeration and canonical variable order: type (tri-tri,
   X-tri x Y-edge, X-edge x Y-tri, X-tri x Y-vertex, X-vertex x Y-tri), then the
   X element index, the Y element index, then rotation / pattern;
