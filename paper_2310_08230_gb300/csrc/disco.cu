@@ -771,11 +771,23 @@ int build_handle(int32_t n, const disco_mesh* X, const disco_mesh* Y, const floa
     h->plans.resize(size_t(n));
     std::vector<int> rcs(n, DISCO_OK);
     std::vector<std::string> errs(n);
-    parallel_chunks(n, outer, [&](int, int64_t i0, int64_t i1) {
-        for (int64_t i = i0; i < i1; ++i)
-            rcs[i] = build_plan(MeshIn{X[i].nv, X[i].nt, X[i].T, X[i].V}, MeshIn{Y[i].nv, Y[i].nt, Y[i].T, Y[i].V}, hd[i].data(),
-                                (allowed && allowed[i]) ? ha[i].data() : nullptr, o.split_chunk, o.split_max_segments,
-                                inner, &h->plans[i], &errs[i], o.normalize_costs != 0, o.cost_model);
+    // one task per instance, largest first (by candidate pairs), taken dynamically by the
+    // host threads, so that uneven pairs balance
+    std::vector<int64_t> est(static_cast<size_t>(n));
+    for (int32_t i = 0; i < n; ++i) {
+        const int64_t pairs = int64_t(X[i].nv) * Y[i].nv;
+        est[i] = (allowed && allowed[i]) ? std::count_if(ha[i].begin(), ha[i].end(), [](uint8_t a) { return a != 0; })
+                                         : pairs;
+    }
+    std::vector<int32_t> order(static_cast<size_t>(n));
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return est[a] > est[b]; });
+    (void)outer;
+    parallel_chunks(n, n, [&](int c, int64_t, int64_t) {
+        const int32_t i = order[c];
+        rcs[i] = build_plan(MeshIn{X[i].nv, X[i].nt, X[i].T, X[i].V}, MeshIn{Y[i].nv, Y[i].nt, Y[i].T, Y[i].V}, hd[i].data(),
+                            (allowed && allowed[i]) ? ha[i].data() : nullptr, o.split_chunk, o.split_max_segments,
+                            inner, &h->plans[i], &errs[i], o.normalize_costs != 0, o.cost_model);
     });
     for (int32_t i = 0; i < n; ++i)
         if (rcs[i]) return fail(rcs[i], "build: instance " + std::to_string(i) + ": " + errs[i]);
