@@ -547,9 +547,16 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     // of an element, so n is a candidate of m: a stable counting sort on n's position in the
     // candidate row of m, then a stable sort by the larger vertex inside each group.
     std::vector<int64_t> brows(size_t(nvx) + 1, 0);
+    // The larger vertex (m', n') of an edge in bucket m has m' in the closed 1-ring of m (the
+    // edge joins two corners of one element), so the counting key is (position of n in m's
+    // candidate row, rank of m' in m's sorted closed ring); inside a key group only n' is left
+    // to order (a few entries). Any entry outside these sets falls back to a plain sort.
     parallel_chunks(nth * 4, nth, [&](int, int64_t c0, int64_t c1) {
         std::vector<int32_t> pos_of(static_cast<size_t>(nvy), -1);
+        std::vector<int32_t> rank_of(static_cast<size_t>(nvx), -1);
+        std::vector<int32_t> ring;
         std::vector<int64_t> cnt;
+        std::vector<int32_t> key;
         std::vector<EdgeEntry> tmp;
         for (int64_t c = c0; c < c1; ++c)
             for (int64_t m = int64_t(nvx) * c / (nth * 4); m < int64_t(nvx) * (c + 1) / (nth * 4); ++m) {
@@ -557,22 +564,34 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                 const int32_t* cand = A.row.item.data() + A.row.ptr[m];
                 const int ncand = A.row.ptr[m + 1] - A.row.ptr[m];
                 for (int i = 0; i < ncand; ++i) pos_of[cand[i]] = i;
+                ring.assign(1, int32_t(m));
+                X.edge_at.for_each(int(m), [&](int e) {
+                    ring.push_back(X.edges[e].first == m ? X.edges[e].second : X.edges[e].first);
+                });
+                std::sort(ring.begin(), ring.end());
+                const int R = int(ring.size());
+                for (int i = 0; i < R; ++i) rank_of[ring[i]] = i;
+                key.resize(size_t(nb));
                 bool ok = true;
                 for (int64_t e = b0; e < b1 && ok; ++e) {
                     const int32_t p = pos_of[ent[e].lo_n];
-                    ok = p >= 0 && p < ncand && cand[p] == int32_t(ent[e].lo_n);
+                    const int32_t mh = int32_t(ent[e].hi / uint32_t(nvy));
+                    const int32_t q = rank_of[mh];
+                    ok = p >= 0 && p < ncand && cand[p] == int32_t(ent[e].lo_n) && q >= 0 && q < R && ring[q] == mh;
+                    key[e - b0] = p * R + q;
                 }
                 if (!ok) {
                     std::sort(ent.get() + b0, ent.get() + b1);
                 } else {
-                    cnt.assign(size_t(ncand) + 1, 0);
-                    for (int64_t e = b0; e < b1; ++e) ++cnt[size_t(pos_of[ent[e].lo_n]) + 1];
-                    for (int i = 0; i < ncand; ++i) cnt[i + 1] += cnt[i];
+                    const int nk = ncand * R;
+                    cnt.assign(size_t(nk) + 1, 0);
+                    for (int64_t e = 0; e < nb; ++e) ++cnt[size_t(key[e]) + 1];
+                    for (int i = 0; i < nk; ++i) cnt[i + 1] += cnt[i];
                     tmp.resize(size_t(nb));
-                    for (int64_t e = b0; e < b1; ++e) tmp[size_t(cnt[pos_of[ent[e].lo_n]]++)] = ent[e];
-                    // cnt[i] is now the end of group i
+                    for (int64_t e = 0; e < nb; ++e) tmp[size_t(cnt[key[e]]++)] = ent[b0 + e];
+                    // cnt[i] is now the end of key group i: order by hi (n' here) by insertion
                     int64_t g0 = 0;
-                    for (int i = 0; i < ncand; ++i) {
+                    for (int i = 0; i < nk; ++i) {
                         const int64_t g1 = cnt[i];
                         EdgeEntry* g = tmp.data() + g0;
                         const int64_t ng = g1 - g0;
@@ -590,6 +609,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                     }
                     std::copy(tmp.begin(), tmp.end(), ent.get() + b0);
                 }
+                for (int i = 0; i < R; ++i) rank_of[ring[i]] = -1;
                 int64_t r = 0;
                 for (int64_t e = b0; e < b1; ++e)
                     if (e == b0 || !ent[e].same_edge(ent[e - 1])) ++r;
