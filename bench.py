@@ -441,9 +441,19 @@ def batched_vs_single(torch, iters: int = 300, n_pairs: int = 64, split_chunk: i
         L.check(lib.disco_candidates(d.data_ptr(), i.X.nv, i.Y.nv, i.topk, ctypes.byref(mx), ctypes.byref(my),
                                      a.data_ptr(), sptr), "candidates")
 
+    phases = {}
+
+    def mark(name, t0):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        phases[name] = phases.get(name, 0.0) + (t1 - t0) * 1e3
+        return t1
+
     def batched():
+        t = time.perf_counter()
         for k in range(n_pairs):
             costs(k)
+        t = mark("costs_candidates_ms", t)
         MX = (L.disco_mesh * n_pairs)(*[m[0][0] for m in meshes])
         MY = (L.disco_mesh * n_pairs)(*[m[1][0] for m in meshes])
         dp = (ctypes.c_void_p * n_pairs)(*[d.data_ptr() for d in ds])
@@ -451,17 +461,21 @@ def batched_vs_single(torch, iters: int = 300, n_pairs: int = 64, split_chunk: i
         h = ctypes.c_void_p()
         L.check(lib.disco_build_batch(n_pairs, MX, MY, ctypes.cast(dp, ctypes.c_void_p), ctypes.cast(ap, ctypes.c_void_p),
                                       ctypes.byref(opts), ctypes.byref(h)), "build_batch")
+        t = mark("build_ms", t)
         info = L.disco_info_t()
         lib.disco_info(h, ctypes.byref(info))
         L.check(lib.disco_dual(h, iters), "dual")
         lbs = np.zeros(n_pairs)
         L.check(lib.disco_lower_bounds(h, lbs.ctypes.data_as(L.c_double_p), n_pairs), "lbs")
+        t = mark("dual_ms", t)
         x = np.zeros(info.nvars, np.uint8)
         cs = np.zeros(n_pairs)
         st = np.zeros(n_pairs, np.int32)
         lib.disco_primal_batch(h, x.ctypes.data, info.nvars, cs.ctypes.data_as(L.c_double_p),
                                st.ctypes.data_as(L.c_int32_p), n_pairs)
+        t = mark("primal_ms", t)
         lib.disco_free(h)
+        mark("free_ms", t)
         return info.nnodes, lbs, cs, st
 
     def single():
@@ -497,13 +511,16 @@ def batched_vs_single(torch, iters: int = 300, n_pairs: int = 64, split_chunk: i
         return e0.elapsed_time(e1), out
 
     timed(batched)  # warm-up (pool, modules)
+    phases.clear()
     tb, (nodes, lbs_b, cs_b, st_b) = timed(batched)
+    breakdown = {k: round(v, 1) for k, v in phases.items()}
     ts, (nodes_s, lbs_s, cs_s, st_s) = timed(single)
     upd = 2.0 * nodes * iters
     return {"pairs": n_pairs, "iters": iters, "bdd_nodes": int(nodes), "batched_ms": tb, "one_by_one_ms": ts,
             "batched_node_updates_per_s": upd / (tb / 1e3), "one_by_one_node_updates_per_s": upd / (ts / 1e3),
             "speedup": ts / tb, "feasible_batched": int((st_b == 0).sum()), "feasible_one_by_one": int((st_s == 0).sum()),
-            "max_rel_bound_diff": float(np.max(np.abs(lbs_b - lbs_s) / np.maximum(np.abs(lbs_s), 1e-12)))}
+            "max_rel_bound_diff": float(np.max(np.abs(lbs_b - lbs_s) / np.maximum(np.abs(lbs_s), 1e-12))),
+            "batched_breakdown_ms": breakdown}
 
 
 def _oracle_workload(config: str, split_chunk: int):
