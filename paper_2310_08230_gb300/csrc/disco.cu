@@ -316,13 +316,19 @@ int upload(disco_handle* h) {
     }
     // classes up to kFusedMaxW share one launch, longest tiles first; wider ones launch on their own
     {
+        // inside a launch group, pair by pair: the warps running at any moment then touch the
+        // averaging tables of one or two pairs (L2-resident) instead of all of them; a pair's
+        // tiles keep their order, longest first
         auto group_index = [](int W) { return W <= kFusedMaxW ? 0 : W <= 8 ? 1 : W <= 16 ? 2 : 3; };
-        std::vector<int64_t> cnt(size_t(4) * (maxL + 1) + 1, 0);
-        auto key = [&](const TileInfo& t) { return size_t(group_index(t.W)) * (maxL + 1) + size_t(maxL - t.L); };
-        for (const TileInfo& t : tiles) ++cnt[key(t) + 1];
-        for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
+        std::vector<int64_t> cnt(size_t(4) * size_t(ni) * (maxL + 1) + 1, 0);
         std::vector<size_t> perm(tiles.size());
-        for (size_t t = 0; t < tiles.size(); ++t) perm[size_t(cnt[key(tiles[t])]++)] = t;
+        auto key = [&](size_t t) {
+            return (size_t(group_index(tiles[t].W)) * size_t(ni) + size_t(tile_inst[t])) * (maxL + 1) +
+                   size_t(maxL - tiles[t].L);
+        };
+        for (size_t t = 0; t < tiles.size(); ++t) ++cnt[key(t) + 1];
+        for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
+        for (size_t t = 0; t < tiles.size(); ++t) perm[size_t(cnt[key(t)]++)] = t;
         std::vector<TileInfo> t2(tiles.size());
         std::vector<int64_t> f2(tiles.size());
         std::vector<int32_t> c2(tiles.size()), i2(tiles.size());
