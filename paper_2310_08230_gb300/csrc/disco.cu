@@ -140,7 +140,8 @@ struct disco_handle {
         float* lam = nullptr;
         float* lam_lo = nullptr;
         float* acc = nullptr;      // averaging sectors the next pass reads
-        float* nodes = nullptr;    // node costs of the other direction
+        float* nodes = nullptr;    // checkpoint: node costs of the other direction; tape: the
+                                   // node costs the pass stored (the next pass's input)
         int cur = 0;               // which averaging buffer they belong to
     };
     std::vector<Snap> checkpoints, tape;
@@ -1264,6 +1265,12 @@ int primal_all(disco_handle* h, uint8_t* x_out, double* costs, int32_t* status) 
     const int64_t nint = h->nint;
     int rc;
     CK(cudaMemsetAsync(h->state, 0, size_t(nint), s));
+    Trace tr;
+    tr.scope = "primal";
+    auto mark = [&](const char* what) {
+        if (tr.on) cudaStreamSynchronize(s);
+        tr.mark(what);
+    };
     float delta = o.perturb_delta0;
     bool done = nint == 0;
     for (int r = 0; r < o.primal_rounds && !done; ++r) {
@@ -1275,6 +1282,7 @@ int primal_all(disco_handle* h, uint8_t* x_out, double* costs, int32_t* status) 
         if ((rc = h->pass(Pass::BwdMM))) return rc;
         // 2. agreement: every slot strictly positive -> 0, strictly negative -> 1
         CK(launch_decide(h->mm_var, h->deg, h->state, nint, o.tie_tau, h->trial, s));
+        mark("min-marginals, decide");
         // 3. propagate the trial fixings to a fixpoint; an instance whose trial runs into a
         //    conflict keeps its fixings of the previous round (other instances go on)
         const int64_t ni = h->n_inst();
@@ -1304,6 +1312,7 @@ int primal_all(disco_handle* h, uint8_t* x_out, double* costs, int32_t* status) 
             if (!changed) break;
             if (++sweeps > o.propagate_limit) return fail(DISCO_ERR_TIMEOUT, "primal: propagation did not settle");
         }
+        mark("propagation");
         CK(cudaMemcpyAsync(h->state, h->trial, size_t(nint), cudaMemcpyDeviceToDevice, s));
         CK(cudaMemsetAsync(h->counters, 0, size_t(4 * ni) * sizeof(int), s));
         CK(launch_count_free(h->state, h->deg, h->var_inst, nint, h->counters, s));
@@ -1320,6 +1329,7 @@ int primal_all(disco_handle* h, uint8_t* x_out, double* costs, int32_t* status) 
             if ((rc = h->pass(Pass::FwdMMARound))) return rc;
             if ((rc = h->pass(Pass::BwdMMARound))) return rc;
         }
+        mark("perturb, dual");
     }
     // read the fixings back
     std::vector<uint8_t> st(static_cast<size_t>(nint), uint8_t(0));
@@ -1333,6 +1343,7 @@ int primal_all(disco_handle* h, uint8_t* x_out, double* costs, int32_t* status) 
     const int64_t ni = h->n_inst();
     const int hw = host_threads(o);
     const int outer = std::max(1, std::min<int>(int(ni), hw));
+    mark("read back");
     std::vector<uint8_t> x(static_cast<size_t>(h->nelems()), uint8_t(0));
     std::vector<uint8_t> ok(static_cast<size_t>(ni), 0);
     std::vector<double> cs(static_cast<size_t>(ni), 0.0);
@@ -1347,7 +1358,9 @@ int primal_all(disco_handle* h, uint8_t* x_out, double* costs, int32_t* status) 
         if (status) status[i] = ok[i] ? DISCO_OK : DISCO_ERR_PRIMAL_FAILED;
         all = all && ok[i];
     }
+    mark("assemble, check");
     if ((rc = write_out(x_out, x.data(), x.size(), s))) return rc;
+    mark("write");
     return all ? DISCO_OK : fail(DISCO_ERR_PRIMAL_FAILED, "primal: no feasible assignment within the round limit");
 }
 
@@ -1396,9 +1409,9 @@ int disco_info(disco_handle* h, disco_info_t* info) {
 // ---------------------------------------------------------------------------------------
 // Differentiation: the bound after T iterations from lambda^0 = c / |J| as a function of the
 // pair costs. disco_record runs the iterations keeping a checkpoint every few iterations;
-// disco_grad replays each block from its checkpoint recording every half-pass's inputs,
-// then walks the passes backwards: each is recomputed by its normal kernel (bit-identical
-// mins) and reversed by its adjoint kernel (adjoint.cu).
+// disco_grad replays each block from its checkpoint, recording every half-pass's inputs and
+// the node costs it stores, then walks the passes backwards, reversing each by its adjoint
+// kernel (adjoint.cu) on the recorded values (bit-identical mins).
 namespace {
 
 using Snap = disco_handle::Snap;
@@ -1418,12 +1431,13 @@ int d2d(void* dst, const void* src, size_t bytes, cudaStream_t s) {
     return DISCO_OK;
 }
 
-// Saves lambda, the averaging sectors the next pass reads and the given node costs.
+// Saves lambda, the averaging sectors the next pass reads and the given node costs (none
+// when nodes is null).
 int save_snap(disco_handle* h, Snap* s, const float* nodes) {
     int rc;
     const size_t ns = size_t(h->nslots_tile) * 4, na = size_t(h->nint) * kAccStride * 4, nn = size_t(h->nnodes_tile) * 4;
     if ((rc = d2d(s->lam, h->lam, ns, h->stream)) || (rc = d2d(s->lam_lo, h->lam_lo, ns, h->stream)) ||
-        (rc = d2d(s->acc, h->acc[h->cur], na, h->stream)) || (rc = d2d(s->nodes, nodes, nn, h->stream)))
+        (rc = d2d(s->acc, h->acc[h->cur], na, h->stream)) || (nodes && (rc = d2d(s->nodes, nodes, nn, h->stream))))
         return rc;
     s->cur = h->cur;
     return DISCO_OK;
@@ -1442,12 +1456,22 @@ int load_snap(disco_handle* h, const Snap& s, float* nodes) {
 AdjArgs adj_args(disco_handle* h) {
     AdjArgs a{};
     a.tiles = h->tiles;
-    a.ntiles = int32_t(h->ntiles);
     a.var = h->var;
     a.desc = h->desc;
     a.lbar = h->lbar;
     a.omega = h->opts.omega;
     return a;
+}
+
+// One adjoint launch per width group, in tile order (tiles are independent).
+cudaError_t launch_adjoint_all(disco_handle* h, Adj kind, AdjArgs a) {
+    for (const WidthClass& c : h->classes) {
+        a.tile0 = c.tile0;
+        a.tile_end = c.tile_end;
+        const cudaError_t e = launch_adjoint(kind, c.W, a, h->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 int64_t pair_cost_count(const disco_handle* h) {
@@ -1527,35 +1551,38 @@ int disco_grad(disco_handle* h, float* dlb_dpair_costs, int64_t n) {
         a.acc_in = h->acc[h->cur];
         a.own = h->F;
         a.mubar_out = h->mub[0];
-        CK(launch_adjoint(Adj::Bound, a, s));
+        CK(launch_adjoint_all(h, Adj::Bound, a));
     }
     mark("bound adjoint");
     int nx = 0;  // mub[nx]: adjoint of the deferred means the pass being reversed produced
     for (int k = nck - 1; k >= 0; --k) {
         if ((rc = load_snap(h, h->checkpoints[k], h->B))) return rc;
         const int nit = std::min(G, T - k * G);
+        // replay: each half-pass's inputs (lambda, the sectors it reads) and the node costs it
+        // stores go to the tape; the node costs it reads are the previous pass's (or the
+        // checkpoint's) stored ones
         for (int t = 0; t < nit; ++t)
             for (int dir = 0; dir < 2; ++dir) {
-                if ((rc = save_snap(h, &h->tape[2 * t + dir], dir == 0 ? h->B : h->F))) return rc;
+                Snap& tp = h->tape[2 * t + dir];
+                if ((rc = save_snap(h, &tp, nullptr))) return rc;
                 if ((rc = h->pass(dir == 0 ? Pass::FwdMMA : Pass::BwdMMA))) return rc;
+                if ((rc = d2d(tp.nodes, dir == 0 ? h->F : h->B, size_t(h->nnodes_tile) * 4, s))) return rc;
             }
         mark("block replay");
         for (int e = 2 * nit - 1; e >= 0; --e) {
             const Snap& tp = h->tape[e];
             const bool fwd = (e % 2) == 0;
-            if ((rc = load_snap(h, tp, fwd ? h->B : h->F))) return rc;
-            if ((rc = h->pass(fwd ? Pass::FwdMMA : Pass::BwdMMA))) return rc;  // recompute
             AdjArgs a = adj_args(h);
             a.lam_in = tp.lam;
             a.lam_in_lo = tp.lam_lo;
             a.acc_in = tp.acc;
-            a.other = tp.nodes;
-            a.own = fwd ? h->F : h->B;
+            a.other = e == 0 ? h->checkpoints[k].nodes : h->tape[e - 1].nodes;
+            a.own = tp.nodes;
             a.own_bar = fwd ? h->Fbar : h->Bbar;
             a.other_bar = fwd ? h->Bbar : h->Fbar;
             a.mubar_next = h->mub[nx];
             a.mubar_out = h->mub[nx ^ 1];
-            CK(launch_adjoint(fwd ? Adj::Fwd : Adj::Bwd, a, s));
+            CK(launch_adjoint_all(h, fwd ? Adj::Fwd : Adj::Bwd, a));
             nx ^= 1;
         }
         mark("block reverse");
@@ -1571,7 +1598,7 @@ int disco_grad(disco_handle* h, float* dlb_dpair_costs, int64_t n) {
         a.acc_in = c0.acc;
         a.own = h->B;
         a.own_bar = h->Bbar;
-        CK(launch_adjoint(Adj::Reset, a, s));
+        CK(launch_adjoint_all(h, Adj::Reset, a));
     }
     CK(launch_adj_cost(h->var, h->desc, h->nslots_tile, h->lbar, h->deg, h->nint, h->mub[nx ^ 1], h->cbar, s));
     if ((rc = load_snap(h, h->final_state, h->B))) return rc;

@@ -459,6 +459,8 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         std::vector<double> cmaxs(nth, 0.0);
         std::vector<int> bad(nth, 0);
         parallel_chunks(nv, nth, [&](int c, int64_t lo, int64_t hi) {
+            double mx = 0.0;  // per-chunk results are written once (no false sharing)
+            int nonfinite = 0;
             for (int64_t i = lo; i < hi; ++i) {
                 double x = 0.0;
                 if (cost_model == 1) {
@@ -470,10 +472,12 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                     for (int v = 0; v < 3; ++v) x += double(d[size_t(P->vm[3 * i + v]) * nvy + P->vn[3 * i + v]]);
                     x /= 3.0;
                 }
-                if (!(x >= 0.0) || x > 3.0e38) bad[c] = 1;
+                if (!(x >= 0.0) || x > 3.0e38) nonfinite = 1;
                 P->cost[i] = x;
-                cmaxs[c] = std::max(cmaxs[c], x);
+                mx = std::max(mx, x);
             }
+            cmaxs[c] = mx;
+            bad[c] = nonfinite;
         });
         for (int c = 0; c < nth; ++c)
             if (bad[c]) { *err = "pair costs must be finite and >= 0"; return DISCO_ERR_INVALID_ARG; }
@@ -621,8 +625,14 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     P->n_closed = n_closed;
     P->row_ptr.assign(size_t(n_closed), 0);
     // projection entries: elements whose X (Y) side is a triangle; all rows are sized once
+    std::vector<int64_t> nproj_part(size_t(nth), 0);
+    parallel_chunks(nv, nth, [&](int c, int64_t lo, int64_t hi) {
+        int64_t k = 0;
+        for (int64_t i = lo; i < hi; ++i) k += (E.type[i] == 0) ? 2 : 1;
+        nproj_part[size_t(c)] += k;
+    });
     int64_t nproj_entries = 0;
-    for (int64_t i = 0; i < nv; ++i) nproj_entries += (E.type[i] == 0) ? 2 : 1;
+    for (int64_t k : nproj_part) nproj_entries += k;
     P->row_var.resize(size_t(ne + nproj_entries));
     P->row_coef.resize(size_t(ne + nproj_entries));
     pod_vector<int32_t> row_ent(static_cast<size_t>(ne + nproj_entries));  // corner (0..2) or 3 + side
@@ -657,7 +667,10 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
 
     tr.mark("closedness rows");
     // ---- projection rows (counting sort keeps the element order inside a row)
-    std::vector<int32_t> proj_row(size_t(2) * nv, -1);  // element -> X / Y projection row
+    pod_vector<int32_t> proj_row(size_t(2) * nv);  // element -> X / Y projection row (-1: none)
+    parallel_chunks(2 * nv, nth, [&](int, int64_t lo, int64_t hi) {
+        std::fill(proj_row.begin() + lo, proj_row.begin() + hi, -1);
+    });
     int64_t proj_end = ne;
     for (int side = 0; side < 2; ++side) {
         const int ntri = side == 0 ? X.nt : Y.nt;
@@ -823,18 +836,55 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         }
         if (any([&](int t) { return bad[t] != 0; })) { *err = "presolve: a row has no solution"; return DISCO_ERR_INFEASIBLE; }
     }
-    for (int64_t r = 0; r < nr; ++r)
-        if (rs[r].np + rs[r].nn == 0 && rs[r].res != 0) { *err = "presolve: violated row"; return DISCO_ERR_INFEASIBLE; }
+    {
+        std::atomic<bool> violated{false};
+        parallel_chunks(nr, nth, [&](int, int64_t lo, int64_t hi) {
+            for (int64_t r = lo; r < hi; ++r)
+                if (rs[r].np + rs[r].nn == 0 && rs[r].res != 0) violated.store(true, std::memory_order_relaxed);
+        });
+        if (violated.load()) { *err = "presolve: violated row"; return DISCO_ERR_INFEASIBLE; }
+    }
     tr.mark("presolve");
-    P->constant = 0.0;
-    std::vector<int32_t> internal(size_t(nv), -1);
-    P->free_orig.clear();
-    for (int64_t i = 0; i < nv; ++i) {
-        if (P->fixed[i] == 1) P->constant += P->cost[i];
-        if (P->fixed[i] < 0) {
-            internal[i] = int32_t(P->free_orig.size());
-            P->free_orig.push_back(int32_t(i));
+    // internal ids of the free variables in element order, and the constant (costs of the
+    // variables fixed to 1), over fixed-size blocks so that the sums do not depend on the
+    // thread count
+    pod_vector<int32_t> internal(static_cast<size_t>(nv));
+    {
+        constexpr int64_t kBlock = int64_t(1) << 16;
+        const int64_t nb = (nv + kBlock - 1) / kBlock;
+        std::vector<int64_t> nfree(size_t(nb) + 1, 0);
+        std::vector<double> part(size_t(nb), 0.0);
+        parallel_chunks(nb, nth, [&](int, int64_t b0, int64_t b1) {
+            for (int64_t b = b0; b < b1; ++b) {
+                int64_t k = 0;
+                double c = 0.0;
+                for (int64_t i = b * kBlock; i < std::min(nv, (b + 1) * kBlock); ++i) {
+                    if (P->fixed[i] == 1) c += P->cost[i];
+                    k += P->fixed[i] < 0;
+                }
+                nfree[size_t(b) + 1] = k;
+                part[size_t(b)] = c;
+            }
+        });
+        P->constant = 0.0;
+        for (int64_t b = 0; b < nb; ++b) {
+            nfree[size_t(b) + 1] += nfree[size_t(b)];
+            P->constant += part[size_t(b)];
         }
+        P->free_orig.resize(size_t(nfree[size_t(nb)]));
+        parallel_chunks(nb, nth, [&](int, int64_t b0, int64_t b1) {
+            for (int64_t b = b0; b < b1; ++b) {
+                int64_t k = nfree[size_t(b)];
+                for (int64_t i = b * kBlock; i < std::min(nv, (b + 1) * kBlock); ++i) {
+                    if (P->fixed[i] < 0) {
+                        internal[size_t(i)] = int32_t(k);
+                        P->free_orig[size_t(k++)] = int32_t(i);
+                    } else {
+                        internal[size_t(i)] = -1;
+                    }
+                }
+            }
+        });
     }
     P->n_free = int64_t(P->free_orig.size());
 
@@ -851,15 +901,28 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
             deg_free[v] = uint8_t(3 + (proj_row[size_t(2) * i] >= 0) + (proj_row[size_t(2) * i + 1] >= 0));
         }
     });
+    // row chunks of about equal entry counts (projection rows are long, closedness rows
+    // short), taken dynamically by the threads; the result does not depend on the chunking
     const int nrc = std::max(1, std::min<int>(nth * 8, int(nr / 1024) + 1));
+    std::vector<int64_t> row_cut(size_t(nrc) + 1, nr);
+    {
+        const int64_t ntot = P->row_ptr[size_t(nr)];
+        row_cut[0] = 0;
+        for (int c = 1; c < nrc; ++c) {
+            const int64_t want = ntot * c / nrc;
+            row_cut[size_t(c)] = std::max<int64_t>(
+                row_cut[size_t(c) - 1],
+                int64_t(std::lower_bound(P->row_ptr.begin(), P->row_ptr.begin() + nr, want) - P->row_ptr.begin()));
+        }
+    }
     std::vector<RowChunk> chunks(nrc);
-    parallel_chunks(nrc, nth, [&](int, int64_t c0, int64_t c1) {
+    parallel_tasks(nrc, nth, [&](int64_t c) {
         std::vector<int32_t> fv, lo, wd;
         std::vector<int8_t> fc;
         std::vector<uint8_t> fr;
-        for (int64_t c = c0; c < c1; ++c) {
+        {
             RowChunk& C = chunks[c];
-            const int64_t r0 = nr * c / nrc, r1 = nr * (c + 1) / nrc;
+            const int64_t r0 = row_cut[size_t(c)], r1 = row_cut[size_t(c) + 1];
             auto add_slot = [&](int32_t var, int w, int wn, int d0, int d1, bool one, int rank) {
                 C.var.push_back(var);
                 C.desc.push_back(pack_desc(w, wn, d0, d1, one, rank, var < 0 ? 2 : deg_free[var]));
@@ -970,8 +1033,8 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     P->segs.resize(size_t(seg_off[nrc]));
     P->deg.assign(size_t(nint), 2);
     std::copy(deg_free.begin(), deg_free.end(), P->deg.begin());
-    parallel_chunks(nrc, nth, [&](int, int64_t c0, int64_t c1) {
-        for (int64_t c = c0; c < c1; ++c) {
+    parallel_tasks(nrc, nth, [&](int64_t c) {
+        {
             const RowChunk& C = chunks[c];
             const int64_t so = slot_off[c];
             for (size_t i = 0; i < C.var.size(); ++i) {

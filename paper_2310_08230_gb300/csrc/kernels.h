@@ -60,7 +60,7 @@ struct KArgs {
 // from the previous pass, written).
 struct AdjArgs {
     const TileInfo* tiles;
-    int32_t ntiles;
+    int32_t tile0, tile_end;  // the launch's tiles (one width group)
     const uint32_t* var;
     const uint32_t* desc;
     const float* lam_in;
@@ -83,7 +83,9 @@ enum class Adj {
     Reset,  // initial backward min-sum on lambda (lbar accumulated)
 };
 
-cudaError_t launch_adjoint(Adj kind, const AdjArgs& a, cudaStream_t s);
+// group: 0 = the fused widths 2, 4, 6; else 8, 16 or 32 (a.tile0 .. a.tile_end must hold
+// only tiles of that group).
+cudaError_t launch_adjoint(Adj kind, int group, const AdjArgs& a, cudaStream_t s);
 // cbar[v] = (sum over v's slots of lbar) / deg[v], via a rank-sector table (tab).
 cudaError_t launch_adj_cost(const uint32_t* var, const uint32_t* desc, int64_t nslots, const float* lbar,
                             const uint8_t* deg, int64_t nint, float* tab, float* cbar, cudaStream_t s);

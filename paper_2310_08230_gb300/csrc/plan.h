@@ -145,6 +145,26 @@ inline void parallel_chunks(int64_t n, int nch, F body) {
     for (auto& th : pool) th.join();
 }
 
+// Runs body(i) for i in [0, n) as dynamically scheduled tasks on up to nth threads (in
+// order on the calling thread when nth <= 1 or called from inside a pool task).
+template <class F>
+inline void parallel_tasks(int64_t n, int nth, F body) {
+    if (nth <= 1 || n < 2) {
+        for (int64_t i = 0; i < n; ++i) body(i);
+        return;
+    }
+    const std::function<void(int)> task = [&](int i) { body(int64_t(i)); };
+    if (WorkerPool::get().try_run(int(n), task)) return;
+    std::atomic<int64_t> next{0};
+    auto worker = [&] {
+        for (int64_t i; (i = next.fetch_add(1)) < n;) body(i);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < std::min<int64_t>(nth, n); ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+}
+
 // Phase timer: with DISCO_TRACE set in the environment, each phase's wall time goes to stderr.
 struct Trace {
     const char* scope = "build";
