@@ -555,15 +555,16 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     // edge joins two corners of one element), so the counting key is (position of n in m's
     // candidate row, rank of m' in m's sorted closed ring); inside a key group only n' is left
     // to order (a few entries). Any entry outside these sets falls back to a plain sort.
-    parallel_chunks(nth * 4, nth, [&](int, int64_t c0, int64_t c1) {
+    const int nbc = std::max(1, std::min(nth * 16, nvx));  // bucket ranges, taken dynamically
+    parallel_tasks(nbc, nth, [&](int64_t c) {
         std::vector<int32_t> pos_of(static_cast<size_t>(nvy), -1);
         std::vector<int32_t> rank_of(static_cast<size_t>(nvx), -1);
         std::vector<int32_t> ring;
         std::vector<int64_t> cnt;
         std::vector<int32_t> key;
         std::vector<EdgeEntry> tmp;
-        for (int64_t c = c0; c < c1; ++c)
-            for (int64_t m = int64_t(nvx) * c / (nth * 4); m < int64_t(nvx) * (c + 1) / (nth * 4); ++m) {
+        {
+            for (int64_t m = int64_t(nvx) * c / nbc; m < int64_t(nvx) * (c + 1) / nbc; ++m) {
                 const int64_t b0 = bstart[m], b1 = bstart[m + 1], nb = b1 - b0;
                 const int32_t* cand = A.row.item.data() + A.row.ptr[m];
                 const int ncand = A.row.ptr[m + 1] - A.row.ptr[m];
@@ -619,11 +620,12 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                     if (e == b0 || !ent[e].same_edge(ent[e - 1])) ++r;
                 brows[m + 1] = r;
             }
+        }
     });
     for (int m = 0; m < nvx; ++m) brows[m + 1] += brows[m];
     const int64_t n_closed = brows[nvx];
     P->n_closed = n_closed;
-    P->row_ptr.assign(size_t(n_closed), 0);
+    P->row_ptr.resize(size_t(n_closed));  // every row start is written below
     // projection entries: elements whose X (Y) side is a triangle; all rows are sized once
     std::vector<int64_t> nproj_part(size_t(nth), 0);
     parallel_chunks(nv, nth, [&](int c, int64_t lo, int64_t hi) {
@@ -636,8 +638,14 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     P->row_var.resize(size_t(ne + nproj_entries));
     P->row_coef.resize(size_t(ne + nproj_entries));
     pod_vector<int32_t> row_ent(static_cast<size_t>(ne + nproj_entries));  // corner (0..2) or 3 + side
-    pod_vector<int32_t> elem_row(static_cast<size_t>(ne));     // element corner -> its closedness row
-    pod_vector<int8_t> elem_coef(static_cast<size_t>(ne));     // and its coefficient there
+    // the rows of every element in one record (presolve reads all of them per fixing):
+    // closed[v] = closedness row of corner v << 1 | (coefficient there > 0); proj[side] = the
+    // X / Y projection row, -1 if none
+    struct ElemRows {
+        uint32_t closed[3];
+        int32_t proj[2];
+    };
+    pod_vector<ElemRows> er(static_cast<size_t>(nv));
     // presolve state of every row: residual right-hand side, free +1 / -1 entries
     struct RowState {
         int32_t res, np, nn, queued;
@@ -656,8 +664,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                 P->row_var[e] = int32_t(id / 3);
                 P->row_coef[e] = neg ? -1 : 1;
                 row_ent[e] = int32_t(id % 3);
-                elem_row[id] = int32_t(r);
-                elem_coef[id] = P->row_coef[e];
+                er[id / 3].closed[id % 3] = uint32_t(r) << 1 | (neg ? 0u : 1u);
                 ++(neg ? rs[r].nn : rs[r].np);
             }
         }
@@ -666,56 +673,57 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     P->rhs.assign(size_t(n_closed), 0);
 
     tr.mark("closedness rows");
-    // ---- projection rows (counting sort keeps the element order inside a row)
-    pod_vector<int32_t> proj_row(size_t(2) * nv);  // element -> X / Y projection row (-1: none)
-    parallel_chunks(2 * nv, nth, [&](int, int64_t lo, int64_t hi) {
-        std::fill(proj_row.begin() + lo, proj_row.begin() + hi, -1);
-    });
-    int64_t proj_end = ne;
-    for (int side = 0; side < 2; ++side) {
-        const int ntri = side == 0 ? X.nt : Y.nt;
-        auto tri_of = [&](int64_t i) -> int {
-            const int ty = E.type[i];
-            if (side == 0) return (ty == 0 || ty == 1 || ty == 3) ? E.xe[i] : -1;
-            return (ty == 0 || ty == 2 || ty == 4) ? E.ye[i] : -1;
-        };
-        std::vector<std::vector<int64_t>> cnt(nth, std::vector<int64_t>(size_t(ntri), 0));
-        parallel_chunks(nv, nth, [&](int c, int64_t lo, int64_t hi) {
-            for (int64_t i = lo; i < hi; ++i) {
-                const int t = tri_of(i);
-                if (t >= 0) ++cnt[c][t];
-            }
-        });
-        const int64_t base = proj_end;
-        const int64_t row0 = int64_t(P->row_ptr.size());
-        std::vector<std::vector<int64_t>> off(nth, std::vector<int64_t>(size_t(ntri), 0));
-        int64_t run = base;
-        for (int t = 0; t < ntri; ++t) {
-            int64_t tot = 0;
-            for (int c = 0; c < nth; ++c) tot += cnt[c][t];
-            if (tot == 0) { *err = "a triangle has no matching element"; return DISCO_ERR_INFEASIBLE; }
-            rs[size_t(row0 + t)] = RowState{1, int32_t(tot), 0, 0};
-            P->row_ptr.push_back(run);
-            for (int c = 0; c < nth; ++c) {
-                off[c][t] = run;
-                run += cnt[c][t];
-            }
+    // ---- projection rows (counting sort keeps the element order inside a row): one row per X
+    // triangle, then one per Y triangle; one counting and one scatter pass serve both sides
+    const int ntx = X.nt, ntri = X.nt + Y.nt;        // row t: X triangle t, or Y triangle t - ntx
+    auto tris_of = [&](int64_t i, int* a, int* b) {
+        const int ty = E.type[i];
+        *a = (ty == 0 || ty == 1 || ty == 3) ? E.xe[i] : -1;
+        *b = (ty == 0 || ty == 2 || ty == 4) ? ntx + E.ye[i] : -1;
+    };
+    std::vector<std::vector<int64_t>> pcnt(nth, std::vector<int64_t>(size_t(ntri), 0));
+    parallel_chunks(nv, nth, [&](int c, int64_t lo, int64_t hi) {
+        int64_t* k = pcnt[c].data();
+        for (int64_t i = lo; i < hi; ++i) {
+            int a, b;
+            tris_of(i, &a, &b);
+            if (a >= 0) ++k[a];
+            if (b >= 0) ++k[b];
         }
-        proj_end = run;
-        parallel_chunks(nv, nth, [&](int c, int64_t lo, int64_t hi) {
-            for (int64_t i = lo; i < hi; ++i) {
-                const int t = tri_of(i);
+    });
+    const int64_t row0 = int64_t(P->row_ptr.size());
+    std::vector<std::vector<int64_t>> poff(nth, std::vector<int64_t>(size_t(ntri), 0));
+    int64_t proj_end = ne;
+    for (int t = 0; t < ntri; ++t) {
+        int64_t tot = 0;
+        for (int c = 0; c < nth; ++c) tot += pcnt[c][t];
+        if (tot == 0) { *err = "a triangle has no matching element"; return DISCO_ERR_INFEASIBLE; }
+        rs[size_t(row0 + t)] = RowState{1, int32_t(tot), 0, 0};
+        P->row_ptr.push_back(proj_end);
+        for (int c = 0; c < nth; ++c) {
+            poff[c][t] = proj_end;
+            proj_end += pcnt[c][t];
+        }
+    }
+    parallel_chunks(nv, nth, [&](int c, int64_t lo, int64_t hi) {
+        int64_t* o = poff[c].data();
+        for (int64_t i = lo; i < hi; ++i) {
+            int ab[2];
+            tris_of(i, &ab[0], &ab[1]);
+            for (int side = 0; side < 2; ++side) {
+                const int t = ab[side];
+                er[size_t(i)].proj[side] = t >= 0 ? int32_t(row0 + t) : -1;
                 if (t < 0) continue;
-                const int64_t pos = off[c][t]++;
+                const int64_t pos = o[t]++;
                 P->row_var[size_t(pos)] = int32_t(i);
                 P->row_coef[size_t(pos)] = 1;
                 row_ent[size_t(pos)] = 3 + side;
-                proj_row[size_t(2) * i + side] = int32_t(row0 + t);
             }
-        });
-        P->rhs.resize(P->rhs.size() + size_t(ntri), 1);
-        (side == 0 ? P->n_projx : P->n_projy) = ntri;
-    }
+        }
+    });
+    P->rhs.resize(P->rhs.size() + size_t(ntri), 1);
+    P->n_projx = X.nt;
+    P->n_projy = Y.nt;
     P->nrows = int64_t(P->rhs.size());
     if (proj_end != int64_t(P->row_var.size())) { *err = "internal: projection entry count"; return DISCO_ERR_INVALID_ARG; }
     P->row_ptr.push_back(proj_end);
@@ -803,12 +811,13 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                         if (f == val) continue;
                         if (f >= 0) { bad[u] = 1; return; }
                         P->fixed[v] = val;
+                        const ElemRows& x = er[size_t(v)];
                         for (int q = 0; q < 3; ++q) {
-                            const int32_t r = elem_row[3 * int64_t(v) + q];
-                            upd[u][row_owner[size_t(r) >> 12]].push_back(Upd{r, val | (elem_coef[3 * int64_t(v) + q] > 0 ? 2 : 0)});
+                            const int32_t r = int32_t(x.closed[q] >> 1);
+                            upd[u][row_owner[size_t(r) >> 12]].push_back(Upd{r, val | ((x.closed[q] & 1u) ? 2 : 0)});
                         }
                         for (int side = 0; side < 2; ++side) {
-                            const int32_t r = proj_row[size_t(2) * v + side];
+                            const int32_t r = x.proj[side];
                             if (r >= 0) upd[u][row_owner[size_t(r) >> 12]].push_back(Upd{r, val | 2});
                         }
                     }
@@ -835,6 +844,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
             });
         }
         if (any([&](int t) { return bad[t] != 0; })) { *err = "presolve: a row has no solution"; return DISCO_ERR_INFEASIBLE; }
+        if (tr.on) std::fprintf(stderr, "disco build  presolve rounds: %d\n", rounds);
     }
     {
         std::atomic<bool> violated{false};
@@ -898,7 +908,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     parallel_chunks(P->n_free, nth, [&](int, int64_t lo, int64_t hi) {
         for (int64_t v = lo; v < hi; ++v) {
             const int64_t i = P->free_orig[v];
-            deg_free[v] = uint8_t(3 + (proj_row[size_t(2) * i] >= 0) + (proj_row[size_t(2) * i + 1] >= 0));
+            deg_free[v] = uint8_t(3 + (er[size_t(i)].proj[0] >= 0) + (er[size_t(i)].proj[1] >= 0));
         }
     });
     // row chunks of about equal entry counts (projection rows are long, closedness rows
@@ -939,7 +949,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                     fc.push_back(P->row_coef[e]);
                     // projection rank: 3 for the first projection row of the element, 4 for the second
                     int rk = row_ent[e];
-                    if (rk == 4 && proj_row[size_t(2) * v] < 0) rk = 3;
+                    if (rk == 4 && er[size_t(v)].proj[0] < 0) rk = 3;
                     fr.push_back(uint8_t(rk));
                 }
                 const int n = int(fv.size());
