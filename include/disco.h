@@ -92,7 +92,12 @@ typedef struct {
                                  d(m_v, n_v) with A the mixed vertex areas (Meyer et al. 2003;
                                  needs the meshes' V) and d the pair distances
                                  (disco_pair_distances) */
-    int32_t reserved[1];
+    int32_t tile_order;       /* [0] order of the warp tiles in the device store (results are the
+                                 same, up to the order of the bound's FP64 tile sums): 0 = by
+                                 size (2 when both averaging tables exceed 64 MB, else 1);
+                                 1 = width class, then length, over each instance; 2 = blocks
+                                 of 4096 segments in row order (table locality), each by width
+                                 class and length */
 } disco_opts;
 
 typedef struct {

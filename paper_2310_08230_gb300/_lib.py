@@ -37,7 +37,7 @@ class disco_opts(ctypes.Structure):
         ("propagate_limit", ctypes.c_int32), ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
         ("host_threads", ctypes.c_int32), ("split_max_segments", ctypes.c_int32),
         ("graph_iters", ctypes.c_int32), ("autotune", ctypes.c_int32), ("normalize_costs", ctypes.c_int32),
-        ("qn_memory", ctypes.c_int32), ("cost_model", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1),
+        ("qn_memory", ctypes.c_int32), ("cost_model", ctypes.c_int32), ("tile_order", ctypes.c_int32),
     ]
 
 

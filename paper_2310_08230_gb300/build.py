@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libdisco.so")
-SOURCES = ["disco.cu", "kernels.cu", "adjoint.cu", "qn.cu", "host_build.cpp", "noalloc.cu"]
+SOURCES = ["disco.cu", "kernels.cu", "adjoint.cu", "qn.cu", "store.cu", "host_build.cpp", "noalloc.cu"]
 HEADERS = ["plan.h", "kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -255,6 +255,11 @@ constexpr bool classes_have_kernels() {
 }
 static_assert(classes_have_kernels(), "every width class needs a kernel instantiation");
 
+// Tile order for table locality (see upload): segments per block, and the size of both
+// averaging tables above which it applies (half of the 126 MB L2).
+constexpr int64_t kLocalityBlock = 4096;
+constexpr int64_t kLocalityTableBytes = int64_t(64) << 20;
+
 int width_class(int w) {
     for (int c : kWidthClasses)
         if (w <= c) return c;
@@ -291,41 +296,111 @@ int upload(disco_handle* h) {
     std::vector<TileSeg> order;
     int maxL = 1;
     for (int64_t i = 0; i < ni; ++i) maxL = std::max(maxL, h->plans[i].max_layers);
-    for (int64_t i = 0; i < ni; ++i) {
+    // Averaging tables far larger than L2 (big batches): every slot's sector gather and
+    // scatter would miss if the warps running at one time held segments from all over the
+    // instance. Then segments are cut into blocks of kLocalityBlock in plan order (rows of
+    // nearby X vertices and triangles touch nearby variables), each block is sorted by width
+    // class and length, and tiles follow the blocks. Otherwise (tables L2-resident) segments
+    // are sorted by width class and length over the whole instance. Instances are ordered in
+    // parallel, then concatenated in instance order.
+    int64_t nint_all = 0;
+    for (int64_t i = 0; i < ni; ++i) nint_all += h->plans[i].n_free + h->plans[i].n_aux;
+    const bool locality = h->opts.tile_order == 2 ||
+                          (h->opts.tile_order == 0 && 2 * nint_all * kAccStride * int64_t(sizeof(float)) > kLocalityTableBytes);
+    auto launch_group = [](int W) { return W <= kFusedMaxW ? 0 : W <= 8 ? 1 : W <= 16 ? 2 : 3; };
+    struct InstTiles {
+        std::vector<int64_t> seg;  // the instance's segments in tile order
+        std::vector<TileInfo> tiles;
+        std::vector<int64_t> first;  // into seg
+        std::vector<int32_t> count;
+    };
+    std::vector<InstTiles> per(static_cast<size_t>(ni));
+    parallel_tasks(ni, nth, [&](int64_t i) {
         const Plan& P = h->plans[i];
+        InstTiles& R = per[size_t(i)];
         const int64_t nseg = int64_t(P.segs.size());
-        std::vector<int64_t> cnt(size_t(kMaxWidth + 1) * (maxL + 1) + 1, 0);
-        auto key = [&](const Segment& sg) {  // class ascending, length descending
-            return size_t(class_index(width_class(sg.max_width))) * (maxL + 1) + size_t(maxL - sg.n_layers);
+        R.seg.resize(size_t(nseg));
+        auto cut_tiles = [&](int64_t k0, int64_t k1) {  // tiles of one run; none straddles a class
+            for (int64_t k = k0; k < k1;) {
+                const int W = width_class(P.segs[R.seg[k]].max_width);
+                const int L = P.segs[R.seg[k]].n_layers;
+                const int64_t first = k;
+                int q = 0;
+                while (q < 32 && k < k1 && width_class(P.segs[R.seg[k]].max_width) == W) ++q, ++k;
+                R.tiles.push_back(TileInfo{0, 0, L, W});
+                R.first.push_back(first);
+                R.count.push_back(q);
+            }
         };
-        for (const Segment& sg : P.segs) ++cnt[key(sg) + 1];
-        for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
-        const size_t o0 = order.size();
-        order.resize(o0 + size_t(nseg));
-        for (int64_t k = 0; k < nseg; ++k) order[o0 + size_t(cnt[key(P.segs[k])]++)] = TileSeg{int32_t(i), k};
-        for (int64_t k = 0; k < nseg;) {
-            const int W = width_class(P.segs[order[o0 + k].seg].max_width);
-            const int64_t first = int64_t(o0) + k;
-            const int L = P.segs[order[o0 + k].seg].n_layers;
-            int q = 0;
-            while (q < 32 && k < nseg && width_class(P.segs[order[o0 + k].seg].max_width) == W) ++q, ++k;
-            tiles.push_back(TileInfo{0, 0, L, W});
-            tile_first.push_back(first);
-            tile_count.push_back(q);
-            tile_inst.push_back(int32_t(i));
+        if (locality) {
+            int64_t gcnt[5] = {0, 0, 0, 0, 0};
+            for (const Segment& sg : P.segs) ++gcnt[launch_group(width_class(sg.max_width)) + 1];
+            for (int g = 0; g < 4; ++g) gcnt[g + 1] += gcnt[g];
+            const int64_t gstart[5] = {gcnt[0], gcnt[1], gcnt[2], gcnt[3], gcnt[4]};
+            for (int64_t k = 0; k < nseg; ++k) R.seg[size_t(gcnt[launch_group(width_class(P.segs[k].max_width))]++)] = k;
+            std::vector<uint64_t> key;
+            for (int g = 0; g < 4; ++g)
+                for (int64_t b0 = gstart[g]; b0 < gstart[g + 1]; b0 += kLocalityBlock) {
+                    const int64_t b1 = std::min(gstart[g + 1], b0 + kLocalityBlock);
+                    // (class, length descending, position): unique keys, so the order is fixed
+                    key.resize(size_t(b1 - b0));
+                    for (int64_t k = b0; k < b1; ++k) {
+                        const Segment& sg = P.segs[R.seg[k]];
+                        key[size_t(k - b0)] = uint64_t(width_class(sg.max_width)) << 48 |
+                                              uint64_t(maxL - sg.n_layers) << 24 | uint64_t(k - b0);
+                    }
+                    std::sort(key.begin(), key.end());
+                    std::vector<int64_t> tmp(R.seg.begin() + b0, R.seg.begin() + b1);
+                    for (int64_t k = b0; k < b1; ++k) R.seg[k] = tmp[size_t(key[size_t(k - b0)] & 0xFFFFFFu)];
+                    cut_tiles(b0, b1);  // tiles never straddle a block
+                }
+        } else {
+            std::vector<int64_t> cnt(size_t(kMaxWidth + 1) * (maxL + 1) + 1, 0);
+            auto key = [&](const Segment& sg) {  // class ascending, length descending
+                return size_t(class_index(width_class(sg.max_width))) * (maxL + 1) + size_t(maxL - sg.n_layers);
+            };
+            for (const Segment& sg : P.segs) ++cnt[key(sg) + 1];
+            for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
+            for (int64_t k = 0; k < nseg; ++k) R.seg[size_t(cnt[key(P.segs[k])]++)] = k;
+            cut_tiles(0, nseg);
         }
+    });
+    {
+        std::vector<int64_t> soff(size_t(ni) + 1, 0), toff(size_t(ni) + 1, 0);
+        for (int64_t i = 0; i < ni; ++i) {
+            soff[size_t(i) + 1] = soff[size_t(i)] + int64_t(per[size_t(i)].seg.size());
+            toff[size_t(i) + 1] = toff[size_t(i)] + int64_t(per[size_t(i)].tiles.size());
+        }
+        order.resize(size_t(soff[size_t(ni)]));
+        tiles.resize(size_t(toff[size_t(ni)]));
+        tile_first.resize(tiles.size());
+        tile_count.resize(tiles.size());
+        tile_inst.resize(tiles.size());
+        parallel_tasks(ni, nth, [&](int64_t i) {
+            InstTiles& R = per[size_t(i)];
+            const int64_t so = soff[size_t(i)], to = toff[size_t(i)];
+            for (size_t k = 0; k < R.seg.size(); ++k) order[size_t(so) + k] = TileSeg{int32_t(i), R.seg[k]};
+            for (size_t t = 0; t < R.tiles.size(); ++t) {
+                tiles[size_t(to) + t] = R.tiles[t];
+                tile_first[size_t(to) + t] = so + R.first[t];
+                tile_count[size_t(to) + t] = R.count[t];
+                tile_inst[size_t(to) + t] = int32_t(i);
+            }
+            InstTiles().seg.swap(R.seg);
+        });
     }
     // classes up to kFusedMaxW share one launch, longest tiles first; wider ones launch on their own
     {
         // inside a launch group, pair by pair: the warps running at any moment then touch the
         // averaging tables of one or two pairs (L2-resident) instead of all of them; a pair's
         // tiles keep their order, longest first
-        auto group_index = [](int W) { return W <= kFusedMaxW ? 0 : W <= 8 ? 1 : W <= 16 ? 2 : 3; };
-        std::vector<int64_t> cnt(size_t(4) * size_t(ni) * (maxL + 1) + 1, 0);
+        // (in locality order the blocks keep their order: the key has no length part)
+        const size_t nlen = locality ? 1 : size_t(maxL + 1);
+        std::vector<int64_t> cnt(size_t(4) * size_t(ni) * nlen + 1, 0);
         std::vector<size_t> perm(tiles.size());
         auto key = [&](size_t t) {
-            return (size_t(group_index(tiles[t].W)) * size_t(ni) + size_t(tile_inst[t])) * (maxL + 1) +
-                   size_t(maxL - tiles[t].L);
+            return (size_t(launch_group(tiles[t].W)) * size_t(ni) + size_t(tile_inst[t])) * nlen +
+                   (locality ? 0 : size_t(maxL - tiles[t].L));
         };
         for (size_t t = 0; t < tiles.size(); ++t) ++cnt[key(t) + 1];
         for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
@@ -370,43 +445,26 @@ int upload(disco_handle* h) {
     const int64_t nslots = h->nslots();
     tr.mark("tile order");
 
-    pod_vector<uint32_t> hvar(slot_base), hdesc(slot_base);
-    pod_vector<float> hlam(slot_base), hlam_lo(slot_base);
-    pod_vector<int64_t> canon(nslots);
+    // one record per segment in tile order (canonical first slot, layers, tile slot, first
+    // variable of its instance); the kernel k_layout scatters the canonical slot arrays
+    const int64_t nseg_all = int64_t(order.size());
+    pod_vector<int64_t> seg_canon(static_cast<size_t>(nseg_all)), seg_pos(static_cast<size_t>(nseg_all));
+    pod_vector<int32_t> seg_len(static_cast<size_t>(nseg_all));
+    pod_vector<uint32_t> seg_vb(static_cast<size_t>(nseg_all));
     parallel_chunks(int64_t(tiles.size()), nth, [&](int, int64_t t0, int64_t t1) {
-        for (int64_t t = t0; t < t1; ++t) {
-            const int64_t b0 = tiles[t].slot_base, b1 = b0 + int64_t(tiles[t].L) * 32;
-            std::fill(hvar.begin() + b0, hvar.begin() + b1, kNoVar);
-            std::fill(hdesc.begin() + b0, hdesc.begin() + b1, 0u);
-            std::fill(hlam.begin() + b0, hlam.begin() + b1, 0.0f);
-            std::fill(hlam_lo.begin() + b0, hlam_lo.begin() + b1, 0.0f);
+        for (int64_t t = t0; t < t1; ++t)
             for (int lane = 0; lane < tile_count[t]; ++lane) {
-                const TileSeg& ts = order[size_t(tile_first[t] + lane)];
-                const int32_t i = ts.inst;
-                const Plan& P = h->plans[i];
-                const Segment& sg = P.segs[ts.seg];
-                const uint32_t vb = uint32_t(h->var_base[i]);
-                const int64_t cb = h->slot_base[i];
-                for (int l = 0; l < sg.n_layers; ++l) {
-                    const int64_t pos = b0 + int64_t(l) * 32 + int64_t(lane);
-                    const int64_t c = sg.first_slot + l;
-                    hvar[pos] = vb + uint32_t(P.slot_var[c]);
-                    hdesc[pos] = P.slot_desc[c];
-                    hlam[pos] = P.slot_lam0[c];
-                    hlam_lo[pos] = P.slot_lam0_lo[c];
-                    canon[cb + c] = pos;
-                }
+                const int64_t k = tile_first[t] + lane;
+                const TileSeg& ts = order[size_t(k)];
+                const Segment& sg = h->plans[ts.inst].segs[ts.seg];
+                seg_canon[k] = h->slot_base[ts.inst] + sg.first_slot;
+                seg_len[k] = sg.n_layers;
+                seg_pos[k] = tiles[t].slot_base + lane;
+                seg_vb[k] = uint32_t(h->var_base[ts.inst]);
             }
-        }
     });
-    std::vector<uint8_t> deg(static_cast<size_t>(h->nint));
-    std::vector<int32_t> var_inst(static_cast<size_t>(h->nint));
     std::vector<double> consts(static_cast<size_t>(ni));
-    for (int64_t i = 0; i < ni; ++i) {
-        std::copy(h->plans[i].deg.begin(), h->plans[i].deg.end(), deg.begin() + h->var_base[i]);
-        std::fill(var_inst.begin() + h->var_base[i], var_inst.begin() + h->var_base[i + 1], int32_t(i));
-        consts[i] = h->plans[i].constant;
-    }
+    for (int64_t i = 0; i < ni; ++i) consts[i] = h->plans[i].constant;
     tr.mark("tile layout");
     int rc;
     if ((rc = h->alloc(&h->tiles, h->ntiles))) return rc;
@@ -440,16 +498,59 @@ int upload(disco_handle* h) {
     CK(cudaMallocHost(&h->h_scalar, size_t(std::max<int64_t>(ni, 1)) * sizeof(double)));
     tr.mark("allocations");
     cudaStream_t s = h->stream;
-    if ((rc = copy_in(h->tiles, tiles.data(), tiles.size() * sizeof(TileInfo), s))) return rc;
-    if ((rc = copy_in(h->var, hvar.data(), hvar.size() * 4, s))) return rc;
-    if ((rc = copy_in(h->desc, hdesc.data(), hdesc.size() * 4, s))) return rc;
-    if ((rc = copy_in(h->lam, hlam.data(), hlam.size() * 4, s))) return rc;
-    if ((rc = copy_in(h->lam_lo, hlam_lo.data(), hlam_lo.size() * 4, s))) return rc;
+    // temporaries: canonical slot arrays, segment records, instance variable bases
+    const size_t b_slots = size_t(nslots) * 4, b_segs = size_t(nseg_all) * 8, b_segs4 = size_t(nseg_all) * 4;
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t b_tmp = 4 * up(b_slots) + 2 * up(b_segs) + 2 * up(b_segs4) + up(size_t(ni + 1) * 8);
+    char* tmp = nullptr;
+    {
+        cudaMemPool_t pool;
+        cudaError_t e = pool_for(h->device, &pool);
+        if (e == cudaSuccess) e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&tmp), std::max<size_t>(b_tmp, 256), pool, s);
+        if (e != cudaSuccess) return fail(DISCO_ERR_OOM, std::string("device allocation: ") + cudaGetErrorString(e));
+    }
+    char* q = tmp;
+    auto carve = [&](size_t b) { char* r = q; q += up(b); return r; };
+    int32_t* cvar = reinterpret_cast<int32_t*>(carve(b_slots));
+    uint32_t* cdesc = reinterpret_cast<uint32_t*>(carve(b_slots));
+    float* clam = reinterpret_cast<float*>(carve(b_slots));
+    float* clam_lo = reinterpret_cast<float*>(carve(b_slots));
+    int64_t* d_seg_canon = reinterpret_cast<int64_t*>(carve(b_segs));
+    int64_t* d_seg_pos = reinterpret_cast<int64_t*>(carve(b_segs));
+    int32_t* d_seg_len = reinterpret_cast<int32_t*>(carve(b_segs4));
+    uint32_t* d_seg_vb = reinterpret_cast<uint32_t*>(carve(b_segs4));
+    int64_t* d_var_base = reinterpret_cast<int64_t*>(carve(size_t(ni + 1) * 8));
+    auto release = [&] { cudaFreeAsync(tmp, s); };
+    rc = DISCO_OK;
+    for (int64_t i = 0; i < ni && !rc; ++i) {
+        const Plan& P = h->plans[i];
+        const int64_t o = h->slot_base[i], n = int64_t(P.slot_var.size());
+        (rc = copy_in(cvar + o, P.slot_var.data(), size_t(n) * 4, s)) || (rc = copy_in(cdesc + o, P.slot_desc.data(), size_t(n) * 4, s)) ||
+            (rc = copy_in(clam + o, P.slot_lam0.data(), size_t(n) * 4, s)) ||
+            (rc = copy_in(clam_lo + o, P.slot_lam0_lo.data(), size_t(n) * 4, s)) ||
+            (rc = copy_in(h->deg + h->var_base[i], P.deg.data(), P.deg.size(), s));
+    }
+    if (!rc) {
+        (rc = copy_in(d_seg_canon, seg_canon.data(), b_segs, s)) || (rc = copy_in(d_seg_pos, seg_pos.data(), b_segs, s)) ||
+            (rc = copy_in(d_seg_len, seg_len.data(), b_segs4, s)) || (rc = copy_in(d_seg_vb, seg_vb.data(), b_segs4, s)) ||
+            (rc = copy_in(d_var_base, h->var_base.data(), size_t(ni + 1) * 8, s)) ||
+            (rc = copy_in(h->tiles, tiles.data(), tiles.size() * sizeof(TileInfo), s));
+    }
+    if (rc) {
+        release();
+        return rc;
+    }
+    // padding lanes and layers: no variable, zero descriptor and lambda
+    CK(cudaMemsetAsync(h->var, 0xFF, size_t(slot_base) * 4, s));
+    CK(cudaMemsetAsync(h->desc, 0, size_t(slot_base) * 4, s));
+    CK(cudaMemsetAsync(h->lam, 0, size_t(slot_base) * 4, s));
+    CK(cudaMemsetAsync(h->lam_lo, 0, size_t(slot_base) * 4, s));
+    CK(launch_layout(d_seg_canon, d_seg_len, d_seg_pos, d_seg_vb, nseg_all, cvar, cdesc, clam, clam_lo, h->var, h->desc,
+                     h->lam, h->lam_lo, h->canon_pos, s));
+    CK(launch_instance_of(d_var_base, int32_t(ni), h->nint, h->var_inst, s));
+    release();
     CK(cudaMemcpyAsync(h->lam0, h->lam, size_t(slot_base) * 4, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(h->lam0_lo, h->lam_lo, size_t(slot_base) * 4, cudaMemcpyDeviceToDevice, s));
-    if ((rc = copy_in(h->canon_pos, canon.data(), canon.size() * 8, s))) return rc;
-    if ((rc = copy_in(h->deg, deg.data(), deg.size(), s))) return rc;
-    if ((rc = copy_in(h->var_inst, var_inst.data(), var_inst.size() * 4, s))) return rc;
     if ((rc = copy_in(h->consts, consts.data(), consts.size() * 8, s))) return rc;
     if ((rc = copy_in(h->d_inst_tile_ptr, h->inst_tile_ptr.data(), h->inst_tile_ptr.size() * 4, s))) return rc;
     if ((rc = copy_in(h->d_inst_tiles, inst_tiles.data(), inst_tiles.size() * 4, s))) return rc;
@@ -750,7 +851,7 @@ int build_handle(int32_t n, const disco_mesh* X, const disco_mesh* Y, const floa
     disco_opts o;
     if (opts) o = *opts; else disco_default_opts(&o);
     if (!(o.omega > 0.0f && o.omega <= 1.0f) || o.split_chunk < 0 || o.split_max_segments < 0 || o.lb_every < 1 ||
-        o.graph_iters < 0 || o.cost_model < 0 || o.cost_model > 1 || o.qn_memory < 0)
+        o.graph_iters < 0 || o.cost_model < 0 || o.cost_model > 1 || o.qn_memory < 0 || o.tile_order < 0 || o.tile_order > 2)
         return fail(DISCO_ERR_INVALID_ARG, "build: bad options");
     std::unique_ptr<disco_handle> h(new disco_handle());
     h->device = o.device;
@@ -1236,20 +1337,29 @@ bool assemble_instance(const Plan& P, const uint8_t* st, int nth, uint8_t* x, do
         }
     });
     const bool all = std::find(undecided.begin(), undecided.end(), uint8_t(1)) == undecided.end();
+    // every row's residual, over row ranges of about equal entry counts (projection rows are
+    // long), taken dynamically; the cost in fixed element blocks (a thread-count-independent sum)
     const int nck = 64;
+    std::vector<int64_t> cut(size_t(nck) + 1, P.nrows);
+    cut[0] = 0;
+    const int64_t ntot = P.row_ptr[size_t(P.nrows)];
+    for (int c = 1; c < nck; ++c)
+        cut[size_t(c)] = std::max<int64_t>(
+            cut[size_t(c) - 1],
+            int64_t(std::lower_bound(P.row_ptr.begin(), P.row_ptr.begin() + P.nrows, ntot * c / nck) - P.row_ptr.begin()));
     std::vector<uint8_t> violated(nck, 0);
     std::vector<double> part(nck, 0.0);
-    parallel_chunks(nck, nth, [&](int, int64_t c0, int64_t c1) {
-        for (int64_t c = c0; c < c1; ++c) {
-            for (int64_t r = P.nrows * c / nck; r < P.nrows * (c + 1) / nck; ++r) {
-                int64_t sum = 0;
-                for (int64_t e = P.row_ptr[r]; e < P.row_ptr[r + 1]; ++e) sum += int64_t(P.row_coef[e]) * x[P.row_var[e]];
-                if (sum != P.rhs[r]) violated[c] = 1;
-            }
-            double s = 0.0;
-            for (int64_t i = P.nvars * c / nck; i < P.nvars * (c + 1) / nck; ++i) s += x[i] ? P.cost[i] : 0.0;
-            part[c] = s;
+    parallel_tasks(nck, nth, [&](int64_t c) {
+        uint8_t bad = 0;
+        for (int64_t r = cut[size_t(c)]; r < cut[size_t(c) + 1]; ++r) {
+            int64_t sum = 0;
+            for (int64_t e = P.row_ptr[r]; e < P.row_ptr[r + 1]; ++e) sum += int64_t(P.row_coef[e]) * x[P.row_var[e]];
+            bad |= uint8_t(sum != P.rhs[r]);
         }
+        violated[size_t(c)] = bad;
+        double s = 0.0;
+        for (int64_t i = P.nvars * c / nck; i < P.nvars * (c + 1) / nck; ++i) s += x[i] ? P.cost[i] : 0.0;
+        part[size_t(c)] = s;
     });
     double c = 0.0;
     for (double q : part) c += q;
@@ -1344,7 +1454,7 @@ int primal_all(disco_handle* h, uint8_t* x_out, double* costs, int32_t* status) 
     const int hw = host_threads(o);
     const int outer = std::max(1, std::min<int>(int(ni), hw));
     mark("read back");
-    std::vector<uint8_t> x(static_cast<size_t>(h->nelems()), uint8_t(0));
+    pod_vector<uint8_t> x(static_cast<size_t>(h->nelems()));  // every element is written by its instance
     std::vector<uint8_t> ok(static_cast<size_t>(ni), 0);
     std::vector<double> cs(static_cast<size_t>(ni), 0.0);
     parallel_chunks(ni, outer, [&](int, int64_t i0, int64_t i1) {

@@ -90,6 +90,16 @@ cudaError_t launch_adjoint(Adj kind, int group, const AdjArgs& a, cudaStream_t s
 cudaError_t launch_adj_cost(const uint32_t* var, const uint32_t* desc, int64_t nslots, const float* lbar,
                             const uint8_t* deg, int64_t nint, float* tab, float* cbar, cudaStream_t s);
 
+// Store construction (store.cu). launch_layout: segment k (in tile order) has seg_len[k]
+// layers at canonical slots seg_canon[k] + l, placed at tile slot seg_pos[k] + 32 l; its
+// variable ids are offset by seg_vb[k] (the instance's first variable). canon_pos[c] = the
+// tile slot of canonical slot c. launch_instance_of: out[v] = i with base[i] <= v < base[i + 1].
+cudaError_t launch_layout(const int64_t* seg_canon, const int32_t* seg_len, const int64_t* seg_pos,
+                          const uint32_t* seg_vb, int64_t nseg, const int32_t* cvar, const uint32_t* cdesc,
+                          const float* clam, const float* clam_lo, uint32_t* var, uint32_t* desc, float* lam,
+                          float* lam_lo, int64_t* canon_pos, cudaStream_t s);
+cudaError_t launch_instance_of(const int64_t* base, int32_t ni, int64_t n, int32_t* out, cudaStream_t s);
+
 // Quasi-Newton vector kernels (qn.cu); n = slots in tile layout.
 cudaError_t launch_qn_sign(const float* mm, const uint32_t* var, int64_t n, float* g, cudaStream_t s);
 int qn_dot_blocks();

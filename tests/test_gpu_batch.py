@@ -84,3 +84,43 @@ def test_batch_bounds_match_oracle(lib):
         ref = o.lower_bound()
         assert abs(lb - ref) <= 1e-5 * max(abs(ref), 1e-3)
     batch.close()
+
+
+def test_tile_orders_give_the_same_results(lib):
+    """Tile order only places lanes: the locality order (blocks of 4096 segments in row order)
+    and the width-and-length order give the same min-marginals and matchings, and bounds that
+    differ only by the order of their FP64 tile sums."""
+    import torch
+
+    from paper_2310_08230_gb300.api import candidates, pair_costs
+
+    Solver = lib
+    pairs = [(i.X.T, i.Y.T, d.astype(np.float32), a) for i, d, a in _pairs()]
+    big = I.config5(1)[0]  # 1280 triangles, top-16: about 20 blocks of segments
+    d = pair_costs(torch.from_numpy(big.FX).cuda(), torch.from_numpy(big.FY).cuda())
+    a = candidates(d, 16, big.X.T, big.Y.T)
+    pairs.append((big.X.T, big.Y.T, d.cpu().numpy(), a.cpu().numpy()))
+    out = []
+    for order in (1, 2):
+        s = Solver.batch(pairs, split_chunk=32, tile_order=order)
+        s.dual(30)
+        xs, costs, ok = s.primal_batch()
+        out.append((s.lower_bounds(), s.min_marginals(), xs, costs, ok, s.info()["ntiles"]))
+        s.close()
+    (lb1, mm1, x1, c1, ok1, nt1), (lb2, mm2, x2, c2, ok2, nt2) = out
+    np.testing.assert_allclose(lb2, lb1, rtol=1e-12, atol=0)
+    np.testing.assert_array_equal(mm2, mm1)
+    assert ok1.all() and ok2.all()
+    for u, v in zip(x1, x2):
+        np.testing.assert_array_equal(u, v)
+    np.testing.assert_allclose(c2, c1, rtol=1e-12)
+    assert nt2 >= nt1  # blocks may leave partial tiles
+
+
+def test_tile_order_is_checked(lib):
+    from paper_2310_08230_gb300 import _lib as L
+
+    Solver = lib
+    inst, d, a = _pairs()[0]
+    with pytest.raises(L.DiscoError):
+        Solver(inst.X.T, inst.Y.T, d.astype(np.float32), a, tile_order=3)

@@ -48,7 +48,7 @@ def test_default_options(L):
     assert L.lib().disco_default_opts(ctypes.byref(o)) == 0
     assert o.omega == 0.5 and o.lb_every == 20 and o.split_max_segments == 8
     assert o.graph_iters == 10 and o.autotune == 1 and o.normalize_costs == 1 and o.qn_memory == 0
-    assert o.cost_model == 0 and list(o.reserved) == [0]
+    assert o.cost_model == 0 and o.tile_order == 0
 
 
 def _compile(L, inst, allowed, d, chunk, maxseg=8):
