@@ -170,17 +170,7 @@ template <class Gen>
 void run_jobs(const std::vector<Job>& jobs, int threads, Elems* out, Gen gen) {
     const int nj = int(jobs.size());
     std::vector<Elems> parts(nj);
-    std::atomic<int> next{0};
-    auto run = [&](auto&& job) {
-        next = 0;
-        std::vector<std::thread> pool;
-        auto worker = [&] {
-            for (int c; (c = next.fetch_add(1)) < nj;) job(c);
-        };
-        for (int t = 1; t < std::min(threads, nj); ++t) pool.emplace_back(worker);
-        worker();
-        for (auto& th : pool) th.join();
-    };
+    auto run = [&](auto&& job) { parallel_tasks(nj, threads, [&](int64_t c) { job(int(c)); }); };
     run([&](int c) { gen(jobs[c], &parts[c]); });
     std::vector<size_t> off(nj + 1, out->size());
     for (int c = 0; c < nj; ++c) off[c + 1] = off[c] + parts[c].size();
@@ -393,10 +383,13 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     if (threads <= 0) threads = std::max(1u, std::thread::hardware_concurrency());
     MeshTopo X, Y;
     int chiX = 0, chiY = 0;
-    int rc = topo(Xin, &X, &chiX, err);
-    if (rc) { *err = "mesh X: " + *err; return rc; }
-    rc = topo(Yin, &Y, &chiY, err);
-    if (rc) { *err = "mesh Y: " + *err; return rc; }
+    std::string errXY[2];
+    int rcXY[2] = {DISCO_OK, DISCO_OK};
+    parallel_tasks(2, threads, [&](int64_t k) {
+        rcXY[k] = k == 0 ? topo(Xin, &X, &chiX, &errXY[0]) : topo(Yin, &Y, &chiY, &errXY[1]);
+    });
+    if (rcXY[0]) { *err = "mesh X: " + errXY[0]; return rcXY[0]; }
+    if (rcXY[1]) { *err = "mesh Y: " + errXY[1]; return rcXY[1]; }
     if (chiX != chiY) { *err = "Euler characteristics differ"; return DISCO_ERR_GENUS_MISMATCH; }
     const int nvx = X.nv, nvy = Y.nv;
     P->nvx = nvx;
