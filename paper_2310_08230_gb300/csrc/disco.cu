@@ -233,8 +233,8 @@ int copy_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
 
 // Reads n elements of a host-or-device array into a host vector.
 template <class T>
-int to_host(const T* src, size_t n, std::vector<T>* out) {
-    out->resize(n);
+int to_host(const T* src, size_t n, pod_vector<T>* out) {
+    out->resize(n);  // no zero fill: the copy writes every element
     if (is_device_ptr(src)) {
         CK(cudaMemcpy(out->data(), src, n * sizeof(T), cudaMemcpyDeviceToHost));
     } else {
@@ -864,14 +864,16 @@ int build_handle(int32_t n, const disco_mesh* X, const disco_mesh* Y, const floa
         h->own_stream = true;
     }
     // costs and masks on the host (they may be device arrays)
-    std::vector<std::vector<float>> hd(n);
-    std::vector<std::vector<uint8_t>> ha(n);
+    Trace tr;
+    std::vector<pod_vector<float>> hd(n);
+    std::vector<pod_vector<uint8_t>> ha(n);
     int rc;
     for (int32_t i = 0; i < n; ++i) {
         const size_t npair = size_t(X[i].nv) * size_t(Y[i].nv);
         if ((rc = to_host(d[i], npair, &hd[i]))) return rc;
         if (allowed && allowed[i] && (rc = to_host(allowed[i], npair, &ha[i]))) return rc;
     }
+    tr.mark("inputs to host");
     // one instance uses every host thread; several instances are compiled side by side
     const int hw = host_threads(o);
     const int outer = std::max(1, std::min<int>(n, hw));
@@ -881,12 +883,12 @@ int build_handle(int32_t n, const disco_mesh* X, const disco_mesh* Y, const floa
     std::vector<std::string> errs(n);
     // one task per instance, largest first (by candidate pairs), taken dynamically by the
     // host threads, so that uneven pairs balance
-    std::vector<int64_t> est(static_cast<size_t>(n));
-    for (int32_t i = 0; i < n; ++i) {
-        const int64_t pairs = int64_t(X[i].nv) * Y[i].nv;
-        est[i] = (allowed && allowed[i]) ? std::count_if(ha[i].begin(), ha[i].end(), [](uint8_t a) { return a != 0; })
-                                         : pairs;
-    }
+    std::vector<int64_t> est(static_cast<size_t>(n), 1);
+    if (n > 1)
+        parallel_tasks(n, hw, [&](int64_t i) {
+            const int64_t pairs = int64_t(X[i].nv) * Y[i].nv;
+            est[i] = (allowed && allowed[i]) ? pairs - int64_t(std::count(ha[i].begin(), ha[i].end(), uint8_t(0))) : pairs;
+        });
     std::vector<int32_t> order(static_cast<size_t>(n));
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return est[a] > est[b]; });
