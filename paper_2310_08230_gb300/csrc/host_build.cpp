@@ -47,6 +47,25 @@ namespace {
 // vertex sequence of a degenerate triangle over an edge (a < b): 0 -> a, 1 -> b
 const int kEdgePattern[6][3] = {{0, 0, 1}, {0, 1, 0}, {1, 0, 0}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
 
+// The patterns p whose first symbol is `first` and whose second and third symbols are
+// allowed: bit p of kPatternMask[first][b1][b2], where bit s of b1 (b2) says that symbol s
+// may sit at the second (third) corner.
+struct PatternMasks {
+    uint8_t m[2][4][4];
+    constexpr PatternMasks() : m{} {
+        for (int f = 0; f < 2; ++f)
+            for (int b1 = 0; b1 < 4; ++b1)
+                for (int b2 = 0; b2 < 4; ++b2) {
+                    uint8_t x = 0;
+                    for (int p = 0; p < 6; ++p)
+                        if (kEdgePattern[p][0] == f && ((b1 >> kEdgePattern[p][1]) & 1) && ((b2 >> kEdgePattern[p][2]) & 1))
+                            x = uint8_t(x | (1u << p));
+                    m[f][b1][b2] = x;
+                }
+    }
+};
+constexpr PatternMasks kPatternMask{};
+
 // Compressed incidence list: the items of vertex v are item[ptr[v] .. ptr[v+1]).
 template <class T>
 struct Csr {
@@ -135,15 +154,9 @@ struct Elems {  // matching elements, structure of arrays
         xe.push_back(x);
         ye.push_back(y);
     }
-    void append(const Elems& o) {
-        m.insert(m.end(), o.m.begin(), o.m.end());
-        n.insert(n.end(), o.n.begin(), o.n.end());
-        type.insert(type.end(), o.type.begin(), o.type.end());
-        xe.insert(xe.end(), o.xe.begin(), o.xe.end());
-        ye.insert(ye.end(), o.ye.begin(), o.ye.end());
-    }
     size_t size() const { return type.size(); }
 };
+
 
 // Candidate pairs: a bit row per X vertex (cache resident) and the allowed Y vertices of
 // every X vertex in ascending order.
@@ -235,11 +248,10 @@ void enumerate(const MeshTopo& X, const MeshTopo& Y, const Allowed& A, int threa
                     Y.edge_at.for_each(n0, [&](int e) {
                         const int ab[2] = {Y.edges[e].first, Y.edges[e].second};
                         const int role = ab[0] == n0 ? 0 : 1;  // patterns whose first corner is n0
-                        const bool b1[2] = {A(m[1], ab[0]), A(m[1], ab[1])};
-                        const bool b2[2] = {A(m[2], ab[0]), A(m[2], ab[1])};
-                        for (int p = 0; p < 6; ++p)
-                            if (kEdgePattern[p][0] == role && b1[kEdgePattern[p][1]] && b2[kEdgePattern[p][2]])
-                                cand.push_back(int64_t(e) * 6 + p);
+                        const int b1 = int(A(m[1], ab[0])) | int(A(m[1], ab[1])) << 1;
+                        const int b2 = int(A(m[2], ab[0])) | int(A(m[2], ab[1])) << 1;
+                        for (unsigned x = kPatternMask.m[role][b1][b2]; x; x &= x - 1)
+                            cand.push_back(int64_t(e) * 6 + __builtin_ctz(x));
                     });
                 });
                 std::sort(cand.begin(), cand.end());
@@ -263,11 +275,10 @@ void enumerate(const MeshTopo& X, const MeshTopo& Y, const Allowed& A, int threa
                     A.row.for_each(ab[first], [&](int n0) {
                         Y.tri_at0.for_each(n0, [&](int s) {
                             const int s1 = TY[3 * s + 1], s2 = TY[3 * s + 2];
-                            const bool b1[2] = {A(ab[0], s1), A(ab[1], s1)};
-                            const bool b2[2] = {A(ab[0], s2), A(ab[1], s2)};
-                            for (int p = 0; p < 6; ++p)
-                                if (kEdgePattern[p][0] == first && b1[kEdgePattern[p][1]] && b2[kEdgePattern[p][2]])
-                                    cand.push_back(int64_t(s) * 6 + p);
+                            const int b1 = int(A(ab[0], s1)) | int(A(ab[1], s1)) << 1;
+                            const int b2 = int(A(ab[0], s2)) | int(A(ab[1], s2)) << 1;
+                            for (unsigned x = kPatternMask.m[first][b1][b2]; x; x &= x - 1)
+                                cand.push_back(int64_t(s) * 6 + __builtin_ctz(x));
                         });
                     });
                 }
