@@ -840,7 +840,11 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                             --q.nn;
                             q.res += m.code & 1;
                         }
-                        if (!q.queued) {
+                        // only a saturated (or violated) row with free entries can act; a
+                        // saturated row stays saturated or turns violated under further
+                        // fixings, so testing after each update misses none. Rows left without
+                        // free entries are checked once after the fixpoint.
+                        if (!q.queued && q.np + q.nn > 0 && (q.res >= q.np || q.res <= -q.nn)) {
                             q.queued = 1;
                             frontier[t].push_back(m.row);
                         }
