@@ -355,13 +355,31 @@ int upload(disco_handle* h) {
                     cut_tiles(b0, b1);  // tiles never straddle a block
                 }
         } else {
-            std::vector<int64_t> cnt(size_t(kMaxWidth + 1) * (maxL + 1) + 1, 0);
-            auto key = [&](const Segment& sg) {  // class ascending, length descending
-                return size_t(class_index(width_class(sg.max_width))) * (maxL + 1) + size_t(maxL - sg.n_layers);
-            };
-            for (const Segment& sg : P.segs) ++cnt[key(sg) + 1];
-            for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
-            for (int64_t k = 0; k < nseg; ++k) R.seg[size_t(cnt[key(P.segs[k])]++)] = k;
+            // stable counting sort by (class ascending, length descending): per-chunk counts,
+            // offsets in (key, chunk) order, scatter; chunks in parallel for a single instance
+            // (a batch orders its instances in parallel instead)
+            const size_t nkey = size_t(kMaxWidth + 1) * (maxL + 1);
+            const int nch = ni > 1 ? 1 : std::max(1, std::min<int>(nth, int(nseg / 16384) + 1));
+            std::vector<uint32_t> key(static_cast<size_t>(nseg));
+            std::vector<std::vector<int64_t>> cnt(size_t(nch), std::vector<int64_t>(nkey, 0));
+            parallel_chunks(nseg, nch, [&](int c, int64_t k0, int64_t k1) {
+                for (int64_t k = k0; k < k1; ++k) {
+                    const Segment& sg = P.segs[k];
+                    key[size_t(k)] = uint32_t(size_t(class_index(width_class(sg.max_width))) * (maxL + 1) +
+                                              size_t(maxL - sg.n_layers));
+                    ++cnt[size_t(c)][key[size_t(k)]];
+                }
+            });
+            int64_t run = 0;
+            for (size_t b = 0; b < nkey; ++b)
+                for (int c = 0; c < nch; ++c) {
+                    const int64_t x = cnt[size_t(c)][b];
+                    cnt[size_t(c)][b] = run;
+                    run += x;
+                }
+            parallel_chunks(nseg, nch, [&](int c, int64_t k0, int64_t k1) {
+                for (int64_t k = k0; k < k1; ++k) R.seg[size_t(cnt[size_t(c)][key[size_t(k)]]++)] = k;
+            });
             cut_tiles(0, nseg);
         }
     });
