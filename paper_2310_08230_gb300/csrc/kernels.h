@@ -52,8 +52,8 @@ struct KArgs {
 };
 
 // Arguments of the adjoint kernels (adjoint.cu). A pass's inputs come from the tape (the
-// values the pass read when it ran), its own-direction node costs from a recomputation by
-// the normal kernel; adjoints: lbar per slot (in: of lambda after the pass; out: of lambda
+// values the pass read when it ran), its own-direction node costs too (as the pass stored
+// them when it was replayed); adjoints: lbar per slot (in: of lambda after the pass; out: of lambda
 // before it), mubar per variable and rank (sectors like the averaging tables; next = the
 // adjoint of the deferred means this pass produced, out = of those it read), node-array
 // adjoints own_bar (of the costs this pass stored, read) and other_bar (of the costs it read
