@@ -97,7 +97,8 @@ template <int W>
 struct LayerIn {
     uint32_t v, dsc;
     float lam, lo, lb;
-    float4 acc0, acc1, mb0, mb1;
+    float2 pend;  // the deferred mean the pass added (double-float, from the pend table)
+    float rb;     // adjoint of the mass the pass removed (from the rbar table)
     float own[W], ownb[W], oth[W];
 };
 
@@ -119,14 +120,8 @@ __device__ __forceinline__ void load_layer(const AdjArgs& a, int64_t sb, int64_t
     x.lam = __ldg(a.lam_in + si);
     x.lo = __ldg(a.lam_in_lo + si);
     x.lb = (kMMA || KIND == Adj::Reset) ? a.lbar[si] : 0.0f;
-    const float4* ap = reinterpret_cast<const float4*>(a.acc_in + size_t(v) * kAccStride);
-    x.acc0 = __ldg(ap);
-    x.acc1 = d.deg > 4 ? __ldg(ap + 1) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (kMMA) {
-        const float4* mp = reinterpret_cast<const float4*>(a.mubar_next + size_t(v) * kAccStride);
-        x.mb0 = __ldg(mp);
-        x.mb1 = d.deg > 4 ? __ldg(mp + 1) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    }
+    x.pend = __ldg(a.pend_in + v);
+    if (kMMA) x.rb = __ldg(a.rbar + v);
     const float* Lr = a.own + nb + int64_t(l) * W * 32;  // own-direction row of layer l
     const float* Nr = Lr + W * 32;                       // and of layer l + 1
 #pragma unroll
@@ -152,7 +147,7 @@ __device__ __forceinline__ void adj_forward_layer(const AdjArgs& a, const LayerI
 #pragma unroll
     for (int s = 0; s < W; ++s) fl_bar[s] = x.ownb[s];
     df Lm{x.lam, x.lo};
-    const df p = pend_from(x.acc0, x.acc1, d.deg);
+    const df p{x.pend.x, x.pend.y};
     float lm;
     int s0 = -1, s1 = -1, c0 = -1, c1 = -1;
     if (!BOUND) {
@@ -211,7 +206,7 @@ __device__ __forceinline__ void adj_forward_layer(const AdjArgs& a, const LayerI
     float mubar;
     if (!BOUND) {
         const float L = x.lb + arcs;
-        const float rbar = removed_bar(x.mb0, x.mb1, d.deg) - L;
+        const float rbar = x.rb - L;
         mubar = L + a.omega * rbar;
         const float m0bar = -a.omega * rbar, m1bar = a.omega * rbar;
         add_dyn(fl_bar, s0, m0bar);
@@ -246,7 +241,7 @@ __device__ __forceinline__ void adj_backward_layer(const AdjArgs& a, const Layer
 #pragma unroll
     for (int s = 0; s < W; ++s) bl_bar[s] = carry[s] + x.ownb[s];
     df Lm{x.lam, x.lo};
-    const df p = pend_from(x.acc0, x.acc1, d.deg);
+    const df p{x.pend.x, x.pend.y};
     float hx[W + 2];
     shift_ext(x.own, d.d0, hx);
     const bool up = d.d1 > d.d0;
@@ -303,7 +298,7 @@ __device__ __forceinline__ void adj_backward_layer(const AdjArgs& a, const Layer
     if (d.one) add_dyn(nxt, d.d1, arcs);
     if (!RESET) {
         const float L = x.lb + arcs;
-        const float rbar = removed_bar(x.mb0, x.mb1, d.deg) - L;
+        const float rbar = x.rb - L;
         const float mubar = L + a.omega * rbar;
         const float m0bar = -a.omega * rbar, m1bar = a.omega * rbar;
         add_dyn(nxt, c0, m0bar);
@@ -382,6 +377,28 @@ __global__ void __launch_bounds__(kAdjWarps * 32, WG == 0 ? 4 : (WG == 8 ? 3 : 1
     }
 }
 
+// pend[v]: the deferred mean of variable v from its averaging sector, as the half-pass
+// kernels compute it (same operations, same order).
+__global__ void k_pend_table(const float* __restrict__ acc, const uint8_t* __restrict__ deg, int64_t n,
+                             float2* __restrict__ out) {
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
+        const int dg = deg[v];
+        const float4* p = reinterpret_cast<const float4*>(acc + size_t(v) * kAccStride);
+        const df m = dg > 0 ? pend_from(p[0], dg > 4 ? p[1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f), dg) : df{0.0f, 0.0f};
+        out[v] = make_float2(m.hi, m.lo);
+    }
+}
+
+// rbar[v]: the adjoint of each removed mass of v, the sum of its sector / deg.
+__global__ void k_rbar_table(const float* __restrict__ mub, const uint8_t* __restrict__ deg, int64_t n,
+                             float* __restrict__ out) {
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
+        const int dg = deg[v];
+        const float4* p = reinterpret_cast<const float4*>(mub + size_t(v) * kAccStride);
+        out[v] = dg > 0 ? removed_bar(p[0], dg > 4 ? p[1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f), dg) : 0.0f;
+    }
+}
+
 __global__ void k_slot_table(const uint32_t* __restrict__ var, const uint32_t* __restrict__ desc, int64_t n,
                              const float* __restrict__ x, float* __restrict__ tab) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
@@ -428,6 +445,20 @@ cudaError_t launch_adjoint(Adj kind, int group, const AdjArgs& a, cudaStream_t s
         case Adj::Bound: launch_kind<Adj::Bound>(group, grid, block, a, s); break;
         case Adj::Reset: launch_kind<Adj::Reset>(group, grid, block, a, s); break;
     }
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pend_table(const float* acc, const uint8_t* deg, int64_t n, float2* out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_pend_table<<<grid_of(n, 256), 256, 0, s>>>(acc, deg, n, out);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rbar_table(const float* mub, const uint8_t* deg, int64_t n, float* out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_rbar_table<<<grid_of(n, 256), 256, 0, s>>>(mub, deg, n, out);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }

@@ -139,7 +139,8 @@ struct disco_handle {
     struct Snap {  // the dual state at an iteration boundary, or the inputs of one half-pass
         float* lam = nullptr;
         float* lam_lo = nullptr;
-        float* acc = nullptr;      // averaging sectors the next pass reads
+        float* acc = nullptr;      // checkpoint: averaging sectors the next pass reads
+        float2* pend = nullptr;    // tape: the deferred means the pass added (per variable)
         float* nodes = nullptr;    // checkpoint: node costs of the other direction; tape: the
                                    // node costs the pass stored (the next pass's input)
         int cur = 0;               // which averaging buffer they belong to
@@ -149,6 +150,8 @@ struct disco_handle {
     int32_t rec_iters = -1, rec_every = 0;
     float* lbar = nullptr;         // adjoint per slot
     float* mub[2] = {nullptr, nullptr};  // adjoint sectors of the deferred means
+    float* rbar = nullptr;         // per variable: adjoint of each removed mass (from mub)
+    float2* pend_tmp = nullptr;    // per variable: deferred means of a checkpoint or the final state
     float* Fbar = nullptr;         // adjoints of the stored node costs
     float* Bbar = nullptr;
     float* cbar = nullptr;         // adjoint per internal variable
@@ -1552,12 +1555,18 @@ namespace {
 
 using Snap = disco_handle::Snap;
 
-int alloc_snap(disco_handle* h, Snap* s) {
+// A checkpoint holds lambda, the averaging sectors and the other direction's node costs; a
+// tape entry holds lambda, the per-variable deferred means and the pass's own node costs.
+int alloc_snap(disco_handle* h, Snap* s, bool tape = false) {
     if (s->lam) return DISCO_OK;
     int rc;
     if ((rc = h->alloc(&s->lam, h->nslots_tile))) return rc;
     if ((rc = h->alloc(&s->lam_lo, h->nslots_tile))) return rc;
-    if ((rc = h->alloc(&s->acc, h->nint * kAccStride))) return rc;
+    if (tape) {
+        if ((rc = h->alloc(&s->pend, h->nint))) return rc;
+    } else if ((rc = h->alloc(&s->acc, h->nint * kAccStride))) {
+        return rc;
+    }
     if ((rc = h->alloc(&s->nodes, h->nnodes_tile))) return rc;
     return DISCO_OK;
 }
@@ -1658,12 +1667,13 @@ int disco_grad(disco_handle* h, float* dlb_dpair_costs, int64_t n) {
     const int nck = std::max(1, (T + G - 1) / G);
     if (h->tape.size() < size_t(2 * G)) h->tape.resize(size_t(2 * G));
     for (int e = 0; e < std::min(2 * G, 2 * T); ++e)
-        if ((rc = alloc_snap(h, &h->tape[e]))) return rc;
+        if ((rc = alloc_snap(h, &h->tape[e], true))) return rc;
     if ((rc = alloc_snap(h, &h->final_state))) return rc;
     if (!h->lbar) {
         if ((rc = h->alloc(&h->lbar, h->nslots_tile)) || (rc = h->alloc(&h->mub[0], h->nint * kAccStride)) ||
             (rc = h->alloc(&h->mub[1], h->nint * kAccStride)) || (rc = h->alloc(&h->Fbar, h->nnodes_tile)) ||
-            (rc = h->alloc(&h->Bbar, h->nnodes_tile)) || (rc = h->alloc(&h->cbar, h->nint)))
+            (rc = h->alloc(&h->Bbar, h->nnodes_tile)) || (rc = h->alloc(&h->cbar, h->nint)) ||
+            (rc = h->alloc(&h->rbar, h->nint)) || (rc = h->alloc(&h->pend_tmp, h->nint)))
             return rc;
     }
     cudaStream_t s = h->stream;
@@ -1681,10 +1691,11 @@ int disco_grad(disco_handle* h, float* dlb_dpair_costs, int64_t n) {
     // the bound: forward min-sum on lambda + pend (recompute its node costs, then reverse)
     if ((rc = h->pass(Pass::FwdMM))) return rc;
     {
+        CK(launch_pend_table(h->acc[h->cur], h->deg, h->nint, h->pend_tmp, s));
         AdjArgs a = adj_args(h);
         a.lam_in = h->lam;
         a.lam_in_lo = h->lam_lo;
-        a.acc_in = h->acc[h->cur];
+        a.pend_in = h->pend_tmp;
         a.own = h->F;
         a.mubar_out = h->mub[0];
         CK(launch_adjoint_all(h, Adj::Bound, a));
@@ -1694,29 +1705,43 @@ int disco_grad(disco_handle* h, float* dlb_dpair_costs, int64_t n) {
     for (int k = nck - 1; k >= 0; --k) {
         if ((rc = load_snap(h, h->checkpoints[k], h->B))) return rc;
         const int nit = std::min(G, T - k * G);
-        // replay: each half-pass's inputs (lambda, the sectors it reads) and the node costs it
-        // stores go to the tape; the node costs it reads are the previous pass's (or the
-        // checkpoint's) stored ones
-        for (int t = 0; t < nit; ++t)
-            for (int dir = 0; dir < 2; ++dir) {
+        // replay: each half-pass's inputs (lambda, and the deferred means it adds as a
+        // per-variable table) go to the tape, and the pass stores its node costs straight into
+        // the tape (the node arrays are pointed there); the node costs it reads are the
+        // previous pass's (or the checkpoint's) stored ones
+        float* const F0 = h->F;
+        float* const B0 = h->B;
+        const size_t ns = size_t(h->nslots_tile) * 4;
+        for (int t = 0; t < nit && !rc; ++t)
+            for (int dir = 0; dir < 2 && !rc; ++dir) {
                 Snap& tp = h->tape[2 * t + dir];
-                if ((rc = save_snap(h, &tp, nullptr))) return rc;
-                if ((rc = h->pass(dir == 0 ? Pass::FwdMMA : Pass::BwdMMA))) return rc;
-                if ((rc = d2d(tp.nodes, dir == 0 ? h->F : h->B, size_t(h->nnodes_tile) * 4, s))) return rc;
+                if ((rc = d2d(tp.lam, h->lam, ns, s)) || (rc = d2d(tp.lam_lo, h->lam_lo, ns, s))) break;
+                const cudaError_t e = launch_pend_table(h->acc[h->cur], h->deg, h->nint, tp.pend, s);
+                if (e != cudaSuccess) {
+                    rc = fail(DISCO_ERR_CUDA, cudaGetErrorString(e));
+                    break;
+                }
+                tp.cur = h->cur;
+                (dir == 0 ? h->F : h->B) = tp.nodes;
+                rc = h->pass(dir == 0 ? Pass::FwdMMA : Pass::BwdMMA);
             }
+        h->F = F0;
+        h->B = B0;
+        if (rc) return rc;
         mark("block replay");
         for (int e = 2 * nit - 1; e >= 0; --e) {
             const Snap& tp = h->tape[e];
             const bool fwd = (e % 2) == 0;
+            CK(launch_rbar_table(h->mub[nx], h->deg, h->nint, h->rbar, s));
             AdjArgs a = adj_args(h);
             a.lam_in = tp.lam;
             a.lam_in_lo = tp.lam_lo;
-            a.acc_in = tp.acc;
+            a.pend_in = tp.pend;
             a.other = e == 0 ? h->checkpoints[k].nodes : h->tape[e - 1].nodes;
             a.own = tp.nodes;
             a.own_bar = fwd ? h->Fbar : h->Bbar;
             a.other_bar = fwd ? h->Bbar : h->Fbar;
-            a.mubar_next = h->mub[nx];
+            a.rbar = h->rbar;
             a.mubar_out = h->mub[nx ^ 1];
             CK(launch_adjoint_all(h, fwd ? Adj::Fwd : Adj::Bwd, a));
             nx ^= 1;
@@ -1728,10 +1753,11 @@ int disco_grad(disco_handle* h, float* dlb_dpair_costs, int64_t n) {
         const Snap& c0 = h->checkpoints[0];
         if ((rc = load_snap(h, c0, h->B))) return rc;
         if ((rc = h->pass(Pass::BwdReset))) return rc;
+        CK(launch_pend_table(c0.acc, h->deg, h->nint, h->pend_tmp, s));
         AdjArgs a = adj_args(h);
         a.lam_in = c0.lam;
         a.lam_in_lo = c0.lam_lo;
-        a.acc_in = c0.acc;
+        a.pend_in = h->pend_tmp;
         a.own = h->B;
         a.own_bar = h->Bbar;
         CK(launch_adjoint_all(h, Adj::Reset, a));

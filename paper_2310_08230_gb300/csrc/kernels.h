@@ -52,12 +52,13 @@ struct KArgs {
 };
 
 // Arguments of the adjoint kernels (adjoint.cu). A pass's inputs come from the tape (the
-// values the pass read when it ran), its own-direction node costs too (as the pass stored
-// them when it was replayed); adjoints: lbar per slot (in: of lambda after the pass; out: of lambda
-// before it), mubar per variable and rank (sectors like the averaging tables; next = the
-// adjoint of the deferred means this pass produced, out = of those it read), node-array
-// adjoints own_bar (of the costs this pass stored, read) and other_bar (of the costs it read
-// from the previous pass, written).
+// values the pass read when it ran, its deferred means as a per-variable table), its
+// own-direction node costs too (as the pass stored them when it was replayed). Adjoints:
+// lbar per slot (in: of lambda after the pass; out: of lambda before it); rbar per variable
+// (the adjoint of each mass the pass removed, from the following pass's sectors); mubar_out
+// per variable and rank (sectors like the averaging tables: of the deferred means the pass
+// read); node-array adjoints own_bar (of the costs this pass stored, read) and other_bar (of
+// the costs it read from the previous pass, written).
 struct AdjArgs {
     const TileInfo* tiles;
     int32_t tile0, tile_end;  // the launch's tiles (one width group)
@@ -65,13 +66,13 @@ struct AdjArgs {
     const uint32_t* desc;
     const float* lam_in;
     const float* lam_in_lo;
-    const float* acc_in;
+    const float2* pend_in;  // per variable: the deferred mean the pass added (launch_pend_table)
     const float* other;     // node costs the pass read (B forward, F backward)
-    const float* own;       // node costs the pass stored (recomputed)
+    const float* own;       // node costs the pass stored (recorded)
     const float* own_bar;   // adjoint of `own` (from the following pass); may be null = 0
     float* other_bar;       // adjoint of `other` (for the preceding pass)
     float* lbar;
-    const float* mubar_next;
+    const float* rbar;      // per variable: adjoint of each mass the pass removed (launch_rbar_table)
     float* mubar_out;
     float omega;
 };
@@ -87,6 +88,10 @@ enum class Adj {
 // only tiles of that group).
 cudaError_t launch_adjoint(Adj kind, int group, const AdjArgs& a, cudaStream_t s);
 // cbar[v] = (sum over v's slots of lbar) / deg[v], via a rank-sector table (tab).
+// pend[v] = the deferred mean of v's averaging sector (double-float, as the half-passes add it);
+// rbar[v] = (sum of v's adjoint sector) / deg[v].
+cudaError_t launch_pend_table(const float* acc, const uint8_t* deg, int64_t n, float2* out, cudaStream_t s);
+cudaError_t launch_rbar_table(const float* mub, const uint8_t* deg, int64_t n, float* out, cudaStream_t s);
 cudaError_t launch_adj_cost(const uint32_t* var, const uint32_t* desc, int64_t nslots, const float* lbar,
                             const uint8_t* deg, int64_t nint, float* tab, float* cbar, cudaStream_t s);
 
