@@ -308,13 +308,15 @@ int disco_record(disco_handle *h, int32_t iters, int32_t checkpoint_every);
 
 /* d(bound after the recorded iterations) / d(pair costs), by reverse mode through the
  * recorded iterations: every block of checkpoint_every iterations is replayed from its
- * checkpoint recording each half-pass's inputs (2 * checkpoint_every copies of the state),
- * then each half-pass is recomputed and reversed by an adjoint kernel. Out: for every
+ * checkpoint recording each half-pass's inputs and stored node costs (2 * checkpoint_every
+ * copies of the state), then each half-pass is reversed by an adjoint kernel. Out: for every
  * instance nvx * nvy floats (row-major, the layout of disco_build's pair costs),
- * concatenated over a batch; host or device pointer, n >= that count. The bound includes
- * the presolve constant (gradient 1 for elements fixed to 1) and, with normalize_costs,
- * the dependence on the largest element cost. The candidate mask and presolve are held
- * fixed. The handle's state is left at the recorded final state. Synchronises.
+ * concatenated over a batch; host or device pointer, n >= that count. The chain rule follows
+ * the handle's cost model (the mean of the three pair costs, or Eq. 2's area-weighted sum).
+ * The bound includes the presolve constant (gradient 1 for elements fixed to 1) and, with
+ * normalize_costs, the dependence on the largest element cost. The candidate mask and
+ * presolve are held fixed. The handle's state is left at the recorded final state.
+ * Synchronises.
  * Errors: DISCO_ERR_INVALID_ARG (no record, output too small), DISCO_ERR_OOM. */
 int disco_grad(disco_handle *h, float *dlb_dpair_costs, int64_t n);
 

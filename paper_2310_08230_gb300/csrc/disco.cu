@@ -1769,7 +1769,8 @@ int disco_grad(disco_handle* h, float* dlb_dpair_costs, int64_t n) {
     CK(cudaMemcpyAsync(cb.data(), h->cbar, cb.size() * 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     mark("reset adjoint, costs");
-    // chain rule to the pair costs: c_e = (mean of e's three pair costs) / scale
+    // chain rule to the pair costs: c_e = (mean of e's three pair costs) / scale, or with
+    // cost model 1 (Eq. 2) c_e = sum over the corners of (A_X(m) + A_Y(n)) d(m, n) / scale
     std::vector<float> g(static_cast<size_t>(need), 0.0f);
     std::vector<int64_t> offs(h->plans.size() + 1, 0);
     for (size_t i = 0; i < h->plans.size(); ++i) offs[i + 1] = offs[i] + int64_t(h->plans[i].nvx) * h->plans[i].nvy;
@@ -1790,7 +1791,14 @@ int disco_grad(disco_handle* h, float* dlb_dpair_costs, int64_t n) {
             double gr = ge[e] / P.cost_scale;
             if (e == P.cost_scale_elem) gr -= cc / P.cost_scale;
             if (gr == 0.0) continue;
-            for (int v = 0; v < 3; ++v) gp[size_t(P.vm[3 * e + v]) * P.nvy + P.vn[3 * e + v]] += gr / 3.0;
+            if (P.area_x.empty()) {
+                for (int v = 0; v < 3; ++v) gp[size_t(P.vm[3 * e + v]) * P.nvy + P.vn[3 * e + v]] += gr / 3.0;
+            } else {
+                for (int v = 0; v < 3; ++v) {
+                    const int m = P.vm[3 * e + v], nn = P.vn[3 * e + v];
+                    gp[size_t(m) * P.nvy + nn] += gr * (P.area_x[size_t(m)] + P.area_y[size_t(nn)]);
+                }
+            }
         }
         for (size_t q = 0; q < gp.size(); ++q) g[size_t(off) + q] = float(gp[q]);
     }

@@ -498,6 +498,10 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         }
     }
 
+    if (cost_model == 1) {  // kept for the chain rule of the gradient
+        P->area_x = std::move(aX);
+        P->area_y = std::move(aY);
+    }
     tr.mark("costs");
     // ---- closedness rows: product edge (p, q), p < q in (m, n) order. Entries are bucketed by
     // the X vertex of p, each bucket sorted by (key, entry), rows are the runs of equal keys.

@@ -213,6 +213,7 @@ struct Plan {
     pod_vector<double> cost;            // c_p per variable (normalised unless disabled)
     double cost_scale = 1.0;            // c_p = (mean of its pair costs) / cost_scale
     int64_t cost_scale_elem = -1;       // the element whose raw cost is cost_scale (normalised)
+    std::vector<double> area_x, area_y; // cost model 1 (Eq. 2): mixed vertex areas; else empty
     pod_vector<int64_t> row_ptr;        // rows: closedness, X projection, Y projection
     pod_vector<int32_t> row_var;
     pod_vector<int8_t> row_coef;

@@ -65,3 +65,36 @@ def test_eq2_needs_positions(torch):
     d = P.pair_euclid(inst.FX, inst.FY).astype(np.float32)
     with pytest.raises(L.DiscoError):
         Solver(inst.X.T, inst.Y.T, d, None, cost_model=1)
+
+
+@pytest.mark.parametrize("normalize", [0, 1])
+def test_eq2_gradient_matches_fp64_autograd(torch, normalize):
+    """The gradient through Eq. 2 costs: the FP64 replica's element-cost gradient, chained to
+    the pair distances with each corner's weight A_X(m) + A_Y(n)."""
+    from oracle import grad as G
+    from paper_2310_08230_gb300.api import Solver
+
+    inst = I.tet()
+    d = P.pair_euclid(inst.FX, inst.FY).astype(np.float32)
+    iters, every = 12, 5
+    s = Solver(inst.X.T, inst.Y.T, d, None, VX=inst.X.V, VY=inst.Y.V, cost_model=1, normalize_costs=normalize,
+               graph_iters=0)
+    s.record(iters, every)
+    g = s.grad().reshape(d.shape)
+    s.close()
+    prob = P.build_problem(inst.X.T, inst.Y.T, d.astype(np.float64), None, cost_model=1, VX=inst.X.V, VY=inst.Y.V,
+                           normalize=False)
+    fixed, const = P.presolve(prob)
+    raw = prob.cost.copy()
+    scale = raw.max() if normalize else 1.0
+    c = raw / scale
+    _, gc = G.bound_and_grad(B.decompose(prob, fixed, const / scale, 0), c, fixed, iters)
+    graw = gc / scale
+    if normalize:
+        graw[int(np.argmax(raw))] -= float(gc @ c) / scale
+    aX, aY = P.mixed_areas(inst.X.V, inst.X.T), P.mixed_areas(inst.Y.V, inst.Y.T)
+    ref = np.zeros(d.shape)
+    for v in range(3):
+        np.add.at(ref, (prob.vm[:, v], prob.vn[:, v]), graw * (aX[prob.vm[:, v]] + aY[prob.vn[:, v]]))
+    err = np.linalg.norm(g - ref) / max(np.linalg.norm(ref), 1e-30)
+    assert err < 1e-3, err
