@@ -167,7 +167,9 @@ def gpu_arm(args):
     allowed = torch.empty((nvx, nvy), dtype=torch.uint8, device="cuda")
     mx, tx = _mesh(inst.X.T, nvx)
     my, ty = _mesh(inst.Y.T, nvy)
-    opts = default_opts(stream=sptr, lb_every=20, conv_rel_tol=1e-6, split_chunk=args.split_chunk)
+    # replicas on one node share its host cores: each rank's host compiler gets its share
+    opts = default_opts(stream=sptr, lb_every=20, conv_rel_tol=1e-6, split_chunk=args.split_chunk,
+                        host_threads=max(1, (os.cpu_count() or 1) // world) if world > 1 else 0)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     max_iters = args.max_iters
 
