@@ -124,3 +124,24 @@ def test_tile_order_is_checked(lib):
     inst, d, a = _pairs()[0]
     with pytest.raises(L.DiscoError):
         Solver(inst.X.T, inst.Y.T, d.astype(np.float32), a, tile_order=3)
+
+
+def test_tile_order_on_a_single_pair(lib):
+    """The locality order forced on one pair (config2, split 16) keeps its min-marginals and
+    rounding; the bound differs at most by the order of the FP64 tile sums."""
+    Solver = lib
+    inst, d, a = _pairs()[2]
+    out = []
+    for order in (1, 2):
+        s = Solver(inst.X.T, inst.Y.T, d.astype(np.float32), a, split_chunk=16, tile_order=order)
+        s.dual(40)
+        x, cost, ok = s.primal()
+        s.dual(5)
+        out.append((s.lower_bound(), s.min_marginals(), x, cost, ok))
+        s.close()
+    (lb1, mm1, x1, c1, ok1), (lb2, mm2, x2, c2, ok2) = out
+    assert lb2 == pytest.approx(lb1, rel=1e-12)
+    np.testing.assert_array_equal(mm2, mm1)
+    assert ok1 and ok2
+    np.testing.assert_array_equal(x2, x1)
+    assert c2 == pytest.approx(c1, rel=1e-12)
