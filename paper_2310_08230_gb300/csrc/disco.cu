@@ -541,7 +541,11 @@ int upload(disco_handle* h) {
     int32_t* d_seg_len = reinterpret_cast<int32_t*>(carve(b_segs4));
     uint32_t* d_seg_vb = reinterpret_cast<uint32_t*>(carve(b_segs4));
     int64_t* d_var_base = reinterpret_cast<int64_t*>(carve(size_t(ni + 1) * 8));
-    auto release = [&] { cudaFreeAsync(tmp, s); };
+    struct Release {  // the temporaries go back to the pool on every exit (stream-ordered)
+        char* p;
+        cudaStream_t s;
+        ~Release() { cudaFreeAsync(p, s); }
+    } release_tmp{tmp, s};
     rc = DISCO_OK;
     for (int64_t i = 0; i < ni && !rc; ++i) {
         const Plan& P = h->plans[i];
@@ -557,10 +561,7 @@ int upload(disco_handle* h) {
             (rc = copy_in(d_var_base, h->var_base.data(), size_t(ni + 1) * 8, s)) ||
             (rc = copy_in(h->tiles, tiles.data(), tiles.size() * sizeof(TileInfo), s));
     }
-    if (rc) {
-        release();
-        return rc;
-    }
+    if (rc) return rc;
     // padding lanes and layers: no variable, zero descriptor and lambda
     CK(cudaMemsetAsync(h->var, 0xFF, size_t(slot_base) * 4, s));
     CK(cudaMemsetAsync(h->desc, 0, size_t(slot_base) * 4, s));
@@ -569,7 +570,6 @@ int upload(disco_handle* h) {
     CK(launch_layout(d_seg_canon, d_seg_len, d_seg_pos, d_seg_vb, nseg_all, cvar, cdesc, clam, clam_lo, h->var, h->desc,
                      h->lam, h->lam_lo, h->canon_pos, s));
     CK(launch_instance_of(d_var_base, int32_t(ni), h->nint, h->var_inst, s));
-    release();
     CK(cudaMemcpyAsync(h->lam0, h->lam, size_t(slot_base) * 4, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(h->lam0_lo, h->lam_lo, size_t(slot_base) * 4, cudaMemcpyDeviceToDevice, s));
     if ((rc = copy_in(h->consts, consts.data(), consts.size() * 8, s))) return rc;
@@ -1813,7 +1813,12 @@ void disco_free(disco_handle* h) {
     if (!h) return;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    // the host plans (hundreds of MB for a large pair) go back to the system on a background
+    // thread: unmapping their pages takes milliseconds the caller need not wait for
+    std::vector<Plan> plans;
+    plans.swap(h->plans);
     delete h;
+    if (!plans.empty()) std::thread([p = std::move(plans)]() mutable { std::vector<Plan>().swap(p); }).detach();
 }
 
 }  // extern "C"
