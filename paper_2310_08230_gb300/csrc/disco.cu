@@ -832,12 +832,20 @@ int disco_candidates(const float* d, int32_t nvx, int32_t nvy, int32_t k, const 
     if (!rings(X, &px, &rx) || !rings(Y, &py, &ry)) return fail(DISCO_ERR_INVALID_ARG, "candidates: bad mesh");
     int32_t *dpx, *drx, *dpy, *dry, *tk;
     float* dT;
-    CK(cudaMallocAsync(&dpx, px.size() * 4, s));
-    CK(cudaMallocAsync(&drx, rx.size() * 4, s));
-    CK(cudaMallocAsync(&dpy, py.size() * 4, s));
-    CK(cudaMallocAsync(&dry, ry.size() * 4, s));
-    CK(cudaMallocAsync(&tk, size_t(std::max(nvx, nvy)) * k * 4, s));
-    CK(cudaMallocAsync(&dT, size_t(nvx) * nvy * 4, s));
+    // temporaries from the library's pool (it keeps freed memory for the next call)
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    CK(pool_for(dev, &pool));
+    auto palloc = [&](auto** p, size_t bytes) {
+        return cudaMallocFromPoolAsync(reinterpret_cast<void**>(p), std::max<size_t>(bytes, 4), pool, s);
+    };
+    CK(palloc(&dpx, px.size() * 4));
+    CK(palloc(&drx, rx.size() * 4));
+    CK(palloc(&dpy, py.size() * 4));
+    CK(palloc(&dry, ry.size() * 4));
+    CK(palloc(&tk, size_t(std::max(nvx, nvy)) * k * 4));
+    CK(palloc(&dT, size_t(nvx) * nvy * 4));
     CK(cudaMemcpyAsync(dpx, px.data(), px.size() * 4, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(drx, rx.data(), rx.size() * 4, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(dpy, py.data(), py.size() * 4, cudaMemcpyHostToDevice, s));
