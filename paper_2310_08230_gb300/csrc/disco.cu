@@ -921,7 +921,6 @@ int build_handle(int32_t n, const disco_mesh* X, const disco_mesh* Y, const floa
     std::vector<int32_t> order(static_cast<size_t>(n));
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return est[a] > est[b]; });
-    (void)outer;
     // more pairs than threads: a pair holding more than half a thread's share of the work
     // (1/hw of the total) would finish last on one thread, so it gets one thread per half
     // share, up to 4 (the largest pairs start first)
