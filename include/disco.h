@@ -96,8 +96,8 @@ typedef struct {
                                  same, up to the order of the bound's FP64 tile sums): 0 = by
                                  size (2 when both averaging tables exceed 64 MB, else 1);
                                  1 = width class, then length, over each instance; 2 = blocks
-                                 of 4096 segments in row order (table locality), each by width
-                                 class and length */
+                                 of 4096 segments in mesh-region order (table locality), each
+                                 by width class and length */
 } disco_opts;
 
 typedef struct {

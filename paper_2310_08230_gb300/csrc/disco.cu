@@ -301,9 +301,11 @@ int upload(disco_handle* h) {
     for (int64_t i = 0; i < ni; ++i) maxL = std::max(maxL, h->plans[i].max_layers);
     // Averaging tables far larger than L2 (big batches): every slot's sector gather and
     // scatter would miss if the warps running at one time held segments from all over the
-    // instance. Then segments are cut into blocks of kLocalityBlock in plan order (rows of
-    // nearby X vertices and triangles touch nearby variables), each block is sorted by width
-    // class and length, and tiles follow the blocks. Otherwise (tables L2-resident) segments
+    // instance. Then segments are ordered by the region of their row (closedness rows by the
+    // X vertex of their bucket, X projection rows beside their triangle's smallest vertex, Y
+    // projection rows last), cut into blocks of kLocalityBlock, each block sorted by width
+    // class and length, and tiles follow the blocks: the warps running together then hold
+    // most of the slots of the variables they touch. Otherwise (tables L2-resident) segments
     // are sorted by width class and length over the whole instance. Instances are ordered in
     // parallel, then concatenated in instance order.
     int64_t nint_all = 0;
@@ -336,11 +338,18 @@ int upload(disco_handle* h) {
             }
         };
         if (locality) {
-            int64_t gcnt[5] = {0, 0, 0, 0, 0};
-            for (const Segment& sg : P.segs) ++gcnt[launch_group(width_class(sg.max_width)) + 1];
-            for (int g = 0; g < 4; ++g) gcnt[g + 1] += gcnt[g];
-            const int64_t gstart[5] = {gcnt[0], gcnt[1], gcnt[2], gcnt[3], gcnt[4]};
-            for (int64_t k = 0; k < nseg; ++k) R.seg[size_t(gcnt[launch_group(width_class(P.segs[k].max_width))]++)] = k;
+            // stable counting sort by (launch group, region of the segment's row), so that the
+            // closedness and X projection rows of one X neighbourhood are adjacent
+            const int64_t nreg = int64_t(P.nvx) + P.n_projy;
+            std::vector<int64_t> rcnt(size_t(4 * nreg) + 1, 0);
+            auto rkey = [&](const Segment& sg) {
+                return size_t(launch_group(width_class(sg.max_width))) * size_t(nreg) + size_t(P.row_region[size_t(sg.row)]);
+            };
+            for (const Segment& sg : P.segs) ++rcnt[rkey(sg) + 1];
+            for (size_t q = 1; q < rcnt.size(); ++q) rcnt[q] += rcnt[q - 1];
+            int64_t gstart[5];
+            for (int g = 0; g <= 4; ++g) gstart[g] = rcnt[size_t(g) * size_t(nreg)];
+            for (int64_t k = 0; k < nseg; ++k) R.seg[size_t(rcnt[rkey(P.segs[k])]++)] = k;
             std::vector<uint64_t> key;
             for (int g = 0; g < 4; ++g)
                 for (int64_t b0 = gstart[g]; b0 < gstart[g + 1]; b0 += kLocalityBlock) {

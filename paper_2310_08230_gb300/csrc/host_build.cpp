@@ -733,6 +733,14 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     P->n_projx = X.nt;
     P->n_projy = Y.nt;
     P->nrows = int64_t(P->rhs.size());
+    P->row_region.resize(size_t(P->nrows));
+    parallel_chunks(nvx, nth, [&](int, int64_t m0, int64_t m1) {
+        for (int64_t m = m0; m < m1; ++m)
+            std::fill(P->row_region.begin() + brows[m], P->row_region.begin() + brows[m + 1], int32_t(m));
+    });
+    for (int t = 0; t < X.nt; ++t)
+        P->row_region[size_t(n_closed + t)] = std::min({X.T[3 * t], X.T[3 * t + 1], X.T[3 * t + 2]});
+    for (int t = 0; t < Y.nt; ++t) P->row_region[size_t(n_closed + X.nt + t)] = nvx + t;
     if (proj_end != int64_t(P->row_var.size())) { *err = "internal: projection entry count"; return DISCO_ERR_INVALID_ARG; }
     P->row_ptr.push_back(proj_end);
     const int64_t nr = P->nrows;

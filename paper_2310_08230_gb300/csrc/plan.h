@@ -214,6 +214,10 @@ struct Plan {
     double cost_scale = 1.0;            // c_p = (mean of its pair costs) / cost_scale
     int64_t cost_scale_elem = -1;       // the element whose raw cost is cost_scale (normalised)
     std::vector<double> area_x, area_y; // cost model 1 (Eq. 2): mixed vertex areas; else empty
+    // per row, the mesh region its variables sit in (a tile-order key): a closedness row the
+    // X vertex of its bucket, an X projection row its triangle's smallest X vertex, a Y
+    // projection row nvx + its Y triangle (Y rows gather elements from all over X)
+    pod_vector<int32_t> row_region;
     pod_vector<int64_t> row_ptr;        // rows: closedness, X projection, Y projection
     pod_vector<int32_t> row_var;
     pod_vector<int8_t> row_coef;
