@@ -93,6 +93,10 @@ struct disco_handle {
     int64_t ntiles = 0, nslots_tile = 0, nnodes_tile = 0, nint = 0;
     // device buffers
     TileInfo* tiles = nullptr;
+    // locality tile order: the same tiles with the region blocks of each launch group in
+    // reverse order, for the backward passes (they start where the forward pass ended, on
+    // averaging sectors still in L2); null in the length order
+    TileInfo* tiles_bwd = nullptr;
     uint32_t* var = nullptr;
     uint32_t* desc = nullptr;
     float* lam = nullptr;
@@ -186,9 +190,9 @@ struct disco_handle {
         return DISCO_OK;
     }
 
-    KArgs args(const WidthClass& c) {
+    KArgs args(const WidthClass& c, bool backward = false) {
         KArgs a{};
-        a.tiles = tiles;
+        a.tiles = backward && tiles_bwd ? tiles_bwd : tiles;
         a.tile0 = c.tile0;
         a.tile_end = c.tile_end;
         a.var = var;
@@ -211,7 +215,8 @@ struct disco_handle {
 
     // One pass over every width class (a half-pass flips the averaging buffers).
     int pass(Pass p) {
-        for (const WidthClass& c : classes) CK(launch_pass(p, c.W, args(c), stream, geometry));
+        const bool bwd = p == Pass::BwdMMA || p == Pass::BwdMMARound || p == Pass::BwdMM || p == Pass::BwdReset;
+        for (const WidthClass& c : classes) CK(launch_pass(p, c.W, args(c, bwd), stream, geometry));
         if (p == Pass::FwdMMA || p == Pass::BwdMMA || p == Pass::FwdMMARound || p == Pass::BwdMMARound) cur ^= 1;
         return DISCO_OK;
     }
@@ -296,6 +301,7 @@ int upload(disco_handle* h) {
     std::vector<TileInfo> tiles;
     std::vector<int64_t> tile_first;  // first entry of the tile's segments in `order`
     std::vector<int32_t> tile_count, tile_inst;
+    std::vector<int64_t> tile_block;  // locality order: each tile's block (global id)
     std::vector<TileSeg> order;
     int maxL = 1;
     for (int64_t i = 0; i < ni; ++i) maxL = std::max(maxL, h->plans[i].max_layers);
@@ -318,6 +324,7 @@ int upload(disco_handle* h) {
         std::vector<TileInfo> tiles;
         std::vector<int64_t> first;  // into seg
         std::vector<int32_t> count;
+        std::vector<int32_t> block;  // locality order: the block each tile belongs to
     };
     std::vector<InstTiles> per(static_cast<size_t>(ni));
     parallel_tasks(ni, nth, [&](int64_t i) {
@@ -351,6 +358,7 @@ int upload(disco_handle* h) {
             for (int g = 0; g <= 4; ++g) gstart[g] = rcnt[size_t(g) * size_t(nreg)];
             for (int64_t k = 0; k < nseg; ++k) R.seg[size_t(rcnt[rkey(P.segs[k])]++)] = k;
             std::vector<uint64_t> key;
+            int32_t nblk = 0;
             for (int g = 0; g < 4; ++g)
                 for (int64_t b0 = gstart[g]; b0 < gstart[g + 1]; b0 += kLocalityBlock) {
                     const int64_t b1 = std::min(gstart[g + 1], b0 + kLocalityBlock);
@@ -364,7 +372,11 @@ int upload(disco_handle* h) {
                     std::sort(key.begin(), key.end());
                     std::vector<int64_t> tmp(R.seg.begin() + b0, R.seg.begin() + b1);
                     for (int64_t k = b0; k < b1; ++k) R.seg[k] = tmp[size_t(key[size_t(k - b0)] & 0xFFFFFFu)];
+                    const size_t t_before = R.tiles.size();
                     cut_tiles(b0, b1);  // tiles never straddle a block
+                    R.block.resize(R.tiles.size());
+                    for (size_t t = t_before; t < R.tiles.size(); ++t) R.block[t] = nblk;
+                    ++nblk;
                 }
         } else {
             // stable counting sort by (class ascending, length descending): per-chunk counts,
@@ -406,6 +418,10 @@ int upload(disco_handle* h) {
         tile_first.resize(tiles.size());
         tile_count.resize(tiles.size());
         tile_inst.resize(tiles.size());
+        if (locality) tile_block.resize(tiles.size());
+        std::vector<int64_t> boff(size_t(ni) + 1, 0);  // global block ids: instance by instance
+        for (int64_t i = 0; i < ni; ++i)
+            boff[size_t(i) + 1] = boff[size_t(i)] + (per[size_t(i)].block.empty() ? 0 : per[size_t(i)].block.back() + 1);
         parallel_tasks(ni, nth, [&](int64_t i) {
             InstTiles& R = per[size_t(i)];
             const int64_t so = soff[size_t(i)], to = toff[size_t(i)];
@@ -415,6 +431,7 @@ int upload(disco_handle* h) {
                 tile_first[size_t(to) + t] = so + R.first[t];
                 tile_count[size_t(to) + t] = R.count[t];
                 tile_inst[size_t(to) + t] = int32_t(i);
+                if (locality) tile_block[size_t(to) + t] = boff[size_t(i)] + R.block[t];
             }
             InstTiles().seg.swap(R.seg);
         });
@@ -436,18 +453,20 @@ int upload(disco_handle* h) {
         for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
         for (size_t t = 0; t < tiles.size(); ++t) perm[size_t(cnt[key(t)]++)] = t;
         std::vector<TileInfo> t2(tiles.size());
-        std::vector<int64_t> f2(tiles.size());
+        std::vector<int64_t> f2(tiles.size()), b2(tile_block.size());
         std::vector<int32_t> c2(tiles.size()), i2(tiles.size());
         for (size_t k = 0; k < perm.size(); ++k) {
             t2[k] = tiles[perm[k]];
             f2[k] = tile_first[perm[k]];
             c2[k] = tile_count[perm[k]];
             i2[k] = tile_inst[perm[k]];
+            if (locality) b2[k] = tile_block[perm[k]];
         }
         tiles.swap(t2);
         tile_first.swap(f2);
         tile_count.swap(c2);
         tile_inst.swap(i2);
+        tile_block.swap(b2);
     }
     h->classes.clear();
     int64_t slot_base = 0, node_base = 0;
@@ -463,6 +482,23 @@ int upload(disco_handle* h) {
     h->ntiles = int64_t(tiles.size());
     h->nslots_tile = slot_base;
     h->nnodes_tile = node_base;
+    // backward order (locality only): inside each launch group, the runs of tiles of one block
+    // in reverse order, each run's tiles (longest first) kept in order
+    std::vector<TileInfo> tiles_bwd;
+    if (locality) {
+        tiles_bwd.reserve(tiles.size());
+        for (const WidthClass& c : h->classes) {
+            std::vector<std::pair<int, int>> runs;  // [begin, end) of each block's tiles
+            for (int t = c.tile0; t < c.tile_end;) {
+                int u = t + 1;
+                while (u < c.tile_end && tile_block[size_t(u)] == tile_block[size_t(t)]) ++u;
+                runs.emplace_back(t, u);
+                t = u;
+            }
+            for (size_t r = runs.size(); r-- > 0;)
+                for (int t = runs[r].first; t < runs[r].second; ++t) tiles_bwd.push_back(tiles[size_t(t)]);
+        }
+    }
     // tiles of each instance, in tile order (the bound sums them in this fixed order)
     h->inst_tile_ptr.assign(size_t(ni) + 1, 0);
     for (int32_t i : tile_inst) ++h->inst_tile_ptr[i + 1];
@@ -498,6 +534,7 @@ int upload(disco_handle* h) {
     tr.mark("tile layout");
     int rc;
     if ((rc = h->alloc(&h->tiles, h->ntiles))) return rc;
+    if (locality && (rc = h->alloc(&h->tiles_bwd, h->ntiles))) return rc;
     if ((rc = h->alloc(&h->var, slot_base))) return rc;
     if ((rc = h->alloc(&h->desc, slot_base))) return rc;
     if ((rc = h->alloc(&h->lam, slot_base))) return rc;
@@ -568,7 +605,8 @@ int upload(disco_handle* h) {
         (rc = copy_in(d_seg_canon, seg_canon.data(), b_segs, s)) || (rc = copy_in(d_seg_pos, seg_pos.data(), b_segs, s)) ||
             (rc = copy_in(d_seg_len, seg_len.data(), b_segs4, s)) || (rc = copy_in(d_seg_vb, seg_vb.data(), b_segs4, s)) ||
             (rc = copy_in(d_var_base, h->var_base.data(), size_t(ni + 1) * 8, s)) ||
-            (rc = copy_in(h->tiles, tiles.data(), tiles.size() * sizeof(TileInfo), s));
+            (rc = copy_in(h->tiles, tiles.data(), tiles.size() * sizeof(TileInfo), s)) ||
+            (locality && (rc = copy_in(h->tiles_bwd, tiles_bwd.data(), tiles_bwd.size() * sizeof(TileInfo), s)));
     }
     if (rc) return rc;
     // padding lanes and layers: no variable, zero descriptor and lambda
