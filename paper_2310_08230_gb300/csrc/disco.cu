@@ -1867,12 +1867,7 @@ void disco_free(disco_handle* h) {
     if (!h) return;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
-    // the host plans (hundreds of MB for a large pair) go back to the system on a background
-    // thread: unmapping their pages takes milliseconds the caller need not wait for
-    std::vector<Plan> plans;
-    plans.swap(h->plans);
     delete h;
-    if (!plans.empty()) std::thread([p = std::move(plans)]() mutable { std::vector<Plan>().swap(p); }).detach();
 }
 
 }  // extern "C"
