@@ -953,6 +953,9 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         {
             RowChunk& C = chunks[c];
             const int64_t r0 = row_cut[size_t(c)], r1 = row_cut[size_t(c) + 1];
+            // about one slot per entry (fixed entries drop out, split chains add a few)
+            C.var.reserve(size_t(P->row_ptr[size_t(r1)] - P->row_ptr[size_t(r0)]));
+            C.desc.reserve(C.var.capacity());
             auto add_slot = [&](int32_t var, int w, int wn, int d0, int d1, bool one, int rank) {
                 C.var.push_back(var);
                 C.desc.push_back(pack_desc(w, wn, d0, d1, one, rank, var < 0 ? 2 : deg_free[var]));
