@@ -83,6 +83,11 @@ struct disco_handle {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // averaging of the MMA half-passes (kernels.cu): slot masses, the positions of each
+    // variable's slots, and the per-variable deferred means they reduce to
+    int32_t* vpos = nullptr;
+    float* slot_mass = nullptr;
+    float2* pend_tab = nullptr;
     disco_opts opts{};
     std::vector<Plan> plans;              // one per instance
     std::vector<int64_t> var_base;        // internal variable offset per instance (n + 1)
@@ -202,6 +207,8 @@ struct disco_handle {
         a.F = F;
         a.B = B;
         a.acc_in = acc[cur];
+        a.pend_tab = pend_tab;
+        a.slot_mass = slot_mass;
         a.acc_out = acc[cur ^ 1];
         a.state = state;
         a.omega = opts.omega;
@@ -217,6 +224,7 @@ struct disco_handle {
     int pass(Pass p) {
         const bool bwd = p == Pass::BwdMMA || p == Pass::BwdMMARound || p == Pass::BwdMM || p == Pass::BwdReset;
         for (const WidthClass& c : classes) CK(launch_pass(p, c.W, args(c, bwd), stream, geometry));
+        if (p == Pass::FwdMMA || p == Pass::BwdMMA) CK(launch_reduce(vpos, slot_mass, deg, nint, pend_tab, stream));
         if (p == Pass::FwdMMA || p == Pass::BwdMMA || p == Pass::FwdMMARound || p == Pass::BwdMMARound) cur ^= 1;
         return DISCO_OK;
     }
@@ -534,6 +542,9 @@ int upload(disco_handle* h) {
     tr.mark("tile layout");
     int rc;
     if ((rc = h->alloc(&h->tiles, h->ntiles))) return rc;
+    if ((rc = h->alloc(&h->vpos, h->nint * kAccStride)) || (rc = h->alloc(&h->slot_mass, slot_base)) ||
+        (rc = h->alloc(&h->pend_tab, h->nint)))
+        return rc;
     if (locality && (rc = h->alloc(&h->tiles_bwd, h->ntiles))) return rc;
     if ((rc = h->alloc(&h->var, slot_base))) return rc;
     if ((rc = h->alloc(&h->desc, slot_base))) return rc;
@@ -617,6 +628,8 @@ int upload(disco_handle* h) {
     CK(launch_layout(d_seg_canon, d_seg_len, d_seg_pos, d_seg_vb, nseg_all, cvar, cdesc, clam, clam_lo, h->var, h->desc,
                      h->lam, h->lam_lo, h->canon_pos, s));
     CK(launch_instance_of(d_var_base, int32_t(ni), h->nint, h->var_inst, s));
+    CK(cudaMemsetAsync(h->vpos, 0, size_t(h->nint) * kAccStride * 4, s));  // unused ranks stay in bounds
+    CK(launch_vpos(h->var, h->desc, slot_base, h->vpos, s));
     CK(cudaMemcpyAsync(h->lam0, h->lam, size_t(slot_base) * 4, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(h->lam0_lo, h->lam_lo, size_t(slot_base) * 4, cudaMemcpyDeviceToDevice, s));
     if ((rc = copy_in(h->consts, consts.data(), consts.size() * 8, s))) return rc;
@@ -724,9 +737,23 @@ int capture_iterations(disco_handle* h) {
     return DISCO_OK;
 }
 
+int run_iterations_tab(disco_handle* h, int iters);
+
+// Dual iterations. Outside this call the averaging sectors acc[cur] hold the state; inside,
+// the MMA half-passes keep it as slot masses and per-variable means: the means are formed
+// from the sectors on entry, and the last pass's masses go back into sector form on exit.
 int run_iterations(disco_handle* h, int iters) {
     int rc;
     if (!h->has_b && (rc = reset_b(h))) return rc;
+    if (iters <= 0) return DISCO_OK;  // no pass writes slot masses: the sectors stay as they are
+    CK(launch_pend_table(h->acc[h->cur], h->deg, h->nint, h->pend_tab, h->stream));
+    if ((rc = run_iterations_tab(h, iters))) return rc;
+    CK(launch_scatter_back(h->vpos, h->slot_mass, h->deg, h->nint, h->acc[h->cur], h->stream));
+    return DISCO_OK;
+}
+
+int run_iterations_tab(disco_handle* h, int iters) {
+    int rc;
     int t = 0;
     if (!h->tuned && h->opts.autotune && iters >= kTrials * 3) {
         int used = 0;
@@ -1763,18 +1790,16 @@ int disco_grad(disco_handle* h, float* dlb_dpair_costs, int64_t n) {
         // per-variable table) go to the tape, and the pass stores its node costs straight into
         // the tape (the node arrays are pointed there); the node costs it reads are the
         // previous pass's (or the checkpoint's) stored ones
+        CK(launch_pend_table(h->acc[h->cur], h->deg, h->nint, h->pend_tab, s));  // the MMA passes read it
         float* const F0 = h->F;
         float* const B0 = h->B;
         const size_t ns = size_t(h->nslots_tile) * 4;
         for (int t = 0; t < nit && !rc; ++t)
             for (int dir = 0; dir < 2 && !rc; ++dir) {
                 Snap& tp = h->tape[2 * t + dir];
-                if ((rc = d2d(tp.lam, h->lam, ns, s)) || (rc = d2d(tp.lam_lo, h->lam_lo, ns, s))) break;
-                const cudaError_t e = launch_pend_table(h->acc[h->cur], h->deg, h->nint, tp.pend, s);
-                if (e != cudaSuccess) {
-                    rc = fail(DISCO_ERR_CUDA, cudaGetErrorString(e));
+                if ((rc = d2d(tp.lam, h->lam, ns, s)) || (rc = d2d(tp.lam_lo, h->lam_lo, ns, s)) ||
+                    (rc = d2d(tp.pend, h->pend_tab, size_t(h->nint) * sizeof(float2), s)))
                     break;
-                }
                 tp.cur = h->cur;
                 (dir == 0 ? h->F : h->B) = tp.nodes;
                 rc = h->pass(dir == 0 ? Pass::FwdMMA : Pass::BwdMMA);

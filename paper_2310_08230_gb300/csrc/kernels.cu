@@ -11,10 +11,14 @@
 // deferred, parallel-across-BDDs min-marginal averaging (Alg. 1 "MMA"), dual bound (Eq. D),
 // rounding by min-marginal agreement and propagation (App. A.5, Sec. 3 pipeline).
 //
-// Averaging without atomics: a slot of variable i with rank r (its position among i's slots)
-// writes the mass it removes to acc_out[i * 8 + r]; the next half-pass reads the deg values
-// of acc_in[i * 8 ..] (one 32-byte sector) and adds their mean. Sums run in rank order, so
-// every result is deterministic.
+// Averaging without atomics, in two forms with the same arithmetic:
+//  * MMA half-passes (MODE 0): every slot writes the mass it removes to slot_mass (tile
+//    layout, coalesced); a reduction kernel (store.cu) sums each variable's deg masses in
+//    rank order into a double-float mean, which the next half-pass reads (8 bytes per slot);
+//  * the other passes: a slot of variable i with rank r writes to acc_out[i * 8 + r]; the
+//    next pass reads the deg values of acc_in[i * 8 ..] (one 32-byte sector) and adds their
+//    mean.
+// Sums run in rank order, so every result is deterministic and both forms agree bit for bit.
 #include <atomic>
 #include <cfloat>
 
@@ -57,6 +61,10 @@ __device__ __forceinline__ void cp_async16(float* dst, const float* src) {
     const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async8(float* dst, const float* src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -68,15 +76,21 @@ __device__ __forceinline__ void load_head(const KArgs& a, int64_t si, bool ok, u
 
 // Copies of one layer's inputs into stage `st` (this lane's slots), then one commit.
 // NODES: 0 none, 1 = B of layer l + 1 (count wn), 2 = F of layer l (count w).
-template <int W, int NODES>
+// TAB: the variable's deferred mean comes ready from the per-variable table (MMA passes:
+// 8 bytes, into the first two floats of the sector slot) instead of its averaging sector.
+template <int W, int NODES, bool TAB>
 __device__ __forceinline__ void stage_issue(const KArgs& a, float* st, int lane, int64_t si, const float* node_row,
                                             uint32_t v, uint32_t dsc) {
     if (v != kNoVar) {
         cp_async4(st + lane, a.lam + si);
         cp_async4(st + 32 + lane, a.lam_lo + si);
-        const float* ap = a.acc_in + size_t(v) * kAccStride;
-        cp_async16(st + 96 + 4 * lane, ap);
-        if (int((dsc >> 25) & 7u) > 4) cp_async4(st + 64 + lane, ap + 4);
+        if (TAB) {
+            cp_async8(st + 96 + 4 * lane, reinterpret_cast<const float*>(a.pend_tab + v));
+        } else {
+            const float* ap = a.acc_in + size_t(v) * kAccStride;
+            cp_async16(st + 96 + 4 * lane, ap);
+            if (int((dsc >> 25) & 7u) > 4) cp_async4(st + 64 + lane, ap + 4);
+        }
         if (NODES) {
             const int n = NODES == 1 ? int((dsc >> 6) & 63u) + 1 : int(dsc & 63u) + 1;
 #pragma unroll
@@ -142,7 +156,7 @@ __device__ __forceinline__ void forward_tile(const KArgs& a, const int tile, con
 #pragma unroll
     for (int k = 0; k < P; ++k) {
         load_head(a, sb + int64_t(k) * 32, k < L, cv[k], cd[k]);
-        stage_issue<W, NODES>(a, ring + k * SF, lane, sb + int64_t(k) * 32, Bl + int64_t(k + 1) * W * 32, cv[k], cd[k]);
+        stage_issue<W, NODES, MODE == 0>(a, ring + k * SF, lane, sb + int64_t(k) * 32, Bl + int64_t(k + 1) * W * 32, cv[k], cd[k]);
         load_head(a, sb + int64_t(k + P) * 32, k + P < L, hv[k], hd[k]);
     }
     for (int l0 = 0; l0 < L; l0 += P) {
@@ -158,7 +172,7 @@ __device__ __forceinline__ void forward_tile(const KArgs& a, const int tile, con
             uint32_t nv, nd;
             load_head(a, sb + int64_t(l + 2 * P) * 32, l + 2 * P < L, nv, nd);
             const int64_t si = sb + int64_t(l) * 32;
-            const df p = pend_staged(c, d.deg);
+            const df p = MODE == 0 ? df{c.acc.x, c.acc.y} : pend_staged(c, d.deg);
             df Lm{c.lam, c.lo};
             const uint8_t st = kRound ? __ldg(a.state + v) : kFree;
             const bool al0 = st != kFix1, al1 = st != kFix0;
@@ -193,7 +207,8 @@ __device__ __forceinline__ void forward_tile(const KArgs& a, const int tile, con
                     a.lam_lo[si] = Lm.lo;
                     lm = Lm.hi;
                 }
-                a.acc_out[size_t(v) * kAccStride + d.rank] = removed;
+                if (MODE == 0) a.slot_mass[si] = removed;  // coalesced; the reduction forms the means
+                else a.acc_out[size_t(v) * kAccStride + d.rank] = removed;
             } else {
                 lm = df_add(Lm, p).hi;
             }
@@ -210,7 +225,7 @@ __device__ __forceinline__ void forward_tile(const KArgs& a, const int tile, con
                 f[s] = s < d.wn ? fminf(v0, v1) : BIG;
             }
             // stage layer l + P into the slot just consumed
-            stage_issue<W, NODES>(a, ring + k * SF, lane, sb + int64_t(l + P) * 32, Bl + int64_t(l + P + 1) * W * 32,
+            stage_issue<W, NODES, MODE == 0>(a, ring + k * SF, lane, sb + int64_t(l + P) * 32, Bl + int64_t(l + P + 1) * W * 32,
                                   hv[k], hd[k]);
             cv[k] = hv[k];
             cd[k] = hd[k];
@@ -280,7 +295,7 @@ __device__ __forceinline__ void backward_tile(const KArgs& a, const TileInfo& ti
     for (int k = 0; k < P; ++k) {
         const int l = L - 1 - k;
         load_head(a, sb + int64_t(l) * 32, l >= 0, cv[k], cd[k]);
-        stage_issue<W, NODES>(a, ring + k * SF, lane, sb + int64_t(l) * 32, Fl + int64_t(l) * W * 32, cv[k], cd[k]);
+        stage_issue<W, NODES, MODE == 0>(a, ring + k * SF, lane, sb + int64_t(l) * 32, Fl + int64_t(l) * W * 32, cv[k], cd[k]);
         load_head(a, sb + int64_t(l - P) * 32, l - P >= 0, hv[k], hd[k]);
     }
     for (int l0 = L - 1; l0 >= 0; l0 -= P) {
@@ -297,7 +312,7 @@ __device__ __forceinline__ void backward_tile(const KArgs& a, const TileInfo& ti
                 Staged<W> c;
                 stage_read<W, NODES>(ring + k * SF, lane, d, c);
                 const int64_t si = sb + int64_t(l) * 32;
-                const df p = pend_staged(c, d.deg);
+                const df p = MODE == 0 ? df{c.acc.x, c.acc.y} : pend_staged(c, d.deg);
                 df Lm{c.lam, c.lo};
                 const uint8_t st = kRound ? __ldg(a.state + v) : kFree;
                 const bool al0 = st != kFix1, al1 = st != kFix0;
@@ -330,7 +345,8 @@ __device__ __forceinline__ void backward_tile(const KArgs& a, const TileInfo& ti
                             a.lam_lo[si] = Lm.lo;
                             lm = Lm.hi;
                         }
-                        a.acc_out[size_t(v) * kAccStride + d.rank] = removed;
+                        if (MODE == 0) a.slot_mass[si] = removed;  // coalesced; the reduction forms the means
+                        else a.acc_out[size_t(v) * kAccStride + d.rank] = removed;
                     } else {
                         lm = df_add(Lm, p).hi;
                         const float M = (m1 + lm) - m0;
@@ -350,7 +366,7 @@ __device__ __forceinline__ void backward_tile(const KArgs& a, const TileInfo& ti
                     if (kStoreB && s < d.w) Br[s * 32] = bn[s];
                 }
             }
-            stage_issue<W, NODES>(a, ring + k * SF, lane, sb + int64_t(l - P) * 32, Fl + int64_t(l - P) * W * 32, hv[k],
+            stage_issue<W, NODES, MODE == 0>(a, ring + k * SF, lane, sb + int64_t(l - P) * 32, Fl + int64_t(l - P) * W * 32, hv[k],
                                   hd[k]);
             cv[k] = hv[k];
             cd[k] = hd[k];

@@ -41,6 +41,8 @@ struct KArgs {
     float* F;
     float* B;
     const float* acc_in;             // mass removed by the previous half-pass (kAccStride per var)
+    const float2* pend_tab;          // MMA half-passes: each variable's deferred mean (double-float)
+    float* slot_mass;                // MMA half-passes: the mass each slot removes (tile layout)
     float* acc_out;                  // mass removed by this half-pass
     const uint8_t* state;            // per variable, rounding only
     float omega;
@@ -104,6 +106,17 @@ cudaError_t launch_layout(const int64_t* seg_canon, const int32_t* seg_len, cons
                           const float* clam, const float* clam_lo, uint32_t* var, uint32_t* desc, float* lam,
                           float* lam_lo, int64_t* canon_pos, cudaStream_t s);
 cudaError_t launch_instance_of(const int64_t* base, int32_t ni, int64_t n, int32_t* out, cudaStream_t s);
+
+// Averaging of the MMA half-passes (store.cu). Every slot writes the mass it removes to
+// slot_mass (tile layout); vpos[v * 8 + r] = the tile slot of variable v's rank-r slot.
+// launch_reduce: pend[v] = (sum over ranks, in rank order, of v's slot masses) / deg[v] in
+// double-float, the same operations as the deferred mean of an averaging sector.
+// launch_scatter_back: acc[v * 8 + r] = v's rank-r slot mass (the sector form).
+cudaError_t launch_vpos(const uint32_t* var, const uint32_t* desc, int64_t nslots, int32_t* vpos, cudaStream_t s);
+cudaError_t launch_reduce(const int32_t* vpos, const float* slot_mass, const uint8_t* deg, int64_t nint, float2* pend,
+                          cudaStream_t s);
+cudaError_t launch_scatter_back(const int32_t* vpos, const float* slot_mass, const uint8_t* deg, int64_t nint,
+                                float* acc, cudaStream_t s);
 
 // Quasi-Newton vector kernels (qn.cu); n = slots in tile layout.
 cudaError_t launch_qn_sign(const float* mm, const uint32_t* var, int64_t n, float* g, cudaStream_t s);
