@@ -53,19 +53,28 @@ __global__ void k_vpos(const uint32_t* __restrict__ var, const uint32_t* __restr
 }
 
 // One thread per variable: its deg slot masses in rank order, summed and divided in
-// double-float exactly as the half-pass kernels form a deferred mean from a sector.
+// double-float exactly as the half-pass kernels form a deferred mean from a sector. The
+// degree and the 32-byte position sector load together, and every mass gather issues before
+// the sum, so a variable waits on two memory round trips, not 2 + deg.
 __global__ void k_reduce(const int32_t* __restrict__ vpos, const float* __restrict__ m, const uint8_t* __restrict__ deg,
                          int64_t n, float2* __restrict__ pend) {
     using namespace dev;
     for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
+        const int4* qp = reinterpret_cast<const int4*>(vpos + size_t(v) * kAccStride);
+        const int4 q0 = qp[0], q1 = qp[1];
         const int dg = deg[v];
-        const int32_t* q = vpos + size_t(v) * kAccStride;
         if (dg < 2) {  // every internal variable has 2 or more slots
             pend[v] = make_float2(0.0f, 0.0f);
             continue;
         }
-        df s = df_add_f(df{m[q[0]], 0.0f}, m[q[1]]);
-        for (int r = 2; r < dg; ++r) s = df_add_f(s, m[q[r]]);
+        const int q[kAccStride] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+        float x[kAccStride];
+#pragma unroll
+        for (int r = 0; r < kAccStride; ++r) x[r] = r < dg ? m[q[r]] : 0.0f;
+        df s = df_add_f(df{x[0], 0.0f}, x[1]);
+#pragma unroll
+        for (int r = 2; r < kAccStride; ++r)
+            if (r < dg) s = df_add_f(s, x[r]);
         const df p = df_div_i(s, dg);
         pend[v] = make_float2(p.hi, p.lo);
     }
