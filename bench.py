@@ -43,22 +43,26 @@ def _peaks():
 
 
 def _traffic(workload: str, split_chunk: int):
-    """DRAM bytes per half-pass launch from the committed ncu summary of this workload, or
-    None when the half-pass kernels changed since the counters were taken (source hash)."""
+    """DRAM bytes per half-pass (the MMA kernel and its mean reduction) from the committed ncu
+    summary of this workload, or None when either kernel's source changed since the counters
+    were taken (sha256 of kernels.cu followed by store.cu)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "halfpass_icosphere4-5120T-top16.md")
-    src = os.path.join(ROOT, "paper_2310_08230_gb300", "csrc", "kernels.cu")
+    csrc = os.path.join(ROOT, "paper_2310_08230_gb300", "csrc")
     if workload != "icosphere4-5120T-top16" or split_chunk != 32 or not os.path.exists(path):
         return None
-    with open(src, "rb") as f:
-        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in ("kernels.cu", "store.cu"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    h = h.hexdigest()[:16]
     fields = {}
     with open(path) as f:
         for ln in f:
-            if ":" in ln and ln.split(":")[0] in ("kernels_cu_sha256_16", "traffic_bytes_per_launch"):
+            if ":" in ln and ln.split(":")[0] in ("sources_sha256_16", "traffic_bytes_per_launch"):
                 k, v = ln.split(":", 1)
                 fields[k] = v.strip()
-    if fields.get("kernels_cu_sha256_16") != h:
+    if fields.get("sources_sha256_16") != h:
         return None
     return int(fields["traffic_bytes_per_launch"])
 
@@ -285,7 +289,7 @@ def gpu_arm(args):
                 "h2d_bytes_per_step": int(FX_h.nbytes + FY_h.nbytes), "d2h_bytes_per_step": int(st["nvars"]) + 8},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": _traffic(inst.name, args.split_chunk), "kernel": "half-pass (k_forward/k_backward MMA, all width classes)",
+                     "traffic": _traffic(inst.name, args.split_chunk), "kernel": "half-pass (k_forward/k_backward MMA, all width classes, + k_reduce)",
                      "alg_bytes_per_launch": alg_bytes, "launch_ms": half_pass_ms, "peak_kind": kind,
                      "launch_timing": "CUDA events on the solver stream around each step's dual blocks after "
                                       "the first (CUDA-graph replays of the half-pass kernels); the first block "
