@@ -93,9 +93,8 @@ typedef struct {
                                  needs the meshes' V) and d the pair distances
                                  (disco_pair_distances) */
     int32_t tile_order;       /* [0] order of the warp tiles in the device store (results are the
-                                 same, up to the order of the bound's FP64 tile sums): 0 = by
-                                 size (2 when both averaging tables exceed 64 MB, else 1);
-                                 1 = width class, then length, over each instance; 2 = blocks
+                                 same, up to the order of the bound's FP64 tile sums): 0 = the
+                                 default, which is 1; 1 = width class, then length, over each instance; 2 = blocks
                                  of 4096 segments in mesh-region order (table locality), each
                                  by width class and length */
 } disco_opts;

@@ -271,10 +271,8 @@ constexpr bool classes_have_kernels() {
 }
 static_assert(classes_have_kernels(), "every width class needs a kernel instantiation");
 
-// Tile order for table locality (see upload): segments per block, and the size of both
-// averaging tables above which it applies (half of the 126 MB L2).
+// Tile order for table locality (opts.tile_order == 2, see upload): segments per block.
 constexpr int64_t kLocalityBlock = 4096;
-constexpr int64_t kLocalityTableBytes = int64_t(64) << 20;
 
 int width_class(int w) {
     for (int c : kWidthClasses)
@@ -313,19 +311,15 @@ int upload(disco_handle* h) {
     std::vector<TileSeg> order;
     int maxL = 1;
     for (int64_t i = 0; i < ni; ++i) maxL = std::max(maxL, h->plans[i].max_layers);
-    // Averaging tables far larger than L2 (big batches): every slot's sector gather and
-    // scatter would miss if the warps running at one time held segments from all over the
-    // instance. Then segments are ordered by the region of their row (closedness rows by the
+    // Locality order (opts.tile_order == 2): segments are ordered by the region of their row (closedness rows by the
     // X vertex of their bucket, X projection rows beside their triangle's smallest vertex, Y
     // projection rows last), cut into blocks of kLocalityBlock, each block sorted by width
     // class and length, and tiles follow the blocks: the warps running together then hold
-    // most of the slots of the variables they touch. Otherwise (tables L2-resident) segments
-    // are sorted by width class and length over the whole instance. Instances are ordered in
+    // most of the slots of the variables they touch. It served half-passes that gathered and
+    // scattered whole per-variable sectors; with 8-byte per-variable means they run faster in
+    // the default order, by width class and length over the whole instance. Instances are ordered in
     // parallel, then concatenated in instance order.
-    int64_t nint_all = 0;
-    for (int64_t i = 0; i < ni; ++i) nint_all += h->plans[i].n_free + h->plans[i].n_aux;
-    const bool locality = h->opts.tile_order == 2 ||
-                          (h->opts.tile_order == 0 && 2 * nint_all * kAccStride * int64_t(sizeof(float)) > kLocalityTableBytes);
+    const bool locality = h->opts.tile_order == 2;
     auto launch_group = [](int W) { return W <= kFusedMaxW ? 0 : W <= 8 ? 1 : W <= 16 ? 2 : 3; };
     struct InstTiles {
         std::vector<int64_t> seg;  // the instance's segments in tile order
