@@ -42,7 +42,12 @@ enum {
     DISCO_ERR_TIMEOUT = -6,       /* a bounded device or host loop hit its limit */
     DISCO_ERR_CUDA = -7,          /* a CUDA runtime call failed (message in disco_last_error) */
     DISCO_ERR_OOM = -8,           /* device or host allocation failed */
-    DISCO_ERR_NOT_READY = -9      /* call order violated (e.g. primal before any dual pass) */
+    DISCO_ERR_NOT_READY = -9,     /* call order violated (e.g. primal before any dual pass) */
+    DISCO_ERR_RANGE = -10,        /* a mass removed by a dual update left the range of the
+                                     fixed-point averaging sums (see disco_dual): costs far too
+                                     large for normalize_costs = 0, or a diverging dual */
+    DISCO_ERR_INTERNAL = -11      /* bounds-checking build only: a kernel index fell outside its
+                                     array; the access was skipped and the results are void */
 };
 
 /* A triangle mesh: nv vertices (V: nv*3 float, may be NULL: positions are not used by the

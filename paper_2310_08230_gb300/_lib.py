@@ -15,7 +15,7 @@ DISCO_OK = 0
 ERRORS = {
     -1: "DISCO_ERR_INVALID_ARG", -2: "DISCO_ERR_NONMANIFOLD", -3: "DISCO_ERR_GENUS_MISMATCH",
     -4: "DISCO_ERR_INFEASIBLE", -5: "DISCO_ERR_PRIMAL_FAILED", -6: "DISCO_ERR_TIMEOUT", -7: "DISCO_ERR_CUDA",
-    -8: "DISCO_ERR_OOM", -9: "DISCO_ERR_NOT_READY",
+    -8: "DISCO_ERR_OOM", -9: "DISCO_ERR_NOT_READY", -10: "DISCO_ERR_RANGE", -11: "DISCO_ERR_INTERNAL",
 }
 globals().update({v: k for k, v in ERRORS.items()})
 

@@ -3,6 +3,11 @@
 Translation units are compiled in parallel and linked into one shared library
 with a plain C ABI (``include/disco.h``). Rebuilds only when a source is newer
 than the library.
+
+With the environment variable ``DISCO_BOUNDS_CHECK=1`` the library is built
+with device-side index checks in the half-pass kernels (an index outside its
+array sets a status bit and the access is skipped; the host reports
+DISCO_ERR_INTERNAL) into ``_build_bc/``, and the binding loads that one.
 """
 from __future__ import annotations
 
@@ -11,7 +16,8 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-OUT_DIR = os.path.join(HERE, "_build")
+BOUNDS_CHECK = os.environ.get("DISCO_BOUNDS_CHECK", "0") not in ("", "0")
+OUT_DIR = os.path.join(HERE, "_build_bc" if BOUNDS_CHECK else "_build")
 LIB = os.path.join(OUT_DIR, "libdisco.so")
 SOURCES = ["disco.cu", "kernels.cu", "adjoint.cu", "qn.cu", "store.cu", "host_build.cpp", "noalloc.cu"]
 HEADERS = ["plan.h", "kernels.h"]
@@ -41,6 +47,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3", "--expt-relaxed-constexpr"] + ARCH
+    if BOUNDS_CHECK:
+        common.append("-DDISCO_BOUNDS_CHECK")
     procs, objs = [], []
     for s in SOURCES:
         obj = os.path.join(OUT_DIR, os.path.splitext(s)[0] + ".o")

@@ -63,20 +63,6 @@ __device__ __forceinline__ int lane_length(const AdjArgs& a, const TileInfo& ti,
     return lo;
 }
 
-// Deferred mean from a variable's averaging sector (ranks 0-3 in a, 4-7 in b); the same
-// operations in the same order as the half-pass kernels, so every decision is reproduced.
-__device__ __forceinline__ df pend_from(const float4& a, const float4& b, int deg) {
-    df s = df_add_f(df{a.x, 0.0f}, a.y);
-    if (deg > 2) s = df_add_f(s, a.z);
-    if (deg > 3) s = df_add_f(s, a.w);
-    if (deg > 4) {
-        s = df_add_f(s, b.x);
-        if (deg > 5) s = df_add_f(s, b.y);
-        if (deg > 6) s = df_add_f(s, b.z);
-    }
-    return df_div_i(s, deg);
-}
-
 // Adjoint of the removed mass: the next mean's adjoint (sum over ranks) divided by |J_v|.
 __device__ __forceinline__ float removed_bar(const float4& a, const float4& b, int deg) {
     const float q[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
@@ -175,8 +161,8 @@ __device__ __forceinline__ void adj_forward_layer(const AdjArgs& a, const LayerI
         }
         c0 = s0 + d.d0;
         const float M = (m1 + Lm.hi) - m0;
-        const float removed = a.omega * M;
-        lm = df_add_f(Lm, -removed).hi;
+        long long q;
+        lm = df_add_f(Lm, -fx_round(a.omega * M, a.fx, q)).hi;  // the mass as the pass removed it
     } else {
         lm = df_add(Lm, p).hi;
     }
@@ -270,8 +256,8 @@ __device__ __forceinline__ void adj_backward_layer(const AdjArgs& a, const Layer
         c0 = s0 + d.d0;
         Lm = df_add(Lm, p);
         const float M = (m1 + Lm.hi) - m0;
-        const float removed = a.omega * M;
-        lm = df_add_f(Lm, -removed).hi;
+        long long q;
+        lm = df_add_f(Lm, -fx_round(a.omega * M, a.fx, q)).hi;  // the mass as the pass removed it
     } else {
         lm = df_add(Lm, p).hi;
     }
@@ -377,14 +363,12 @@ __global__ void __launch_bounds__(kAdjWarps * 32, WG == 0 ? 4 : (WG == 8 ? 3 : 1
     }
 }
 
-// pend[v]: the deferred mean of variable v from its averaging sector, as the half-pass
-// kernels compute it (same operations, same order).
-__global__ void k_pend_table(const float* __restrict__ acc, const uint8_t* __restrict__ deg, int64_t n,
+// pend[v]: the deferred mean of variable v from its averaging sum, exactly as the passes add it.
+__global__ void k_pend_table(const long long* __restrict__ msum, const uint8_t* __restrict__ deg, int64_t n, float inv,
                              float2* __restrict__ out) {
     for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
         const int dg = deg[v];
-        const float4* p = reinterpret_cast<const float4*>(acc + size_t(v) * kAccStride);
-        const df m = dg > 0 ? pend_from(p[0], dg > 4 ? p[1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f), dg) : df{0.0f, 0.0f};
+        const df m = dg > 0 ? fx_mean(msum[v], dg, inv) : df{0.0f, 0.0f};
         out[v] = make_float2(m.hi, m.lo);
     }
 }
@@ -449,9 +433,10 @@ cudaError_t launch_adjoint(Adj kind, int group, const AdjArgs& a, cudaStream_t s
     return cudaGetLastError();
 }
 
-cudaError_t launch_pend_table(const float* acc, const uint8_t* deg, int64_t n, float2* out, cudaStream_t s) {
+cudaError_t launch_pend_table(const long long* msum, const uint8_t* deg, int64_t n, float inv, float2* out,
+                              cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_pend_table<<<grid_of(n, 256), 256, 0, s>>>(acc, deg, n, out);
+    k_pend_table<<<grid_of(n, 256), 256, 0, s>>>(msum, deg, n, inv, out);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }

@@ -89,21 +89,31 @@ __device__ __forceinline__ df df_div_i(df a, int n) {
     return fast2sum(q, r * rcp);
 }
 
-// Deferred mean of variable v: sum of its deg removed masses (rank order) / deg, in df.
-__device__ __forceinline__ df pend_of(const float* __restrict__ acc, uint32_t v, int deg) {
-    const float4* p = reinterpret_cast<const float4*>(acc + size_t(v) * kAccStride);
-    const float4 a = __ldg(p);
-    df s = df_add_f(df{a.x, 0.0f}, a.y);
-    if (deg > 2) s = df_add_f(s, a.z);
-    if (deg > 3) s = df_add_f(s, a.w);
-    if (deg > 4) {
-        const float4 b = __ldg(p + 1);
-        s = df_add_f(s, b.x);
-        if (deg > 5) s = df_add_f(s, b.y);
-        if (deg > 6) s = df_add_f(s, b.z);
-    }
-    return df_div_i(s, deg);
+// Deferred means from fixed-point sums (the averaging step of Alg. 1 "MMA"). Every update
+// pass adds the mass each slot removes, on the grid 2^-F, into one signed 64-bit integer per
+// variable: integer addition is exact and order-free, so the sum, and everything built on it,
+// is the same for every schedule of the lanes and needs no second pass over the slots. The
+// slot subtracts exactly the rounded mass from its lambda, so sum_j lambda^j_i + |J_i| pend_i
+// = c_i (Eq. D) holds as exactly as before. F is chosen per handle from the largest cost;
+// lim = 2^(59 - F) bounds one mass, so sums of up to 7 stay inside the 64-bit range.
+//
+// m on the grid: q = round(m 2^F) and the return value q 2^-F, both exact (m 2^F has 24
+// significant bits, so rounding it to an integer leaves at most 24, which FP32 holds).
+__device__ __forceinline__ float fx_round(float m, const FxScale& fx, long long& q) {
+    const float t = rintf(m * fx.scale);
+    q = __float2ll_rn(t);
+    return t * fx.inv;
 }
+// A sum S (units of 2^-F) as double-float: hi = S rounded to FP32, lo = the exact integer
+// remainder S - hi rounded to FP32 (|lo| <= ulp(hi) / 2, so the pair is normalised); the
+// scaling by 2^-F is exact. Relative error about 2^-48.
+__device__ __forceinline__ df fx_to_df(long long S, float inv) {
+    const float hi = __ll2float_rn(S);
+    const float lo = __ll2float_rn(S - __float2ll_rn(hi));
+    return df{hi * inv, lo * inv};
+}
+// The deferred mean of a variable: its sum / deg, in double-float.
+__device__ __forceinline__ df fx_mean(long long S, int deg, float inv) { return df_div_i(fx_to_df(S, inv), deg); }
 
 __device__ __forceinline__ uint64_t shl(uint64_t x, int k) { return k >= 0 ? (x << k) : (x >> (-k)); }
 __device__ __forceinline__ uint64_t low_mask(int n) { return n >= 64 ? ~0ull : ((1ull << n) - 1ull); }

@@ -83,11 +83,15 @@ struct disco_handle {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    // averaging of the MMA half-passes (kernels.cu): slot masses, the positions of each
-    // variable's slots, and the per-variable deferred means they reduce to
-    int32_t* vpos = nullptr;
-    float* slot_mass = nullptr;
-    float2* pend_tab = nullptr;
+    // averaging state (kernels.h, KArgs): three rotating buffers of one fixed-point sum per
+    // variable. msum[phase] is the buffer the next update pass writes (all zero between
+    // passes), msum[(phase + 2) % 3] holds the current state (the sums of the last update
+    // pass: each variable's deferred mean is its sum / deg).
+    long long* msum[3] = {nullptr, nullptr, nullptr};
+    int phase = 0;
+    FxScale fx{};
+    uint32_t* status = nullptr;    // device status word (kStatus* bits)
+    uint32_t* h_status = nullptr;  // pinned copy, read at synchronisation points
     disco_opts opts{};
     std::vector<Plan> plans;              // one per instance
     std::vector<int64_t> var_base;        // internal variable offset per instance (n + 1)
@@ -110,8 +114,6 @@ struct disco_handle {
     float* lam0_lo = nullptr;
     float* F = nullptr;
     float* B = nullptr;
-    float* acc[2] = {nullptr, nullptr};
-    int cur = 0;
     double* tile_sum = nullptr;
     double* scalar = nullptr;      // per instance: lower bound
     double* consts = nullptr;      // per instance: presolve constant
@@ -140,19 +142,20 @@ struct disco_handle {
     std::vector<void*> allocations;
     int geometry = 2;              // warps per block of the fused MMA half-passes
     bool tuned = false;            // autotuner done (or off)
-    cudaGraphExec_t iter_graph = nullptr;  // opts.graph_iters iterations, replayed as a block
-    int graph_cur = 0;             // averaging-buffer parity the graph was captured at
-    int64_t graph_launches = 0;    // kernels in one replay
+    // opts.graph_iters iterations, replayed as a block; one graph per averaging phase at which
+    // it starts (the kernel arguments name the three sum buffers in rotation)
+    cudaGraphExec_t iter_graph[3] = {nullptr, nullptr, nullptr};
+    int64_t graph_launches[3] = {0, 0, 0};  // kernels in one replay
     bool graph_failed = false;     // the stream could not be captured: launch plainly
     // ---- differentiation (disco_record / disco_grad)
     struct Snap {  // the dual state at an iteration boundary, or the inputs of one half-pass
         float* lam = nullptr;
         float* lam_lo = nullptr;
-        float* acc = nullptr;      // checkpoint: averaging sectors the next pass reads
+        long long* msum = nullptr; // checkpoint: the averaging sums the next pass reads
         float2* pend = nullptr;    // tape: the deferred means the pass added (per variable)
         float* nodes = nullptr;    // checkpoint: node costs of the other direction; tape: the
                                    // node costs the pass stored (the next pass's input)
-        int cur = 0;               // which averaging buffer they belong to
+        int phase = 0;             // checkpoint: the averaging phase it was taken at
     };
     std::vector<Snap> checkpoints, tape;
     Snap final_state;
@@ -195,6 +198,8 @@ struct disco_handle {
         return DISCO_OK;
     }
 
+    long long* msum_rd() const { return msum[(phase + 2) % 3]; }
+
     KArgs args(const WidthClass& c, bool backward = false) {
         KArgs a{};
         a.tiles = backward && tiles_bwd ? tiles_bwd : tiles;
@@ -206,10 +211,14 @@ struct disco_handle {
         a.lam_lo = lam_lo;
         a.F = F;
         a.B = B;
-        a.acc_in = acc[cur];
-        a.pend_tab = pend_tab;
-        a.slot_mass = slot_mass;
-        a.acc_out = acc[cur ^ 1];
+        a.msum_rd = msum[(phase + 2) % 3];
+        a.msum_wr = msum[phase];
+        a.msum_zero = msum[(phase + 1) % 3];
+        a.fx = fx;
+        a.status = status;
+        a.nslots = nslots_tile;
+        a.nnodes = nnodes_tile;
+        a.nvars = nint;
         a.state = state;
         a.omega = opts.omega;
         a.mm_slot = mm_slot;
@@ -220,21 +229,47 @@ struct disco_handle {
         return a;
     }
 
-    // One pass over every width class (a half-pass flips the averaging buffers).
+    // One pass over every width class (an update pass moves the averaging phase on).
     int pass(Pass p) {
         const bool bwd = p == Pass::BwdMMA || p == Pass::BwdMMARound || p == Pass::BwdMM || p == Pass::BwdReset;
         for (const WidthClass& c : classes) CK(launch_pass(p, c.W, args(c, bwd), stream, geometry));
-        if (p == Pass::FwdMMA || p == Pass::BwdMMA) CK(launch_reduce(vpos, slot_mass, deg, nint, pend_tab, stream));
-        if (p == Pass::FwdMMA || p == Pass::BwdMMA || p == Pass::FwdMMARound || p == Pass::BwdMMARound) cur ^= 1;
+        if (p == Pass::FwdMMA || p == Pass::BwdMMA || p == Pass::FwdMMARound || p == Pass::BwdMMARound)
+            phase = (phase + 1) % 3;
         return DISCO_OK;
     }
 
+    // The averaging state set to "no deferred mass": every sum zero.
+    int clear_sums() {
+        for (long long* m : msum) CK(cudaMemsetAsync(m, 0, size_t(nint) * sizeof(long long), stream));
+        return DISCO_OK;
+    }
+
+    // Queues a copy of the device status word to h_status on the handle's stream;
+    // check_status() reads it once the stream has been synchronised and turns a set bit into
+    // an error. The word is then cleared, so that the handle stays usable.
+    int fetch_status() {
+        CK(cudaMemcpyAsync(h_status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+        return DISCO_OK;
+    }
+    int check_status() {
+        const uint32_t st = *h_status;
+        if (!st) return DISCO_OK;
+        *h_status = 0;
+        CK(cudaMemsetAsync(status, 0, sizeof(uint32_t), stream));
+        if (st & kStatusBounds)
+            return fail(DISCO_ERR_INTERNAL, "bounds check: a kernel index fell outside its array (access skipped)");
+        return fail(DISCO_ERR_RANGE, "a removed mass left the fixed-point range of the averaging sums (costs too "
+                                     "large for normalize_costs = 0, or the dual diverged)");
+    }
+
     ~disco_handle() {
-        if (iter_graph) cudaGraphExecDestroy(iter_graph);
+        for (cudaGraphExec_t g : iter_graph)
+            if (g) cudaGraphExecDestroy(g);
         for (void* p : allocations) cudaFreeAsync(p, stream);
         if (stream) cudaStreamSynchronize(stream);
         if (h_counters) cudaFreeHost(h_counters);
         if (h_scalar) cudaFreeHost(h_scalar);
+        if (h_status) cudaFreeHost(h_status);
         if (qn_hpart) cudaFreeHost(qn_hpart);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
@@ -296,6 +331,27 @@ int upload(disco_handle* h) {
     }
     h->nint = h->var_base[ni];
     if (h->nint >= (int64_t(1) << 32) - 1) return fail(DISCO_ERR_INVALID_ARG, "build: too many variables");
+    // Every internal variable lies in 2 to 7 BDD segments: the descriptor holds the degree in
+    // 3 bits, and a variable in one segment would have been fixed by the presolve (a row with
+    // one free variable forces it). The deferred mean divides by it.
+    for (int64_t i = 0; i < ni; ++i)
+        for (uint8_t dg : h->plans[i].deg)
+            if (dg < 2 || dg > 7)
+                return fail(DISCO_ERR_INVALID_ARG, "build: an internal variable lies in " + std::to_string(int(dg)) +
+                                                       " segments (2 to 7 expected)");
+    // Fixed-point grid of the averaging sums: 2^-F with 2^(40 - F) >= the largest |cost| (at
+    // least 2^-20), so one mass may grow to 2^19 times the largest cost before the kernels flag
+    // it, and the grid is about 1e-12 of the largest cost.
+    {
+        double cmax = 0.0;
+        for (int64_t i = 0; i < ni; ++i)
+            for (double c : h->plans[i].cost) cmax = std::max(cmax, std::fabs(c));
+        int e = 0;
+        std::frexp(std::max(cmax, std::ldexp(1.0, -20)), &e);  // cmax < 2^e
+        e = std::min(e, 30);
+        const int F = 40 - e;
+        h->fx = FxScale{std::ldexp(1.0f, F), std::ldexp(1.0f, -F), std::ldexp(1.0f, 59 - F)};
+    }
     // ---- tiles: per instance, segments grouped by width class, longest first; a tile never
     // mixes instances (its bound sum belongs to one instance). Counting sorts by (class,
     // length), then the tiles by (launch group, length): both stable.
@@ -536,9 +592,9 @@ int upload(disco_handle* h) {
     tr.mark("tile layout");
     int rc;
     if ((rc = h->alloc(&h->tiles, h->ntiles))) return rc;
-    if ((rc = h->alloc(&h->vpos, h->nint * kAccStride)) || (rc = h->alloc(&h->slot_mass, slot_base)) ||
-        (rc = h->alloc(&h->pend_tab, h->nint)))
-        return rc;
+    for (long long*& m : h->msum)
+        if ((rc = h->alloc(&m, h->nint))) return rc;
+    if ((rc = h->alloc(&h->status, 1))) return rc;
     if (locality && (rc = h->alloc(&h->tiles_bwd, h->ntiles))) return rc;
     if ((rc = h->alloc(&h->var, slot_base))) return rc;
     if ((rc = h->alloc(&h->desc, slot_base))) return rc;
@@ -548,8 +604,6 @@ int upload(disco_handle* h) {
     if ((rc = h->alloc(&h->lam0_lo, slot_base))) return rc;
     if ((rc = h->alloc(&h->F, node_base))) return rc;
     if ((rc = h->alloc(&h->B, node_base))) return rc;
-    if ((rc = h->alloc(&h->acc[0], h->nint * kAccStride))) return rc;
-    if ((rc = h->alloc(&h->acc[1], h->nint * kAccStride))) return rc;
     if ((rc = h->alloc(&h->tile_sum, h->ntiles))) return rc;
     if ((rc = h->alloc(&h->scalar, ni))) return rc;
     if ((rc = h->alloc(&h->consts, ni))) return rc;
@@ -568,6 +622,8 @@ int upload(disco_handle* h) {
     if ((rc = h->alloc(&h->var_inst, h->nint))) return rc;
     CK(cudaMallocHost(&h->h_counters, size_t(4 * std::max<int64_t>(ni, 1)) * sizeof(int)));
     CK(cudaMallocHost(&h->h_scalar, size_t(std::max<int64_t>(ni, 1)) * sizeof(double)));
+    CK(cudaMallocHost(&h->h_status, sizeof(uint32_t)));
+    *h->h_status = 0;
     tr.mark("allocations");
     cudaStream_t s = h->stream;
     // temporaries: canonical slot arrays, segment records, instance variable bases
@@ -622,8 +678,6 @@ int upload(disco_handle* h) {
     CK(launch_layout(d_seg_canon, d_seg_len, d_seg_pos, d_seg_vb, nseg_all, cvar, cdesc, clam, clam_lo, h->var, h->desc,
                      h->lam, h->lam_lo, h->canon_pos, s));
     CK(launch_instance_of(d_var_base, int32_t(ni), h->nint, h->var_inst, s));
-    CK(cudaMemsetAsync(h->vpos, 0, size_t(h->nint) * kAccStride * 4, s));  // unused ranks stay in bounds
-    CK(launch_vpos(h->var, h->desc, slot_base, h->vpos, s));
     CK(cudaMemcpyAsync(h->lam0, h->lam, size_t(slot_base) * 4, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(h->lam0_lo, h->lam_lo, size_t(slot_base) * 4, cudaMemcpyDeviceToDevice, s));
     if ((rc = copy_in(h->consts, consts.data(), consts.size() * 8, s))) return rc;
@@ -631,8 +685,9 @@ int upload(disco_handle* h) {
     if ((rc = copy_in(h->d_inst_tiles, inst_tiles.data(), inst_tiles.size() * 4, s))) return rc;
     CK(cudaMemsetAsync(h->F, 0, size_t(node_base) * 4, s));
     CK(cudaMemsetAsync(h->B, 0, size_t(node_base) * 4, s));
-    CK(cudaMemsetAsync(h->acc[0], 0, size_t(h->nint) * kAccStride * 4, s));
-    CK(cudaMemsetAsync(h->acc[1], 0, size_t(h->nint) * kAccStride * 4, s));
+    if ((rc = h->clear_sums())) return rc;
+    h->phase = 0;
+    CK(cudaMemsetAsync(h->status, 0, sizeof(uint32_t), s));
     CK(cudaMemsetAsync(h->state, 0, size_t(h->nint), s));
     CK(cudaStreamSynchronize(s));
     tr.mark("copies");
@@ -692,9 +747,11 @@ int autotune(disco_handle* h, int* used) {
     return rc;
 }
 
-// Captures opts.graph_iters iterations into one executable graph (kernels only).
+// Captures opts.graph_iters iterations, starting at the current averaging phase, into one
+// executable graph (kernels only).
 int capture_iterations(disco_handle* h) {
     const int G = h->opts.graph_iters;
+    const int ph = h->phase;
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
@@ -702,7 +759,6 @@ int capture_iterations(disco_handle* h) {
         return DISCO_OK;
     }
     const int64_t before = g_launches.load();
-    const int cur0 = h->cur;
     int rc = DISCO_OK;
     for (int t = 0; t < G && !rc; ++t) {
         rc = h->pass(Pass::FwdMMA);
@@ -711,58 +767,46 @@ int capture_iterations(disco_handle* h) {
     const cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
     const int64_t captured = g_launches.load() - before;
     g_launches.fetch_sub(captured);  // recorded, not run
-    h->cur = cur0;
+    h->phase = ph;
     if (rc || e != cudaSuccess || !graph) {
         if (graph) cudaGraphDestroy(graph);
         cudaGetLastError();
         h->graph_failed = true;
         return DISCO_OK;
     }
-    const cudaError_t ei = cudaGraphInstantiate(&h->iter_graph, graph, 0);
+    const cudaError_t ei = cudaGraphInstantiate(&h->iter_graph[ph], graph, 0);
     cudaGraphDestroy(graph);
     if (ei != cudaSuccess) {
         cudaGetLastError();
-        h->iter_graph = nullptr;
+        h->iter_graph[ph] = nullptr;
         h->graph_failed = true;
         return DISCO_OK;
     }
-    h->graph_cur = cur0;
-    h->graph_launches = captured;
+    h->graph_launches[ph] = captured;
     return DISCO_OK;
 }
 
-int run_iterations_tab(disco_handle* h, int iters);
-
-// Dual iterations. Outside this call the averaging sectors acc[cur] hold the state; inside,
-// the MMA half-passes keep it as slot masses and per-variable means: the means are formed
-// from the sectors on entry, and the last pass's masses go back into sector form on exit.
+// Dual iterations: forward and backward MMA half-passes. The averaging state stays in the
+// rotating sum buffers between calls, so nothing is converted on entry or exit.
 int run_iterations(disco_handle* h, int iters) {
     int rc;
     if (!h->has_b && (rc = reset_b(h))) return rc;
-    if (iters <= 0) return DISCO_OK;  // no pass writes slot masses: the sectors stay as they are
-    CK(launch_pend_table(h->acc[h->cur], h->deg, h->nint, h->pend_tab, h->stream));
-    if ((rc = run_iterations_tab(h, iters))) return rc;
-    CK(launch_scatter_back(h->vpos, h->slot_mass, h->deg, h->nint, h->acc[h->cur], h->stream));
-    return DISCO_OK;
-}
-
-int run_iterations_tab(disco_handle* h, int iters) {
-    int rc;
     int t = 0;
-    if (!h->tuned && h->opts.autotune && iters >= kTrials * 3) {
+    if (iters > 0 && !h->tuned && h->opts.autotune && iters >= kTrials * 3) {
         int used = 0;
         if ((rc = autotune(h, &used))) return rc;
         t += used;
     }
     const int G = h->opts.graph_iters;
-    if (G > 0 && !h->graph_failed && iters - t >= G) {
-        if (!h->iter_graph && (h->tuned || !h->opts.autotune) && (rc = capture_iterations(h))) return rc;
-        if (h->iter_graph && h->cur == h->graph_cur) {
-            for (; iters - t >= G; t += G) {
-                CK(cudaGraphLaunch(h->iter_graph, h->stream));
-                g_launches.fetch_add(h->graph_launches, std::memory_order_relaxed);
-                h->iterations += G;
-            }
+    if (G > 0 && (h->tuned || !h->opts.autotune)) {
+        while (!h->graph_failed && iters - t >= G) {
+            if (!h->iter_graph[h->phase] && (rc = capture_iterations(h))) return rc;
+            if (!h->iter_graph[h->phase]) break;
+            CK(cudaGraphLaunch(h->iter_graph[h->phase], h->stream));
+            g_launches.fetch_add(h->graph_launches[h->phase], std::memory_order_relaxed);
+            h->phase = (h->phase + 2 * G) % 3;
+            h->iterations += G;
+            t += G;
         }
     }
     for (; t < iters; ++t)
@@ -777,8 +821,9 @@ int lower_bounds(disco_handle* h) {
     CK(launch_sum_instances(h->tile_sum, h->d_inst_tile_ptr, h->d_inst_tiles, h->consts, h->n_inst(), h->scalar,
                             h->stream));
     CK(cudaMemcpyAsync(h->h_scalar, h->scalar, size_t(h->n_inst()) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if ((rc = h->fetch_status())) return rc;
     CK(cudaStreamSynchronize(h->stream));
-    return DISCO_OK;
+    return h->check_status();
 }
 
 // Sum of the instances' bounds (the bound of a single instance).
@@ -842,6 +887,8 @@ const char* disco_strerror(int code) {
         case DISCO_ERR_CUDA: return "CUDA error";
         case DISCO_ERR_OOM: return "out of memory";
         case DISCO_ERR_NOT_READY: return "call order violated";
+        case DISCO_ERR_RANGE: return "a dual update left the range of the averaging sums";
+        case DISCO_ERR_INTERNAL: return "a kernel index check failed (bounds-checking build)";
         default: return "unknown error";
     }
 }
@@ -1098,8 +1145,8 @@ int qn_call(disco_handle* h, int mma_iters) {
     const int64_t n = h->nslots_tile;
     if ((rc = qn_init(h, h->opts.qn_memory > 0 ? h->opts.qn_memory : 5))) return rc;
     // lambda <- lambda + pend
-    CK(launch_flush(h->var, h->desc, n, h->acc[h->cur], h->lam, h->lam_lo, s));
-    CK(cudaMemsetAsync(h->acc[h->cur], 0, size_t(h->nint) * kAccStride * 4, s));
+    CK(launch_flush(h->var, h->desc, n, h->msum_rd(), h->fx.inv, h->lam, h->lam_lo, s));
+    CK(cudaMemsetAsync(h->msum_rd(), 0, size_t(h->nint) * sizeof(long long), s));
     double E0;
     if ((rc = lower_bound(h, &E0))) return rc;
     if (h->qn_calls == 0) h->qn_Estart = E0;
@@ -1148,7 +1195,8 @@ int qn_call(disco_handle* h, int mma_iters) {
     // L-BFGS memory (Alg. 4): s = lambda_new - lambda_old, y = g_old - g_new
     if ((rc = qn_subgradient(h, h->qn_g2))) return rc;
     const int b = h->qn_spare;
-    CK(launch_qn_delta(h->lam, h->lam_lo, h->acc[h->cur], h->qn_old, h->qn_old_lo, h->var, h->desc, n, h->qn_S[b], s));
+    CK(launch_qn_delta(h->lam, h->lam_lo, h->msum_rd(), h->fx.inv, h->qn_old, h->qn_old_lo, h->var, h->desc, n,
+                       h->qn_S[b], s));
     CK(launch_qn_sub(h->qn_g, h->qn_g2, n, h->qn_Y[b], s));
     double sy, yy;
     if ((rc = qn_dot(h, h->qn_S[b], h->qn_Y[b], &sy))) return rc;
@@ -1387,7 +1435,9 @@ int disco_min_marginals(disco_handle* h, float* out, int64_t n) {
     if ((rc = h->pass(Pass::FwdMM))) return rc;
     if ((rc = h->pass(Pass::BwdMM))) return rc;
     CK(launch_gather_f32(h->mm_slot, h->canon_pos, ns, h->tmp, h->stream));
-    return write_out(out, h->tmp, size_t(ns) * 4, h->stream);
+    if ((rc = h->fetch_status())) return rc;
+    if ((rc = write_out(out, h->tmp, size_t(ns) * 4, h->stream))) return rc;
+    return h->check_status();
 }
 
 int disco_get_state(disco_handle* h, float* lam, int64_t n, float* pend, int64_t n_pend) {
@@ -1398,7 +1448,7 @@ int disco_get_state(disco_handle* h, float* lam, int64_t n, float* pend, int64_t
     CK(launch_gather_f32(h->lam, h->canon_pos, ns, h->tmp, h->stream));
     if ((rc = write_out(lam, h->tmp, size_t(ns) * 4, h->stream))) return rc;
     if (pend) {
-        CK(launch_pend(h->acc[h->cur], h->deg, h->nint, h->tmp, h->stream));
+        CK(launch_pend(h->msum_rd(), h->deg, h->nint, h->fx.inv, h->tmp, h->stream));
         if ((rc = write_out(pend, h->tmp, size_t(h->nint) * 4, h->stream))) return rc;
     }
     return DISCO_OK;
@@ -1414,10 +1464,11 @@ int disco_set_state(disco_handle* h, const float* lam, int64_t n, const float* p
     CK(cudaMemsetAsync(h->lam_lo, 0, size_t(h->nslots_tile) * 4, h->stream));
     if (pend) {
         CK(cudaMemcpyAsync(h->tmp, pend, size_t(h->nint) * 4, cudaMemcpyDefault, h->stream));
-        CK(launch_set_pend(h->tmp, h->deg, h->nint, h->acc[h->cur], h->stream));
+        CK(launch_set_pend(h->tmp, h->deg, h->nint, h->fx.scale, h->msum_rd(), h->stream));
     } else {
-        CK(cudaMemsetAsync(h->acc[h->cur], 0, size_t(h->nint) * kAccStride * 4, h->stream));
+        CK(cudaMemsetAsync(h->msum_rd(), 0, size_t(h->nint) * sizeof(long long), h->stream));
     }
+    CK(cudaMemsetAsync(h->msum[h->phase], 0, size_t(h->nint) * sizeof(long long), h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->has_b = false;
     return DISCO_OK;
@@ -1489,9 +1540,8 @@ int primal_all(disco_handle* h, uint8_t* x_out, double* costs, int32_t* status) 
     bool done = nint == 0;
     for (int r = 0; r < o.primal_rounds && !done; ++r) {
         // 1. lambda <- lambda + pend; min-marginals under the fixings
-        CK(launch_flush(h->var, h->desc, h->nslots_tile, h->acc[h->cur], h->lam, h->lam_lo, s));
-        CK(cudaMemsetAsync(h->acc[0], 0, size_t(nint) * kAccStride * 4, s));
-        CK(cudaMemsetAsync(h->acc[1], 0, size_t(nint) * kAccStride * 4, s));
+        CK(launch_flush(h->var, h->desc, h->nslots_tile, h->msum_rd(), h->fx.inv, h->lam, h->lam_lo, s));
+        if ((rc = h->clear_sums())) return rc;
         if ((rc = h->pass(Pass::FwdMM))) return rc;
         if ((rc = h->pass(Pass::BwdMM))) return rc;
         // 2. agreement: every slot strictly positive -> 0, strictly negative -> 1
@@ -1547,10 +1597,10 @@ int primal_all(disco_handle* h, uint8_t* x_out, double* costs, int32_t* status) 
     }
     // read the fixings back
     std::vector<uint8_t> st(static_cast<size_t>(nint), uint8_t(0));
-    if (nint) {
-        CK(cudaMemcpyAsync(st.data(), h->state, size_t(nint), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-    }
+    if (nint) CK(cudaMemcpyAsync(st.data(), h->state, size_t(nint), cudaMemcpyDeviceToHost, s));
+    if ((rc = h->fetch_status())) return rc;
+    CK(cudaStreamSynchronize(s));
+    if ((rc = h->check_status())) return rc;
     // the dual continues from an unrestricted state
     CK(cudaMemsetAsync(h->state, 0, size_t(nint), s));
     h->has_b = false;
@@ -1639,7 +1689,7 @@ int alloc_snap(disco_handle* h, Snap* s, bool tape = false) {
     if ((rc = h->alloc(&s->lam_lo, h->nslots_tile))) return rc;
     if (tape) {
         if ((rc = h->alloc(&s->pend, h->nint))) return rc;
-    } else if ((rc = h->alloc(&s->acc, h->nint * kAccStride))) {
+    } else if ((rc = h->alloc(&s->msum, h->nint))) {
         return rc;
     }
     if ((rc = h->alloc(&s->nodes, h->nnodes_tile))) return rc;
@@ -1651,25 +1701,30 @@ int d2d(void* dst, const void* src, size_t bytes, cudaStream_t s) {
     return DISCO_OK;
 }
 
-// Saves lambda, the averaging sectors the next pass reads and the given node costs (none
-// when nodes is null).
+// Saves lambda, the averaging sums the next pass reads and the given node costs (none when
+// nodes is null).
 int save_snap(disco_handle* h, Snap* s, const float* nodes) {
     int rc;
-    const size_t ns = size_t(h->nslots_tile) * 4, na = size_t(h->nint) * kAccStride * 4, nn = size_t(h->nnodes_tile) * 4;
+    const size_t ns = size_t(h->nslots_tile) * 4, na = size_t(h->nint) * sizeof(long long),
+                 nn = size_t(h->nnodes_tile) * 4;
     if ((rc = d2d(s->lam, h->lam, ns, h->stream)) || (rc = d2d(s->lam_lo, h->lam_lo, ns, h->stream)) ||
-        (rc = d2d(s->acc, h->acc[h->cur], na, h->stream)) || (nodes && (rc = d2d(s->nodes, nodes, nn, h->stream))))
+        (rc = d2d(s->msum, h->msum_rd(), na, h->stream)) || (nodes && (rc = d2d(s->nodes, nodes, nn, h->stream))))
         return rc;
-    s->cur = h->cur;
+    s->phase = h->phase;
     return DISCO_OK;
 }
 
+// Restores a saved state at its averaging phase (the buffer the next update pass writes is
+// cleared, as it is between passes).
 int load_snap(disco_handle* h, const Snap& s, float* nodes) {
     int rc;
-    const size_t ns = size_t(h->nslots_tile) * 4, na = size_t(h->nint) * kAccStride * 4, nn = size_t(h->nnodes_tile) * 4;
+    const size_t ns = size_t(h->nslots_tile) * 4, na = size_t(h->nint) * sizeof(long long),
+                 nn = size_t(h->nnodes_tile) * 4;
+    h->phase = s.phase;
     if ((rc = d2d(h->lam, s.lam, ns, h->stream)) || (rc = d2d(h->lam_lo, s.lam_lo, ns, h->stream)) ||
-        (rc = d2d(h->acc[s.cur], s.acc, na, h->stream)) || (rc = d2d(nodes, s.nodes, nn, h->stream)))
+        (rc = d2d(h->msum_rd(), s.msum, na, h->stream)) || (rc = d2d(nodes, s.nodes, nn, h->stream)))
         return rc;
-    h->cur = s.cur;
+    CK(cudaMemsetAsync(h->msum[h->phase], 0, na, h->stream));
     return DISCO_OK;
 }
 
@@ -1680,6 +1735,7 @@ AdjArgs adj_args(disco_handle* h) {
     a.desc = h->desc;
     a.lbar = h->lbar;
     a.omega = h->opts.omega;
+    a.fx = h->fx;
     return a;
 }
 
@@ -1715,10 +1771,9 @@ int disco_record(disco_handle* h, int32_t iters, int32_t checkpoint_every) {
     cudaStream_t s = h->stream;
     const size_t ns = size_t(h->nslots_tile) * 4;
     if ((rc = d2d(h->lam, h->lam0, ns, s)) || (rc = d2d(h->lam_lo, h->lam0_lo, ns, s))) return rc;
-    CK(cudaMemsetAsync(h->acc[0], 0, size_t(h->nint) * kAccStride * 4, s));
-    CK(cudaMemsetAsync(h->acc[1], 0, size_t(h->nint) * kAccStride * 4, s));
+    if ((rc = h->clear_sums())) return rc;
     CK(cudaMemsetAsync(h->state, 0, size_t(h->nint), s));
-    h->cur = 0;
+    h->phase = 0;
     h->iterations = 0;
     if ((rc = reset_b(h))) return rc;
     for (int k = 0; k < nck; ++k) {
@@ -1766,7 +1821,7 @@ int disco_grad(disco_handle* h, float* dlb_dpair_costs, int64_t n) {
     // the bound: forward min-sum on lambda + pend (recompute its node costs, then reverse)
     if ((rc = h->pass(Pass::FwdMM))) return rc;
     {
-        CK(launch_pend_table(h->acc[h->cur], h->deg, h->nint, h->pend_tmp, s));
+        CK(launch_pend_table(h->msum_rd(), h->deg, h->nint, h->fx.inv, h->pend_tmp, s));
         AdjArgs a = adj_args(h);
         a.lam_in = h->lam;
         a.lam_in_lo = h->lam_lo;
@@ -1784,17 +1839,18 @@ int disco_grad(disco_handle* h, float* dlb_dpair_costs, int64_t n) {
         // per-variable table) go to the tape, and the pass stores its node costs straight into
         // the tape (the node arrays are pointed there); the node costs it reads are the
         // previous pass's (or the checkpoint's) stored ones
-        CK(launch_pend_table(h->acc[h->cur], h->deg, h->nint, h->pend_tab, s));  // the MMA passes read it
         float* const F0 = h->F;
         float* const B0 = h->B;
         const size_t ns = size_t(h->nslots_tile) * 4;
         for (int t = 0; t < nit && !rc; ++t)
             for (int dir = 0; dir < 2 && !rc; ++dir) {
                 Snap& tp = h->tape[2 * t + dir];
-                if ((rc = d2d(tp.lam, h->lam, ns, s)) || (rc = d2d(tp.lam_lo, h->lam_lo, ns, s)) ||
-                    (rc = d2d(tp.pend, h->pend_tab, size_t(h->nint) * sizeof(float2), s)))
+                if ((rc = d2d(tp.lam, h->lam, ns, s)) || (rc = d2d(tp.lam_lo, h->lam_lo, ns, s))) break;
+                const cudaError_t e = launch_pend_table(h->msum_rd(), h->deg, h->nint, h->fx.inv, tp.pend, s);
+                if (e != cudaSuccess) {
+                    rc = fail(DISCO_ERR_CUDA, std::string("grad: pend table: ") + cudaGetErrorString(e));
                     break;
-                tp.cur = h->cur;
+                }
                 (dir == 0 ? h->F : h->B) = tp.nodes;
                 rc = h->pass(dir == 0 ? Pass::FwdMMA : Pass::BwdMMA);
             }
@@ -1826,7 +1882,7 @@ int disco_grad(disco_handle* h, float* dlb_dpair_costs, int64_t n) {
         const Snap& c0 = h->checkpoints[0];
         if ((rc = load_snap(h, c0, h->B))) return rc;
         if ((rc = h->pass(Pass::BwdReset))) return rc;
-        CK(launch_pend_table(c0.acc, h->deg, h->nint, h->pend_tmp, s));
+        CK(launch_pend_table(c0.msum, h->deg, h->nint, h->fx.inv, h->pend_tmp, s));
         AdjArgs a = adj_args(h);
         a.lam_in = c0.lam;
         a.lam_in_lo = c0.lam_lo;

@@ -11,14 +11,11 @@
 // deferred, parallel-across-BDDs min-marginal averaging (Alg. 1 "MMA"), dual bound (Eq. D),
 // rounding by min-marginal agreement and propagation (App. A.5, Sec. 3 pipeline).
 //
-// Averaging without atomics, in two forms with the same arithmetic:
-//  * MMA half-passes (MODE 0): every slot writes the mass it removes to slot_mass (tile
-//    layout, coalesced); a reduction kernel (store.cu) sums each variable's deg masses in
-//    rank order into a double-float mean, which the next half-pass reads (8 bytes per slot);
-//  * the other passes: a slot of variable i with rank r writes to acc_out[i * 8 + r]; the
-//    next pass reads the deg values of acc_in[i * 8 ..] (one 32-byte sector) and adds their
-//    mean.
-// Sums run in rank order, so every result is deterministic and both forms agree bit for bit.
+// Averaging in the same launch, without waiting: a slot of variable i reads i's sum of the
+// masses the previous update pass removed (8 bytes; its mean is the deferred mean), and adds
+// the mass it removes itself, rounded to the fixed-point grid, into i's sum of this pass with
+// a fire-and-forget red.add (device_util.cuh). Integer sums do not depend on the order of the
+// additions, so every result is deterministic and the same for every launch geometry.
 #include <atomic>
 #include <cfloat>
 
@@ -37,19 +34,33 @@ constexpr int kFusedWarpsPerSM = 24;
 
 using namespace dev;
 
+// Index checks of the bounds-checking build (DISCO_BOUNDS_CHECK): an index outside its array
+// sets kStatusBounds in the status word and the access is skipped; the host turns the bit into
+// an error at its next synchronisation. The normal build compiles the checks away.
+#ifdef DISCO_BOUNDS_CHECK
+__device__ __forceinline__ bool in_bounds(int64_t i, int64_t n, uint32_t* status) {
+    if (i >= 0 && i < n) return true;
+    atomicOr(status, kStatusBounds);
+    return false;
+}
+#define DISCO_IN(i, n) in_bounds((i), (n), a.status)
+#else
+#define DISCO_IN(i, n) true
+#endif
+
 // ---------------------------------------------------------------------------------------
 // Inputs of one layer of one lane are staged in shared memory ahead of their use. A lane's
 // layers form a sequential recurrence only through the node costs it keeps in registers;
-// every load (lambda, its low part, the variable's averaging sector, the other direction's
+// every load (lambda, its low part, the variable's averaging sum, the other direction's
 // node costs) is independent of it. Each lane therefore keeps kRing layers in flight with
 // asynchronous copies (cp.async, one commit group per layer) into its own slots of a
 // per-warp ring; descriptors and variable ids are fetched kRing layers before the copies
 // that need them. Lanes only ever read their own slots, so no warp synchronisation is needed.
 constexpr int kRing = 3;
 
-// Stage layout (floats, per warp): lam[32] lo[32] acc4[32] acc[32][4] nodes[W][32].
+// Stage layout (floats, per warp): lam[32] lo[32] sum[32][2] nodes[W][32].
 template <int W>
-__host__ __device__ constexpr int stage_floats() { return (7 + W) * 32; }
+__host__ __device__ constexpr int stage_floats() { return (4 + W) * 32; }
 template <int W>
 __host__ __device__ constexpr int ring_floats() { return kRing * stage_floats<W>(); }
 
@@ -57,11 +68,7 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
     const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
-    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(float* dst, const float* src) {
+__device__ __forceinline__ void cp_async8(float* dst, const void* src) {
     const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
 }
@@ -69,33 +76,36 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// red.add of a signed fixed-point mass into a variable's sum (two's complement: the unsigned
+// 64-bit add is the signed one); the result is not read, so no round trip is waited for.
+__device__ __forceinline__ void red_add(long long* p, long long q) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(q));
+}
+
 __device__ __forceinline__ void load_head(const KArgs& a, int64_t si, bool ok, uint32_t& v, uint32_t& d) {
+    ok = ok && DISCO_IN(si, a.nslots);
     v = ok ? __ldg(a.var + si) : kNoVar;
     d = ok ? __ldg(a.desc + si) : 0u;
+#ifdef DISCO_BOUNDS_CHECK
+    if (v != kNoVar && !DISCO_IN(int64_t(v), a.nvars)) v = kNoVar;
+#endif
 }
 
 // Copies of one layer's inputs into stage `st` (this lane's slots), then one commit.
-// NODES: 0 none, 1 = B of layer l + 1 (count wn), 2 = F of layer l (count w).
-// TAB: the variable's deferred mean comes ready from the per-variable table (MMA passes:
-// 8 bytes, into the first two floats of the sector slot) instead of its averaging sector.
-template <int W, int NODES, bool TAB>
-__device__ __forceinline__ void stage_issue(const KArgs& a, float* st, int lane, int64_t si, const float* node_row,
-                                            uint32_t v, uint32_t dsc) {
+// NODES: 0 none, 1 = B of layer l + 1 (count wn), 2 = F of layer l (count w); `nodes` is that
+// array and `ni` the index of the row's first node (state 0) of this lane.
+template <int W, int NODES>
+__device__ __forceinline__ void stage_issue(const KArgs& a, float* st, int lane, int64_t si, const float* nodes,
+                                            int64_t ni, uint32_t v, uint32_t dsc) {
     if (v != kNoVar) {
         cp_async4(st + lane, a.lam + si);
         cp_async4(st + 32 + lane, a.lam_lo + si);
-        if (TAB) {
-            cp_async8(st + 96 + 4 * lane, reinterpret_cast<const float*>(a.pend_tab + v));
-        } else {
-            const float* ap = a.acc_in + size_t(v) * kAccStride;
-            cp_async16(st + 96 + 4 * lane, ap);
-            if (int((dsc >> 25) & 7u) > 4) cp_async4(st + 64 + lane, ap + 4);
-        }
+        cp_async8(st + 64 + 2 * lane, a.msum_rd + v);
         if (NODES) {
             const int n = NODES == 1 ? int((dsc >> 6) & 63u) + 1 : int(dsc & 63u) + 1;
 #pragma unroll
             for (int s = 0; s < W; ++s)
-                if (s < n) cp_async4(st + (7 + s) * 32 + lane, node_row + s * 32);
+                if (s < n && DISCO_IN(ni + s * 32, a.nnodes)) cp_async4(st + (4 + s) * 32 + lane, nodes + ni + s * 32);
         }
     }
     cp_commit();
@@ -105,8 +115,7 @@ __device__ __forceinline__ void stage_issue(const KArgs& a, float* st, int lane,
 template <int W>
 struct Staged {
     float lam, lo;
-    float4 acc;
-    float acc4;
+    long long sum;
     float nb[W];
 };
 
@@ -114,22 +123,23 @@ template <int W, int NODES>
 __device__ __forceinline__ void stage_read(const float* st, int lane, const Desc& d, Staged<W>& x) {
     x.lam = st[lane];
     x.lo = st[32 + lane];
-    x.acc = *reinterpret_cast<const float4*>(st + 96 + 4 * lane);
-    x.acc4 = d.deg > 4 ? st[64 + lane] : 0.0f;
+    x.sum = *reinterpret_cast<const long long*>(st + 64 + 2 * lane);
     if (NODES) {
         const int n = NODES == 1 ? d.wn : d.w;
 #pragma unroll
-        for (int s = 0; s < W; ++s) x.nb[s] = s < n ? st[(7 + s) * 32 + lane] : BIG;
+        for (int s = 0; s < W; ++s) x.nb[s] = s < n ? st[(4 + s) * 32 + lane] : BIG;
     }
 }
 
-template <int W>
-__device__ __forceinline__ df pend_staged(const Staged<W>& x, int deg) {
-    df s = df_add_f(df{x.acc.x, 0.0f}, x.acc.y);
-    if (deg > 2) s = df_add_f(s, x.acc.z);
-    if (deg > 3) s = df_add_f(s, x.acc.w);
-    if (deg > 4) s = df_add_f(s, x.acc4);
-    return df_div_i(s, deg);
+// The averaging step of an update pass for a free variable: round the removed mass to the
+// grid, add it to the variable's sum of this pass, flag a mass outside the grid's range.
+// Returns the mass as rounded (what lambda loses).
+__device__ __forceinline__ float deposit(const KArgs& a, uint32_t v, float removed) {
+    long long q;
+    const float r = fx_round(removed, a.fx, q);
+    if (!(fabsf(removed) < a.fx.lim)) atomicOr(a.status, kStatusRange);
+    red_add(a.msum_wr + v, q);
+    return r;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -146,8 +156,7 @@ __device__ __forceinline__ void forward_tile(const KArgs& a, const int tile, con
     constexpr int SF = stage_floats<W>();
     const int lane = threadIdx.x & 31;
     const int64_t sb = ti.slot_base + lane;
-    const float* Bl = a.B + ti.node_base + lane;  // B of layer l at Bl + l * W * 32
-    float* Fl = a.F + ti.node_base + lane;
+    const int64_t nb = ti.node_base + lane;  // node (l, s) of this lane at nb + (l * W + s) * 32
     const int L = ti.L;
     float f[W];
 #pragma unroll
@@ -156,7 +165,8 @@ __device__ __forceinline__ void forward_tile(const KArgs& a, const int tile, con
 #pragma unroll
     for (int k = 0; k < P; ++k) {
         load_head(a, sb + int64_t(k) * 32, k < L, cv[k], cd[k]);
-        stage_issue<W, NODES, MODE == 0>(a, ring + k * SF, lane, sb + int64_t(k) * 32, Bl + int64_t(k + 1) * W * 32, cv[k], cd[k]);
+        stage_issue<W, NODES>(a, ring + k * SF, lane, sb + int64_t(k) * 32, a.B, nb + int64_t(k + 1) * W * 32, cv[k],
+                              cd[k]);
         load_head(a, sb + int64_t(k + P) * 32, k + P < L, hv[k], hd[k]);
     }
     for (int l0 = 0; l0 < L; l0 += P) {
@@ -172,19 +182,18 @@ __device__ __forceinline__ void forward_tile(const KArgs& a, const int tile, con
             uint32_t nv, nd;
             load_head(a, sb + int64_t(l + 2 * P) * 32, l + 2 * P < L, nv, nd);
             const int64_t si = sb + int64_t(l) * 32;
-            const df p = MODE == 0 ? df{c.acc.x, c.acc.y} : pend_staged(c, d.deg);
+            const df p = fx_mean(c.sum, d.deg, a.fx.inv);
             df Lm{c.lam, c.lo};
             const uint8_t st = kRound ? __ldg(a.state + v) : kFree;
             const bool al0 = st != kFix1, al1 = st != kFix0;
             float lm = Lm.hi;
             if (kStoreF) {
-                float* Fr = Fl + int64_t(l) * W * 32;
+                const int64_t fr = nb + int64_t(l) * W * 32;
 #pragma unroll
                 for (int s = 0; s < W; ++s)
-                    if (s < d.w) Fr[s * 32] = f[s];
+                    if (s < d.w && DISCO_IN(fr + s * 32, a.nnodes)) a.F[fr + s * 32] = f[s];
             }
             if (kUpdate) {
-                float removed = 0.0f;
                 if (st == kFree) {
                     Lm = df_add(Lm, p);
                     // hx[s + 1] = b of node s's 0-child, hx[s + 1 + a] = b of its arithmetic 1-child
@@ -201,14 +210,12 @@ __device__ __forceinline__ void forward_tile(const KArgs& a, const int tile, con
                         for (int s = 0; s < W; ++s) m1 = fminf(m1, f[s] + (up ? hx[s + 2] : hx[s]));
                     }
                     const float M = (m1 + Lm.hi) - m0;
-                    removed = a.omega * M;
-                    Lm = df_add_f(Lm, -removed);
+                    Lm = df_add_f(Lm, -deposit(a, v, a.omega * M));
                     a.lam[si] = Lm.hi;
                     a.lam_lo[si] = Lm.lo;
                     lm = Lm.hi;
                 }
-                if (MODE == 0) a.slot_mass[si] = removed;  // coalesced; the reduction forms the means
-                else a.acc_out[size_t(v) * kAccStride + d.rank] = removed;
+                if (d.rank == 0) a.msum_zero[v] = 0;  // the next update pass's sums start at zero
             } else {
                 lm = df_add(Lm, p).hi;
             }
@@ -225,7 +232,7 @@ __device__ __forceinline__ void forward_tile(const KArgs& a, const int tile, con
                 f[s] = s < d.wn ? fminf(v0, v1) : BIG;
             }
             // stage layer l + P into the slot just consumed
-            stage_issue<W, NODES, MODE == 0>(a, ring + k * SF, lane, sb + int64_t(l + P) * 32, Bl + int64_t(l + P + 1) * W * 32,
+            stage_issue<W, NODES>(a, ring + k * SF, lane, sb + int64_t(l + P) * 32, a.B, nb + int64_t(l + P + 1) * W * 32,
                                   hv[k], hd[k]);
             cv[k] = hv[k];
             cd[k] = hd[k];
@@ -284,8 +291,7 @@ __device__ __forceinline__ void backward_tile(const KArgs& a, const TileInfo& ti
     constexpr int SF = stage_floats<W>();
     const int lane = threadIdx.x & 31;
     const int64_t sb = ti.slot_base + lane;
-    const float* Fl = a.F + ti.node_base + lane;
-    float* Bl = a.B + ti.node_base + lane;
+    const int64_t nb = ti.node_base + lane;  // node (l, s) of this lane at nb + (l * W + s) * 32
     const int L = ti.L;
     float bn[W];
 #pragma unroll
@@ -295,7 +301,7 @@ __device__ __forceinline__ void backward_tile(const KArgs& a, const TileInfo& ti
     for (int k = 0; k < P; ++k) {
         const int l = L - 1 - k;
         load_head(a, sb + int64_t(l) * 32, l >= 0, cv[k], cd[k]);
-        stage_issue<W, NODES, MODE == 0>(a, ring + k * SF, lane, sb + int64_t(l) * 32, Fl + int64_t(l) * W * 32, cv[k], cd[k]);
+        stage_issue<W, NODES>(a, ring + k * SF, lane, sb + int64_t(l) * 32, a.F, nb + int64_t(l) * W * 32, cv[k], cd[k]);
         load_head(a, sb + int64_t(l - P) * 32, l - P >= 0, hv[k], hd[k]);
     }
     for (int l0 = L - 1; l0 >= 0; l0 -= P) {
@@ -312,7 +318,7 @@ __device__ __forceinline__ void backward_tile(const KArgs& a, const TileInfo& ti
                 Staged<W> c;
                 stage_read<W, NODES>(ring + k * SF, lane, d, c);
                 const int64_t si = sb + int64_t(l) * 32;
-                const df p = MODE == 0 ? df{c.acc.x, c.acc.y} : pend_staged(c, d.deg);
+                const df p = fx_mean(c.sum, d.deg, a.fx.inv);
                 df Lm{c.lam, c.lo};
                 const uint8_t st = kRound ? __ldg(a.state + v) : kFree;
                 const bool al0 = st != kFix1, al1 = st != kFix0;
@@ -335,18 +341,15 @@ __device__ __forceinline__ void backward_tile(const KArgs& a, const TileInfo& ti
                         }
                     }
                     if (kUpdate) {
-                        float removed = 0.0f;
                         if (st == kFree) {
                             Lm = df_add(Lm, p);
                             const float M = (m1 + Lm.hi) - m0;
-                            removed = a.omega * M;
-                            Lm = df_add_f(Lm, -removed);
+                            Lm = df_add_f(Lm, -deposit(a, v, a.omega * M));
                             a.lam[si] = Lm.hi;
                             a.lam_lo[si] = Lm.lo;
                             lm = Lm.hi;
                         }
-                        if (MODE == 0) a.slot_mass[si] = removed;  // coalesced; the reduction forms the means
-                        else a.acc_out[size_t(v) * kAccStride + d.rank] = removed;
+                        if (d.rank == 0) a.msum_zero[v] = 0;  // the next update pass's sums start at zero
                     } else {
                         lm = df_add(Lm, p).hi;
                         const float M = (m1 + lm) - m0;
@@ -356,18 +359,18 @@ __device__ __forceinline__ void backward_tile(const KArgs& a, const TileInfo& ti
                 } else {
                     lm = df_add(Lm, p).hi;
                 }
-                float* Br = Bl + int64_t(l) * W * 32;
+                const int64_t br = nb + int64_t(l) * W * 32;
 #pragma unroll
                 for (int s = 0; s < W; ++s) {
                     const float v0 = al0 ? hx[s + 1] : BIG;
                     float v1 = BIG;
                     if (al1) v1 = (d.one ? (s == 0 ? b1 : BIG) : (up ? hx[s + 2] : hx[s])) + lm;
                     bn[s] = s < d.w ? fminf(v0, v1) : BIG;
-                    if (kStoreB && s < d.w) Br[s * 32] = bn[s];
+                    if (kStoreB && s < d.w && DISCO_IN(br + s * 32, a.nnodes)) a.B[br + s * 32] = bn[s];
                 }
             }
-            stage_issue<W, NODES, MODE == 0>(a, ring + k * SF, lane, sb + int64_t(l - P) * 32, Fl + int64_t(l - P) * W * 32, hv[k],
-                                  hd[k]);
+            stage_issue<W, NODES>(a, ring + k * SF, lane, sb + int64_t(l - P) * 32, a.F, nb + int64_t(l - P) * W * 32,
+                                  hv[k], hd[k]);
             cv[k] = hv[k];
             cd[k] = hd[k];
             hv[k] = nv;
@@ -542,24 +545,26 @@ __global__ void k_scatter(const float* __restrict__ src, const int64_t* __restri
         dst[pos[i]] = src[i];
 }
 
-__global__ void k_pend(const float* __restrict__ acc, const uint8_t* __restrict__ deg, int64_t n, float* pend) {
+__global__ void k_pend(const long long* __restrict__ msum, const uint8_t* __restrict__ deg, int64_t n, float inv,
+                       float* pend) {
     for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x)
-        pend[v] = deg[v] ? pend_of(acc, uint32_t(v), deg[v]).hi : 0.0f;
+        pend[v] = deg[v] ? fx_mean(msum[v], deg[v], inv).hi : 0.0f;
 }
 
-__global__ void k_set_pend(const float* __restrict__ pend, const uint8_t* __restrict__ deg, int64_t n, float* acc) {
-    for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
-        // a deferred mean p is reproduced by deg removed masses of p each
-        for (int r = 0; r < kAccStride; ++r) acc[v * kAccStride + r] = r < deg[v] ? pend[v] : 0.0f;
-    }
+// The sum whose deferred mean is pend[v]: pend[v] deg[v] on the grid (a one-off import, so
+// FP64 is fine here).
+__global__ void k_set_pend(const float* __restrict__ pend, const uint8_t* __restrict__ deg, int64_t n, float scale,
+                           long long* msum) {
+    for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x)
+        msum[v] = __double2ll_rn(double(pend[v]) * double(deg[v]) * double(scale));
 }
 
 __global__ void k_flush(const uint32_t* __restrict__ var, const uint32_t* __restrict__ desc, int64_t n,
-                        const float* __restrict__ acc, float* lam, float* lam_lo) {
+                        const long long* __restrict__ msum, float inv, float* lam, float* lam_lo) {
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
         const uint32_t v = var[i];
         if (v == kNoVar) continue;
-        const df L = df_add(df{lam[i], lam_lo[i]}, pend_of(acc, v, decode(desc[i]).deg));
+        const df L = df_add(df{lam[i], lam_lo[i]}, fx_mean(msum[v], decode(desc[i]).deg, inv));
         lam[i] = L.hi;
         lam_lo[i] = L.lo;
     }
@@ -688,7 +693,8 @@ __global__ void k_transpose(const float* __restrict__ src, int rows, int cols, f
 }
 
 // k smallest entries of every row (ties to the lower column), one warp per row: k rounds of
-// a warp-wide arg-min over the entries ordered after the previous pick.
+// a warp-wide arg-min over the entries ordered after the previous pick. Entries that are not
+// below FLT_MAX (+inf, NaN) are never picked; the missing picks are written as -1.
 __global__ void k_topk_rows(const float* __restrict__ d, int rows, int cols, int k, int32_t* __restrict__ idx) {
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -710,7 +716,8 @@ __global__ void k_topk_rows(const float* __restrict__ d, int rows, int cols, int
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if ((ov < bv) || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
         }
-        if (lane == 0) idx[size_t(row) * k + t] = bi;
+        // no entry left below the sentinel (the rest are +inf or NaN): no pick
+        if (lane == 0) idx[size_t(row) * k + t] = bi == INT32_MAX ? -1 : bi;
         pv = bv;
         pi = bi;
     }
@@ -724,6 +731,7 @@ __global__ void k_dilate(const int32_t* __restrict__ topk, int rows, int k, cons
     if (row >= rows) return;
     for (int t = threadIdx.y; t < k; t += blockDim.y) {
         const int c = topk[size_t(row) * k + t];
+        if (c < 0) continue;  // fewer than k finite entries in the row
         for (int j = ring_ptr[c] + threadIdx.x; j < ring_ptr[c + 1]; j += blockDim.x) {
             const int o = ring[j];
             if (!transposed) allowed[size_t(row) * nvy + o] = 1;
@@ -770,19 +778,20 @@ cudaError_t launch_scatter_f32(const float* src, const int64_t* pos, int64_t n, 
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
-cudaError_t launch_pend(const float* acc, const uint8_t* deg, int64_t n, float* pend, cudaStream_t s) {
-    if (n > 0) k_pend<<<grid_for(n, 256), 256, 0, s>>>(acc, deg, n, pend);
+cudaError_t launch_pend(const long long* msum, const uint8_t* deg, int64_t n, float inv, float* pend, cudaStream_t s) {
+    if (n > 0) k_pend<<<grid_for(n, 256), 256, 0, s>>>(msum, deg, n, inv, pend);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
-cudaError_t launch_set_pend(const float* pend, const uint8_t* deg, int64_t n, float* acc, cudaStream_t s) {
-    if (n > 0) k_set_pend<<<grid_for(n, 256), 256, 0, s>>>(pend, deg, n, acc);
+cudaError_t launch_set_pend(const float* pend, const uint8_t* deg, int64_t n, float scale, long long* msum,
+                            cudaStream_t s) {
+    if (n > 0) k_set_pend<<<grid_for(n, 256), 256, 0, s>>>(pend, deg, n, scale, msum);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
-cudaError_t launch_flush(const uint32_t* var, const uint32_t* desc, int64_t n, const float* acc, float* lam,
-                         float* lam_lo, cudaStream_t s) {
-    if (n > 0) k_flush<<<grid_for(n, 256), 256, 0, s>>>(var, desc, n, acc, lam, lam_lo);
+cudaError_t launch_flush(const uint32_t* var, const uint32_t* desc, int64_t n, const long long* msum, float inv,
+                         float* lam, float* lam_lo, cudaStream_t s) {
+    if (n > 0) k_flush<<<grid_for(n, 256), 256, 0, s>>>(var, desc, n, msum, inv, lam, lam_lo);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }

@@ -25,7 +25,20 @@ struct TileInfo {
 };
 
 constexpr uint32_t kNoVar = 0xFFFFFFFFu;
-constexpr int kAccStride = 8;  // floats per variable in the averaging tables
+constexpr int kAccStride = 8;  // entries per variable in the per-rank tables (min-marginals, supports, adjoints)
+
+// Fixed-point grid of the averaging sums (device_util.cuh): scale = 2^F, inv = 2^-F, lim =
+// the largest mass one slot may remove (2^(59 - F)).
+struct FxScale {
+    float scale, inv, lim;
+};
+
+// Bits of the per-handle device status word, set by kernels and read by the host at its
+// synchronisation points.
+enum : uint32_t {
+    kStatusRange = 1u,   // a removed mass reached FxScale::lim (or was not finite)
+    kStatusBounds = 2u,  // bounds-checking build: an index fell outside its array (access skipped)
+};
 // Width classes up to kFusedMaxW share one launch (launch_pass with W = 0); wider classes
 // launch on their own.
 constexpr int kFusedMaxW = 6;
@@ -40,10 +53,15 @@ struct KArgs {
     float* lam_lo;                   // low part: lambda = lam + lam_lo (double-float)
     float* F;
     float* B;
-    const float* acc_in;             // mass removed by the previous half-pass (kAccStride per var)
-    const float2* pend_tab;          // MMA half-passes: each variable's deferred mean (double-float)
-    float* slot_mass;                // MMA half-passes: the mass each slot removes (tile layout)
-    float* acc_out;                  // mass removed by this half-pass
+    // Averaging state (three rotating buffers of one signed 64-bit sum per variable): msum_rd
+    // holds the masses removed by the last update pass (its mean is each variable's deferred
+    // mean, read by every pass); an update pass adds its removed masses into msum_wr (zero on
+    // entry) and clears msum_zero, the buffer the next update pass writes (rank-0 slots).
+    const long long* msum_rd;
+    long long* msum_wr;
+    long long* msum_zero;
+    FxScale fx;
+    uint32_t* status;                // device status word (kStatus* bits)
     const uint8_t* state;            // per variable, rounding only
     float omega;
     float* mm_slot;                  // per slot (tile layout)
@@ -51,6 +69,8 @@ struct KArgs {
     double* tile_sum;                // per tile
     uint32_t* reach;                 // per slot (tile layout)
     uint8_t* sup_var;                // kAccStride per variable
+    // array sizes, checked by the bounds-checking build only
+    int64_t nslots, nnodes, nvars;
 };
 
 // Arguments of the adjoint kernels (adjoint.cu). A pass's inputs come from the tape (the
@@ -77,6 +97,7 @@ struct AdjArgs {
     const float* rbar;      // per variable: adjoint of each mass the pass removed (launch_rbar_table)
     float* mubar_out;
     float omega;
+    FxScale fx;             // the forward passes' rounding of the removed masses
 };
 
 enum class Adj {
@@ -90,9 +111,10 @@ enum class Adj {
 // only tiles of that group).
 cudaError_t launch_adjoint(Adj kind, int group, const AdjArgs& a, cudaStream_t s);
 // cbar[v] = (sum over v's slots of lbar) / deg[v], via a rank-sector table (tab).
-// pend[v] = the deferred mean of v's averaging sector (double-float, as the half-passes add it);
+// pend[v] = the deferred mean of v's averaging sum (double-float, exactly as the passes add it);
 // rbar[v] = (sum of v's adjoint sector) / deg[v].
-cudaError_t launch_pend_table(const float* acc, const uint8_t* deg, int64_t n, float2* out, cudaStream_t s);
+cudaError_t launch_pend_table(const long long* msum, const uint8_t* deg, int64_t n, float inv, float2* out,
+                              cudaStream_t s);
 cudaError_t launch_rbar_table(const float* mub, const uint8_t* deg, int64_t n, float* out, cudaStream_t s);
 cudaError_t launch_adj_cost(const uint32_t* var, const uint32_t* desc, int64_t nslots, const float* lbar,
                             const uint8_t* deg, int64_t nint, float* tab, float* cbar, cudaStream_t s);
@@ -107,17 +129,6 @@ cudaError_t launch_layout(const int64_t* seg_canon, const int32_t* seg_len, cons
                           float* lam_lo, int64_t* canon_pos, cudaStream_t s);
 cudaError_t launch_instance_of(const int64_t* base, int32_t ni, int64_t n, int32_t* out, cudaStream_t s);
 
-// Averaging of the MMA half-passes (store.cu). Every slot writes the mass it removes to
-// slot_mass (tile layout); vpos[v * 8 + r] = the tile slot of variable v's rank-r slot.
-// launch_reduce: pend[v] = (sum over ranks, in rank order, of v's slot masses) / deg[v] in
-// double-float, the same operations as the deferred mean of an averaging sector.
-// launch_scatter_back: acc[v * 8 + r] = v's rank-r slot mass (the sector form).
-cudaError_t launch_vpos(const uint32_t* var, const uint32_t* desc, int64_t nslots, int32_t* vpos, cudaStream_t s);
-cudaError_t launch_reduce(const int32_t* vpos, const float* slot_mass, const uint8_t* deg, int64_t nint, float2* pend,
-                          cudaStream_t s);
-cudaError_t launch_scatter_back(const int32_t* vpos, const float* slot_mass, const uint8_t* deg, int64_t nint,
-                                float* acc, cudaStream_t s);
-
 // Quasi-Newton vector kernels (qn.cu); n = slots in tile layout.
 cudaError_t launch_qn_sign(const float* mm, const uint32_t* var, int64_t n, float* g, cudaStream_t s);
 int qn_dot_blocks();
@@ -129,7 +140,7 @@ cudaError_t launch_qn_project(float* x, const uint32_t* var, const uint32_t* des
                               cudaStream_t s);
 cudaError_t launch_qn_step(const float* lam, const float* lam_lo, const float* d, float gamma, const uint32_t* var,
                            int64_t n, float* out, float* out_lo, cudaStream_t s);
-cudaError_t launch_qn_delta(const float* lam, const float* lam_lo, const float* acc, const float* old,
+cudaError_t launch_qn_delta(const float* lam, const float* lam_lo, const long long* msum, float inv, const float* old,
                             const float* old_lo, const uint32_t* var, const uint32_t* desc, int64_t n, float* s_out,
                             cudaStream_t s);
 
@@ -156,10 +167,13 @@ cudaError_t launch_sum_instances(const double* tile_sum, const int32_t* ptr, con
                                  int64_t n, double* out, cudaStream_t s);
 cudaError_t launch_gather_f32(const float* src, const int64_t* pos, int64_t n, float* dst, cudaStream_t s);
 cudaError_t launch_scatter_f32(const float* src, const int64_t* pos, int64_t n, float* dst, cudaStream_t s);
-cudaError_t launch_pend(const float* acc, const uint8_t* deg, int64_t n, float* pend, cudaStream_t s);
-cudaError_t launch_set_pend(const float* pend, const uint8_t* deg, int64_t n, float* acc, cudaStream_t s);
-cudaError_t launch_flush(const uint32_t* var, const uint32_t* desc, int64_t nslots, const float* acc, float* lam,
-                         float* lam_lo, cudaStream_t s);
+// pend[v] = the deferred mean of v (FP32); launch_set_pend: the sums whose means are pend
+// (pend[v] deg[v] on the grid); launch_flush: lambda += the deferred mean of its variable.
+cudaError_t launch_pend(const long long* msum, const uint8_t* deg, int64_t n, float inv, float* pend, cudaStream_t s);
+cudaError_t launch_set_pend(const float* pend, const uint8_t* deg, int64_t n, float scale, long long* msum,
+                            cudaStream_t s);
+cudaError_t launch_flush(const uint32_t* var, const uint32_t* desc, int64_t nslots, const long long* msum, float inv,
+                         float* lam, float* lam_lo, cudaStream_t s);
 cudaError_t launch_decide(const float* mm_var, const uint8_t* deg, const uint8_t* state, int64_t n, float tau,
                           uint8_t* trial, cudaStream_t s);
 cudaError_t launch_apply(const uint8_t* sup_var, const uint8_t* deg, const int32_t* inst, int64_t n, uint8_t* state,

@@ -93,17 +93,17 @@ __global__ void k_step(const float* lam, const float* lam_lo, const float* __res
 }
 
 // s = (lambda + pend) - old, in double-float, rounded to FP32.
-__global__ void k_delta(const float* __restrict__ lam, const float* __restrict__ lam_lo, const float* __restrict__ acc,
-                        const float* __restrict__ old, const float* __restrict__ old_lo,
-                        const uint32_t* __restrict__ var, const uint32_t* __restrict__ desc, int64_t n,
-                        float* __restrict__ s) {
+__global__ void k_delta(const float* __restrict__ lam, const float* __restrict__ lam_lo,
+                        const long long* __restrict__ msum, float inv, const float* __restrict__ old,
+                        const float* __restrict__ old_lo, const uint32_t* __restrict__ var,
+                        const uint32_t* __restrict__ desc, int64_t n, float* __restrict__ s) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
         const uint32_t v = var[i];
         if (v == kNoVar) {
             s[i] = 0.0f;
             continue;
         }
-        const df t = df_add(df{lam[i], lam_lo[i]}, pend_of(acc, v, decode(desc[i]).deg));
+        const df t = df_add(df{lam[i], lam_lo[i]}, fx_mean(msum[v], decode(desc[i]).deg, inv));
         const df r = df_add(t, df{-old[i], -old_lo[i]});
         s[i] = r.hi + r.lo;
     }
@@ -158,10 +158,10 @@ cudaError_t launch_qn_step(const float* lam, const float* lam_lo, const float* d
     return cudaGetLastError();
 }
 
-cudaError_t launch_qn_delta(const float* lam, const float* lam_lo, const float* acc, const float* old,
+cudaError_t launch_qn_delta(const float* lam, const float* lam_lo, const long long* msum, float inv, const float* old,
                             const float* old_lo, const uint32_t* var, const uint32_t* desc, int64_t n, float* s_out,
                             cudaStream_t s) {
-    k_delta<<<grid_of(n), 256, 0, s>>>(lam, lam_lo, acc, old, old_lo, var, desc, n, s_out);
+    k_delta<<<grid_of(n), 256, 0, s>>>(lam, lam_lo, msum, inv, old, old_lo, var, desc, n, s_out);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }

@@ -44,48 +44,6 @@ __global__ void k_instance_of(const int64_t* __restrict__ base, int32_t ni, int6
     }
 }
 
-__global__ void k_vpos(const uint32_t* __restrict__ var, const uint32_t* __restrict__ desc, int64_t n,
-                       int32_t* __restrict__ vpos) {
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        const uint32_t v = var[i];
-        if (v != kNoVar) vpos[size_t(v) * kAccStride + ((desc[i] >> 22) & 7u)] = int32_t(i);
-    }
-}
-
-// One thread per variable: its deg slot masses in rank order, summed and divided in
-// double-float exactly as the half-pass kernels form a deferred mean from a sector. The
-// degree and the 32-byte position sector load together, and every mass gather issues before
-// the sum, so a variable waits on two memory round trips, not 2 + deg.
-__global__ void k_reduce(const int32_t* __restrict__ vpos, const float* __restrict__ m, const uint8_t* __restrict__ deg,
-                         int64_t n, float2* __restrict__ pend) {
-    using namespace dev;
-    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
-        const int4* qp = reinterpret_cast<const int4*>(vpos + size_t(v) * kAccStride);
-        const int4 q0 = qp[0], q1 = qp[1];
-        const int dg = deg[v];
-        if (dg < 2) {  // every internal variable has 2 or more slots
-            pend[v] = make_float2(0.0f, 0.0f);
-            continue;
-        }
-        const int q[kAccStride] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-        float x[kAccStride];
-#pragma unroll
-        for (int r = 0; r < kAccStride; ++r) x[r] = r < dg ? m[q[r]] : 0.0f;
-        df s = df_add_f(df{x[0], 0.0f}, x[1]);
-#pragma unroll
-        for (int r = 2; r < kAccStride; ++r)
-            if (r < dg) s = df_add_f(s, x[r]);
-        const df p = df_div_i(s, dg);
-        pend[v] = make_float2(p.hi, p.lo);
-    }
-}
-
-__global__ void k_scatter_back(const int32_t* __restrict__ vpos, const float* __restrict__ m,
-                               const uint8_t* __restrict__ deg, int64_t n, float* __restrict__ acc) {
-    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x)
-        for (int r = 0; r < deg[v]; ++r) acc[size_t(v) * kAccStride + r] = m[vpos[size_t(v) * kAccStride + r]];
-}
-
 inline unsigned grid_for(int64_t n, int block) {
     const int64_t g = (n + block - 1) / block;
     return unsigned(g < 1 ? 1 : (g > 152 * 64 ? 152 * 64 : g));
@@ -100,29 +58,6 @@ cudaError_t launch_layout(const int64_t* seg_canon, const int32_t* seg_len, cons
     if (nseg <= 0) return cudaSuccess;
     k_layout<<<grid_for(nseg, 128), 128, 0, s>>>(seg_canon, seg_len, seg_pos, seg_vb, nseg, cvar, cdesc, clam, clam_lo,
                                                    var, desc, lam, lam_lo, canon_pos);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_vpos(const uint32_t* var, const uint32_t* desc, int64_t nslots, int32_t* vpos, cudaStream_t s) {
-    if (nslots <= 0) return cudaSuccess;
-    k_vpos<<<grid_for(nslots, 256), 256, 0, s>>>(var, desc, nslots, vpos);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_reduce(const int32_t* vpos, const float* slot_mass, const uint8_t* deg, int64_t nint, float2* pend,
-                          cudaStream_t s) {
-    if (nint <= 0) return cudaSuccess;
-    k_reduce<<<grid_for(nint, 256), 256, 0, s>>>(vpos, slot_mass, deg, nint, pend);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_scatter_back(const int32_t* vpos, const float* slot_mass, const uint8_t* deg, int64_t nint,
-                                float* acc, cudaStream_t s) {
-    if (nint <= 0) return cudaSuccess;
-    k_scatter_back<<<grid_for(nint, 256), 256, 0, s>>>(vpos, slot_mass, deg, nint, acc);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
