@@ -3,9 +3,15 @@
 // double-float arithmetic for the dual variables.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "kernels.h"
+
+// Functions marked DH are also compiled for the host: the averaging arithmetic is checked on
+// the CPU against exact integer arithmetic.
+#define DH __host__ __device__ __forceinline__
 
 namespace disco {
 namespace dev {
@@ -59,21 +65,40 @@ struct df {
     float hi, lo;
 };
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+DH uint32_t bits_of(float x) {
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(x);
+#else
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    return u;
+#endif
+}
+DH float float_of(uint32_t u) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float x;
+    std::memcpy(&x, &u, 4);
+    return x;
+#endif
+}
+
+DH void two_sum(float a, float b, float& s, float& e) {
     s = a + b;
     const float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
 }
-__device__ __forceinline__ df fast2sum(float s, float e) {
+DH df fast2sum(float s, float e) {
     const float h = s + e;
     return df{h, e - (h - s)};
 }
-__device__ __forceinline__ df df_add(df a, df b) {
+DH df df_add(df a, df b) {
     float s, e;
     two_sum(a.hi, b.hi, s, e);
     return fast2sum(s, e + (a.lo + b.lo));
 }
-__device__ __forceinline__ df df_add_f(df a, float b) {
+DH df df_add_f(df a, float b) {
     float s, e;
     two_sum(a.hi, b, s, e);
     return fast2sum(s, e + a.lo);
@@ -81,9 +106,15 @@ __device__ __forceinline__ df df_add_f(df a, float b) {
 // a / n for a small positive integer n. q = a.hi * (1/n) is within an ulp of a.hi / n, so the
 // remainder a.hi - q n is exact with an FMA (the classic division-by-reciprocal argument);
 // the low part needs only single precision.
-__device__ __forceinline__ df df_div_i(df a, int n) {
-    const float fn = float(n);
-    const float rcp = n == 2 ? 0.5f : (n == 3 ? 0.333333343f : (n == 4 ? 0.25f : (n == 5 ? 0.2f : 1.0f / fn)));
+DH df df_div_i(df a, int n) {
+    const float fn = float_of(0x4B000000u | uint32_t(n)) - 8388608.0f;  // exact for 0 <= n < 2^23
+    // 1/n correctly rounded to FP32 (n = 2 .. 7, the possible degrees)
+    const float rcp = n == 2 ? 0.5f
+                    : n == 3 ? 0.333333343f
+                    : n == 4 ? 0.25f
+                    : n == 5 ? 0.200000003f
+                    : n == 6 ? 0.166666672f
+                             : 0.142857149f;
     const float q = a.hi * rcp;
     const float r = fmaf(-q, fn, a.hi) + a.lo;
     return fast2sum(q, r * rcp);
@@ -95,25 +126,57 @@ __device__ __forceinline__ df df_div_i(df a, int n) {
 // is the same for every schedule of the lanes and needs no second pass over the slots. The
 // slot subtracts exactly the rounded mass from its lambda, so sum_j lambda^j_i + |J_i| pend_i
 // = c_i (Eq. D) holds as exactly as before. F is chosen per handle from the largest cost;
-// lim = 2^(59 - F) bounds one mass, so sums of up to 7 stay inside the 64-bit range.
+// one rounded mass is at most 2^42 grid units (lim = 2^(42 - F); the kernels flag a larger
+// one), so a sum of up to 7 stays below 2^45.
 //
-// m on the grid: q = round(m 2^F) and the return value q 2^-F, both exact (m 2^F has 24
-// significant bits, so rounding it to an integer leaves at most 24, which FP32 holds).
-__device__ __forceinline__ float fx_round(float m, const FxScale& fx, long long& q) {
-    const float t = rintf(m * fx.scale);
-    q = __float2ll_rn(t);
-    return t * fx.inv;
+// No conversion instruction touches a 64-bit integer: those run on the FP64 pipe, which is a
+// small fraction of the FP32 rate on this GPU. Integers of fewer than 24 bits move between
+// the integer and FP32 registers by the 2^23 significand trick: for 0 <= n < 2^23 the float
+// with bits 0x4B000000 + n is exactly 2^23 + n (and 0x4B400000 + n is 1.5 * 2^23 + n for
+// -2^22 <= n < 2^22).
+constexpr float kTwo23 = 8388608.0f;        // 2^23
+constexpr float kOneHalf23 = 12582912.0f;   // 1.5 * 2^23
+constexpr float kTwo42 = 4398046511104.0f;  // 2^42
+constexpr int kFxSumBits = 45;              // |sum| < 2^45 grid units
+
+// The integer value of an integer-valued float x with |x| <= 2^53: x = s 2^(e - 150) with s its
+// 24-bit significand and e its biased exponent, i.e. (s 2^32) >> (182 - e) (the shift is at
+// least 2 here; 0 has e = 0 and shifts everything out).
+DH long long int_of_float(float x) {
+    const uint32_t u = bits_of(x);
+    const uint32_t a = u & 0x7FFFFFFFu;
+    const uint32_t sig = (a & 0x7FFFFFu) | 0x800000u;
+    const int sh = min(182 - int(a >> 23), 63);
+    const long long q = (long long)(((unsigned long long)sig << 32) >> sh);
+    return (u >> 31) ? -q : q;
 }
-// A sum S (units of 2^-F) as double-float: hi = S rounded to FP32, lo = the exact integer
-// remainder S - hi rounded to FP32 (|lo| <= ulp(hi) / 2, so the pair is normalised); the
-// scaling by 2^-F is exact. Relative error about 2^-48.
-__device__ __forceinline__ df fx_to_df(long long S, float inv) {
-    const float hi = __ll2float_rn(S);
-    const float lo = __ll2float_rn(S - __float2ll_rn(hi));
-    return df{hi * inv, lo * inv};
+
+// m on the grid: q = m 2^F rounded to an integer (ties to even), and the return value q 2^-F,
+// both exact (m 2^F has 24 significant bits, so rounding it to an integer leaves at most 24,
+// which FP32 holds; from 2^23 on a float is an integer already). |m 2^F| is clamped to 2^42
+// first; a clamped mass is flagged by the caller as out of range.
+DH float fx_round(float m, const FxScale& fx, long long& q) {
+    const float t = fminf(fmaxf(m * fx.scale, -kTwo42), kTwo42);
+    const float a = fabsf(t);
+    const float r = copysignf(a < kTwo23 ? (a + kTwo23) - kTwo23 : a, t);
+    q = int_of_float(r);
+    return r * fx.inv;
+}
+
+// A sum S (units of 2^-F, |S| < 2^45) as double-float, exactly: S = A 2^23 + C with
+// 0 <= C < 2^23 and |A| < 2^22, both parts exact in FP32; TwoSum adds them without error
+// (the pair holds 48 bits), and the scaling by 2^-F is exact.
+DH df fx_to_df(long long S, float inv) {
+    const uint32_t c = uint32_t(S) & 0x7FFFFFu;
+    const int32_t a = int32_t(S >> 23);
+    const float cf = float_of(0x4B000000u + c) - kTwo23;
+    const float af = (float_of(uint32_t(0x4B400000 + a)) - kOneHalf23) * kTwo23;
+    float s, e;
+    two_sum(af, cf, s, e);
+    return df{s * inv, e * inv};
 }
 // The deferred mean of a variable: its sum / deg, in double-float.
-__device__ __forceinline__ df fx_mean(long long S, int deg, float inv) { return df_div_i(fx_to_df(S, inv), deg); }
+DH df fx_mean(long long S, int deg, float inv) { return df_div_i(fx_to_df(S, inv), deg); }
 
 __device__ __forceinline__ uint64_t shl(uint64_t x, int k) { return k >= 0 ? (x << k) : (x >> (-k)); }
 __device__ __forceinline__ uint64_t low_mask(int n) { return n >= 64 ? ~0ull : ((1ull << n) - 1ull); }

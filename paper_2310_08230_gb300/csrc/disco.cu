@@ -339,9 +339,9 @@ int upload(disco_handle* h) {
             if (dg < 2 || dg > 7)
                 return fail(DISCO_ERR_INVALID_ARG, "build: an internal variable lies in " + std::to_string(int(dg)) +
                                                        " segments (2 to 7 expected)");
-    // Fixed-point grid of the averaging sums: 2^-F with 2^(40 - F) >= the largest |cost| (at
-    // least 2^-20), so one mass may grow to 2^19 times the largest cost before the kernels flag
-    // it, and the grid is about 1e-12 of the largest cost.
+    // Fixed-point grid of the averaging sums: 2^-F with 2^(32 - F) >= the largest |cost| (at
+    // least 2^-20), so one mass may reach 2^10 times the largest cost before the kernels flag
+    // it (the sums stay below 2^45 grid units), and the grid is about 2e-10 of the largest cost.
     {
         double cmax = 0.0;
         for (int64_t i = 0; i < ni; ++i)
@@ -349,8 +349,8 @@ int upload(disco_handle* h) {
         int e = 0;
         std::frexp(std::max(cmax, std::ldexp(1.0, -20)), &e);  // cmax < 2^e
         e = std::min(e, 30);
-        const int F = 40 - e;
-        h->fx = FxScale{std::ldexp(1.0f, F), std::ldexp(1.0f, -F), std::ldexp(1.0f, 59 - F)};
+        const int F = 32 - e;
+        h->fx = FxScale{std::ldexp(1.0f, F), std::ldexp(1.0f, -F), std::ldexp(1.0f, 42 - F)};
     }
     // ---- tiles: per instance, segments grouped by width class, longest first; a tile never
     // mixes instances (its bound sum belongs to one instance). Counting sorts by (class,
@@ -1464,7 +1464,7 @@ int disco_set_state(disco_handle* h, const float* lam, int64_t n, const float* p
     CK(cudaMemsetAsync(h->lam_lo, 0, size_t(h->nslots_tile) * 4, h->stream));
     if (pend) {
         CK(cudaMemcpyAsync(h->tmp, pend, size_t(h->nint) * 4, cudaMemcpyDefault, h->stream));
-        CK(launch_set_pend(h->tmp, h->deg, h->nint, h->fx.scale, h->msum_rd(), h->stream));
+        CK(launch_set_pend(h->tmp, h->deg, h->nint, h->fx.scale, h->msum_rd(), h->status, h->stream));
     } else {
         CK(cudaMemsetAsync(h->msum_rd(), 0, size_t(h->nint) * sizeof(long long), h->stream));
     }

@@ -552,11 +552,18 @@ __global__ void k_pend(const long long* __restrict__ msum, const uint8_t* __rest
 }
 
 // The sum whose deferred mean is pend[v]: pend[v] deg[v] on the grid (a one-off import, so
-// FP64 is fine here).
+// FP64 is fine here); a value outside the sums' range is clamped and flagged.
 __global__ void k_set_pend(const float* __restrict__ pend, const uint8_t* __restrict__ deg, int64_t n, float scale,
-                           long long* msum) {
-    for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x)
-        msum[v] = __double2ll_rn(double(pend[v]) * double(deg[v]) * double(scale));
+                           long long* msum, uint32_t* status) {
+    const double lim = double(1ll << (kFxSumBits - 1));
+    for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
+        double x = double(pend[v]) * double(deg[v]) * double(scale);
+        if (!(fabs(x) < lim)) {
+            atomicOr(status, kStatusRange);
+            x = x > 0.0 ? lim : -lim;
+        }
+        msum[v] = __double2ll_rn(x);
+    }
 }
 
 __global__ void k_flush(const uint32_t* __restrict__ var, const uint32_t* __restrict__ desc, int64_t n,
@@ -784,8 +791,8 @@ cudaError_t launch_pend(const long long* msum, const uint8_t* deg, int64_t n, fl
     return cudaGetLastError();
 }
 cudaError_t launch_set_pend(const float* pend, const uint8_t* deg, int64_t n, float scale, long long* msum,
-                            cudaStream_t s) {
-    if (n > 0) k_set_pend<<<grid_for(n, 256), 256, 0, s>>>(pend, deg, n, scale, msum);
+                            uint32_t* status, cudaStream_t s) {
+    if (n > 0) k_set_pend<<<grid_for(n, 256), 256, 0, s>>>(pend, deg, n, scale, msum, status);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }

@@ -28,7 +28,7 @@ constexpr uint32_t kNoVar = 0xFFFFFFFFu;
 constexpr int kAccStride = 8;  // entries per variable in the per-rank tables (min-marginals, supports, adjoints)
 
 // Fixed-point grid of the averaging sums (device_util.cuh): scale = 2^F, inv = 2^-F, lim =
-// the largest mass one slot may remove (2^(59 - F)).
+// the largest mass one slot may remove (2^(42 - F)).
 struct FxScale {
     float scale, inv, lim;
 };
@@ -171,7 +171,7 @@ cudaError_t launch_scatter_f32(const float* src, const int64_t* pos, int64_t n, 
 // (pend[v] deg[v] on the grid); launch_flush: lambda += the deferred mean of its variable.
 cudaError_t launch_pend(const long long* msum, const uint8_t* deg, int64_t n, float inv, float* pend, cudaStream_t s);
 cudaError_t launch_set_pend(const float* pend, const uint8_t* deg, int64_t n, float scale, long long* msum,
-                            cudaStream_t s);
+                            uint32_t* status, cudaStream_t s);
 cudaError_t launch_flush(const uint32_t* var, const uint32_t* desc, int64_t nslots, const long long* msum, float inv,
                          float* lam, float* lam_lo, cudaStream_t s);
 cudaError_t launch_decide(const float* mm_var, const uint8_t* deg, const uint8_t* state, int64_t n, float tau,
