@@ -148,8 +148,10 @@ int disco_pair_distances(const float *FX, const float *FY, int32_t nvx, int32_t 
  * Candidate mask of the top-k pruned product space (Sec. 4 pruning to neighbourhoods of
  * vertex matches): allowed[m*nvy + n] = 1 iff n lies in the closed 1-ring (on Y) of one of
  * the k smallest d[m, .] (ties to the lower index), or m lies in the closed 1-ring (on X)
- * of one of the k smallest d[., n]. d and allowed are DEVICE pointers; X and Y are host
- * meshes (only T is read). 1 <= k <= 64. Asynchronous on `stream`.
+ * of one of the k smallest d[., n]. Only finite entries are ranked: a row or column with
+ * fewer than k finite entries (the rest +inf or NaN) contributes just those. d and allowed
+ * are DEVICE pointers; X and Y are host meshes (only T is read). 1 <= k <= 64.
+ * Asynchronous on `stream`.
  */
 int disco_candidates(const float *d, int32_t nvx, int32_t nvy, int32_t k, const disco_mesh *X,
                      const disco_mesh *Y, uint8_t *allowed, void *stream);
@@ -163,9 +165,11 @@ int disco_candidates(const float *d, int32_t nvx, int32_t nvy, int32_t k, const 
  * loading the library holds until the process exits. Limits: at most 16384 vertices and
  * 32768 triangles per mesh, 1 <= k <= 32 (and k <= both vertex counts); larger sizes return
  * DISCO_ERR_INVALID_ARG before any GPU work. The first call on a device resolves the
- * array's address (make it before any stream capture). All calls on a device share the
- * array: calls whose GPU work overlaps race and must be serialised by the caller. Each call
- * clears what it needs and synchronises `stream` before returning.
+ * array's address (make it before any stream capture) and caches it; a cudaDeviceReset
+ * invalidates the cached address, so the entry point must not be called again in that
+ * process after one. All calls on a device share the array: calls whose GPU work overlaps
+ * race and must be serialised by the caller. Each call clears what it needs and
+ * synchronises `stream` before returning.
  */
 int disco_candidates_noalloc(const float *d, int32_t nvx, int32_t nvy, int32_t k, const disco_mesh *X,
                              const disco_mesh *Y, uint8_t *allowed, void *stream);

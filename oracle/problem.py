@@ -128,15 +128,20 @@ def candidate_pairs(d: np.ndarray, k: int, TX: np.ndarray, TY: np.ndarray) -> np
 
     (m, n) is allowed iff n lies in the closed 1-ring of one of the k feature-nearest
     Y vertices of m, or m lies in the closed 1-ring of one of the k feature-nearest X
-    vertices of n (ties to the lower index)."""
+    vertices of n (ties to the lower index). Only finite costs are ranked: a row (or
+    column) with fewer than k finite entries contributes just those."""
     nx, ny = d.shape
+    fin = np.isfinite(d)
+    dr = np.where(fin, d, np.inf)  # non-finite entries sort last and are dropped below
     # 0/1 indicator matrices; the products below count ring hits, exact in float64
     cxy = np.zeros((nx, ny), dtype=np.float64)  # n0 among the k nearest of m
     cyx = np.zeros((nx, ny), dtype=np.float64)  # m0 among the k nearest of n
-    rows = np.argsort(d, axis=1, kind="stable")[:, : min(k, ny)]
-    cxy[np.arange(nx)[:, None], rows] = 1
-    cols = np.argsort(d, axis=0, kind="stable")[: min(k, nx), :]
-    cyx[cols, np.arange(ny)[None, :]] = 1
+    rows = np.argsort(dr, axis=1, kind="stable")[:, : min(k, ny)]
+    ri = np.broadcast_to(np.arange(nx)[:, None], rows.shape)
+    cxy[ri, rows] = fin[ri, rows]
+    cols = np.argsort(dr, axis=0, kind="stable")[: min(k, nx), :]
+    ci = np.broadcast_to(np.arange(ny)[None, :], cols.shape)
+    cyx[cols, ci] = fin[cols, ci]
     AX = closed_one_ring(nx, TX).astype(np.float64)
     AY = closed_one_ring(ny, TY).astype(np.float64)
     return ((cxy @ AY) > 0) | ((AX @ cyx) > 0)

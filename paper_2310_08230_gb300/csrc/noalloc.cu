@@ -20,7 +20,9 @@
 //
 // Set-up: the first call on a device resolves the array's device address with
 // cudaGetSymbolAddress (with that device current) and caches it; make that first call
-// before any stream capture.
+// before any stream capture. A cudaDeviceReset invalidates the cached address: after one,
+// this entry point must not be called again in the same process.
+#include <cfloat>
 #include <mutex>
 
 #include "../../include/disco.h"
@@ -107,15 +109,17 @@ __global__ void k_fill(const int32_t* __restrict__ T, int nt, int32_t* cursor, i
         inc[atomicAdd(cursor + T[i], 1)] = i / 3;
 }
 
-// k smallest entries of every column of d (ties to the lower row), one warp per column.
+// k smallest entries of every column of d (ties to the lower row), one warp per column; the
+// same rule as the row kernel (k_topk_rows): only finite entries are picked, a missing pick
+// is written as -1.
 __global__ void k_topk_cols(const float* __restrict__ d, int rows, int cols, int k, int32_t* __restrict__ idx) {
     const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (col >= cols) return;
-    float pv = -3.4e38f;
+    float pv = -FLT_MAX;
     int pi = -1;
     for (int t = 0; t < k; ++t) {
-        float bv = 3.4e38f;
+        float bv = FLT_MAX;
         int bi = 0x7fffffff;
         for (int r = lane; r < rows; r += 32) {
             const float x = d[size_t(r) * cols + col];
@@ -127,7 +131,7 @@ __global__ void k_topk_cols(const float* __restrict__ d, int rows, int cols, int
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if ((ov < bv) || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
         }
-        if (lane == 0) idx[size_t(col) * k + t] = bi;
+        if (lane == 0) idx[size_t(col) * k + t] = bi == 0x7fffffff ? -1 : bi;
         pv = bv;
         pi = bi;
     }
@@ -142,6 +146,7 @@ __global__ void k_mark(const int32_t* __restrict__ topk, int rows, int k, const 
     if (r >= rows) return;
     for (int t = threadIdx.y; t < k; t += blockDim.y) {
         const int c = topk[size_t(r) * k + t];
+        if (c < 0) continue;  // fewer than k finite entries
         const size_t self = transposed ? size_t(c) * nvy + r : size_t(r) * nvy + c;
         if (threadIdx.x == 0) allowed[self] = 1;
         for (int j = ptr[c] + threadIdx.x; j < ptr[c + 1]; j += blockDim.x) {

@@ -5,13 +5,16 @@ allocator's fixed pool, or an allocation's hidden synchronisation would stall a
 latency-critical loop. For them the library offers a variant whose temporaries live in a
 fixed, library-owned device array. This file is collected last on purpose; it calls both
 entry points through the C ABI, twice in a row on different shape pairs (so stale scratch
-from the first call would show), and requires identical masks. It also checks that sizes
-beyond the fixed array are refused before any GPU work."""
+from the first call would show), and requires identical masks. It also checks that repeated
+calls leave the device's free memory unchanged (nothing is allocated), that rows and
+columns with fewer than k finite costs give the same masks on both entry points and in the
+oracle, and that sizes beyond the fixed array are refused before any GPU work."""
 import ctypes
 
 import numpy as np
 import pytest
 
+from oracle import problem as P
 from synth import instances as I
 
 pytestmark = pytest.mark.gpu
@@ -75,3 +78,61 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(env):
     rc = L.lib().disco_candidates_noalloc(d.data_ptr(), 20000, 20000, 4, ctypes.byref(big), ctypes.byref(big),
                                           out.data_ptr(), None)
     assert rc == L.DISCO_ERR_INVALID_ARG
+
+
+def test_noalloc_allocates_nothing(env):
+    """After the first call (which resolves the array's address and loads the kernels), more
+    calls leave cudaMemGetInfo's free bytes exactly where they were."""
+    torch, L = env
+    inst = I.config2()
+    nvx, nvy = inst.X.nv, inst.Y.nv
+    d = torch.from_numpy(P.pair_distance(inst.FX, inst.FY).astype(np.float32)).cuda()
+    out = torch.empty((nvx, nvy), dtype=torch.uint8, device="cuda")
+    TX = np.ascontiguousarray(inst.X.T, np.int32)
+    TY = np.ascontiguousarray(inst.Y.T, np.int32)
+    mx = L.disco_mesh(nvx, TX.shape[0], None, TX.ctypes.data)
+    my = L.disco_mesh(nvy, TY.shape[0], None, TY.ctypes.data)
+    lib = L.lib()
+
+    def call():
+        return lib.disco_candidates_noalloc(d.data_ptr(), nvx, nvy, 10, ctypes.byref(mx), ctypes.byref(my),
+                                            out.data_ptr(), None)
+
+    assert call() == L.DISCO_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        assert call() == L.DISCO_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+def test_noalloc_with_non_finite_costs(env):
+    """Costs of +inf or NaN are never ranked: rows and columns with fewer than k finite
+    entries contribute only those, on both entry points and in the oracle (same FP32 costs)."""
+    torch, L = env
+    inst = I.config1()
+    nvx, nvy = inst.X.nv, inst.Y.nv
+    d = P.pair_distance(inst.FX, inst.FY).astype(np.float32)
+    d[0, :] = np.inf          # a row with no finite entry
+    d[1, 3:] = np.nan         # a row with 3 finite entries (k = 4)
+    d[5:, 2] = np.inf         # a column with 5 finite entries
+    k = 4
+    dd = torch.from_numpy(d).cuda()
+    TX = np.ascontiguousarray(inst.X.T, np.int32)
+    TY = np.ascontiguousarray(inst.Y.T, np.int32)
+    mx = L.disco_mesh(nvx, TX.shape[0], None, TX.ctypes.data)
+    my = L.disco_mesh(nvy, TY.shape[0], None, TY.ctypes.data)
+    lib = L.lib()
+    ref = torch.empty((nvx, nvy), dtype=torch.uint8, device="cuda")
+    got = torch.full((nvx, nvy), 7, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    L.check(lib.disco_candidates(dd.data_ptr(), nvx, nvy, k, ctypes.byref(mx), ctypes.byref(my), ref.data_ptr(),
+                                 stream), "candidates")
+    assert lib.disco_candidates_noalloc(dd.data_ptr(), nvx, nvy, k, ctypes.byref(mx), ctypes.byref(my),
+                                        got.data_ptr(), stream) == L.DISCO_OK
+    torch.cuda.synchronize()
+    want = P.candidate_pairs(d.astype(np.float64), k, inst.X.T, inst.Y.T)
+    assert np.array_equal(ref.cpu().numpy().astype(bool), want)
+    assert np.array_equal(got.cpu().numpy().astype(bool), want)
