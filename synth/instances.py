@@ -22,6 +22,9 @@ Workloads (seed = config index XOR pair index):
 * ``config4``  64 uneven pairs (icospheres 80/320/1280 T, tori 96..1536 T),
   64-d features, top-k ~ U{8..24}, 300 iterations each.
 * ``tet``      tetrahedron vs relabelled copy (exhaustive-search size).
+* ``bipyramid_pair(n)``  bipyramid over an n-gon vs relabelled copy, 16-d
+  features, noise 0.05, full product space: high-valence apexes give BDD layers
+  wider than 8 (n = 12: up to 14, n = 16: up to 18).
 """
 from __future__ import annotations
 
@@ -95,6 +98,13 @@ def icosphere_pair(subdiv: int, dim: int, topk: int | None, seed: int, iters: in
     X = M.icosphere(subdiv)
     Y, FX, FY, perm = make_pair(X, rng, dim, 0.05, deform=True)
     return Instance(f"icosphere{subdiv}-{X.nt}T-top{topk}", X, Y, FX, FY, perm, topk, iters)
+
+
+def bipyramid_pair(n: int, seed: int = 11) -> Instance:
+    rng = _rng(seed ^ n)
+    X = M.bipyramid(n)
+    Y, FX, FY, perm = make_pair(X, rng, 16, 0.05)
+    return Instance(f"bipyramid{n}-{X.nt}T-full", X, Y, FX, FY, perm, None, None)
 
 
 def config4(n_pairs: int = 64) -> list[Instance]:

@@ -9,6 +9,8 @@ about 450 faces, Sec. 4 "Datasets"), which are not available here:
 * ``icosphere(s)`` 10*4^s+2 vertices, 20*4^s triangles (s = 2: 162 / 320,
   s = 4: 2562 / 5120)
 * ``torus(n, m)``  n*m vertices, 2*n*m triangles (genus 1)
+* ``bipyramid(n)`` n+2 vertices, 2*n triangles: two apexes of valence n over an
+  n-gon, so the constraint rows around the apexes are long and their BDDs wide
 
 This module holds only geometry generation (no part of the matching method)
 and is shared by the oracle and the CUDA path as the single source of inputs.
@@ -119,6 +121,19 @@ def torus(n: int, m: int, R: float = 1.0, r: float = 0.4) -> Mesh:
             p, q, s, t = idx(a, b), idx(a + 1, b), idx(a + 1, b + 1), idx(a, b + 1)
             T += [(p, q, s), (p, s, t)]
     return Mesh(V.astype(np.float32), np.array(T, dtype=np.int32))
+
+
+def bipyramid(n: int) -> Mesh:
+    """Two apexes (vertices n, n + 1) over a regular n-gon in the z = 0 plane."""
+    assert n >= 3
+    a = 2 * np.pi * np.arange(n) / n
+    V = np.concatenate([np.stack([np.cos(a), np.sin(a), np.zeros(n)], 1), [[0.0, 0.0, 1.0], [0.0, 0.0, -1.0]]])
+    T = []
+    for i in range(n):
+        j = (i + 1) % n
+        T += [(i, j, n), (j, i, n + 1)]
+    T = np.array(T, dtype=np.int64)
+    return Mesh(V.astype(np.float32), _orient_outward(V, T).astype(np.int32))
 
 
 def _real_sph_harm(l: int, mm: int, theta: np.ndarray, phi: np.ndarray) -> np.ndarray:
