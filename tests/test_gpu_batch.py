@@ -65,7 +65,8 @@ def test_batch_matches_single_instances(lib, chunk):
     for (inst, d, a), x, c, lb in zip(pairs, xs, costs, lbs):
         prob = P.build_problem(inst.X.T, inst.Y.T, d, a)
         assert not np.any(prob.residual(x))
-        assert lb <= c + 1e-6 * abs(c)
+        # the GPU bound is the FP64 one to 1e-5 relative (FP32 min-sum), and that is <= OPT <= c
+        assert lb <= c + 1e-5 * abs(c)
     batch.close()
 
 

@@ -70,4 +70,5 @@ def test_three_levels(torch):
     pf = res[-1]["pairs"]
     assert np.mean(fine.perm[pf[:, 0]] == pf[:, 1]) > 0.9
     assert res[-1]["density"] < 0.05
-    assert all(r["lower_bound"] <= r["cost"] + 1e-6 * abs(r["cost"]) for r in res)
+    # bound <= feasible cost, to the bound's own tolerance (1e-5 relative, FP32 min-sum)
+    assert all(r["lower_bound"] <= r["cost"] + 1e-5 * abs(r["cost"]) for r in res)

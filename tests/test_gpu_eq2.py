@@ -53,7 +53,7 @@ def test_eq2_bound_and_primal(torch, which, chunk, iters):
     x, cost, ok = s.primal()
     assert ok and not np.any(prob.residual(x))
     assert cost == pytest.approx(float(prob.cost @ x), rel=1e-6)
-    assert lb <= cost + 1e-6 * abs(cost)
+    assert lb <= cost + 1e-5 * abs(cost)  # the bound's tolerance: 1e-5 relative (FP32 min-sum)
     s.close()
 
 

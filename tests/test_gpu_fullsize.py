@@ -39,7 +39,7 @@ def test_fullsize_properties(setup):
     for _ in range(4):
         s.dual(10)
         lb = s.lower_bound()
-        assert lb >= prev - 1e-6 * abs(lb)
+        assert lb >= prev - 2e-5 * abs(lb)  # two values, each within 1e-5 of a monotone FP64 sequence
         prev = lb
     # alone vs inside a batch with a second pair: same per-lane arithmetic, same bound
     other = I.config2()
@@ -54,7 +54,7 @@ def test_fullsize_properties(setup):
     assert b.lower_bounds()[0] == pytest.approx(s.lower_bound(), rel=1e-12)
     b.close()
     x, cost, ok = s.primal()
-    assert ok and cost >= s.lower_bound() - 1e-6 * abs(cost)
+    assert ok and cost >= s.lower_bound() - 1e-5 * abs(cost)  # the bound's tolerance
     s.close()
 
 
@@ -67,7 +67,7 @@ def test_fullsize_qn_reaches_the_bound(setup):
     na, lba, oka = a.converge(2000)
     nq, lbq, okq = q.converge(2000)
     assert oka and okq
-    assert lbq >= lba - 1e-6 * abs(lba)
+    assert lbq >= lba - 2e-5 * abs(lba)  # two bounds, each within 1e-5 of its FP64 value
     lam, pend = q.get_state()
     assert np.all(np.isfinite(lam)) and np.all(np.isfinite(pend))
     a.close()

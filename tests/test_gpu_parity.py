@@ -176,12 +176,12 @@ def test_bound_is_monotone_and_below_primal(torch):
     for _ in range(10):
         s.dual(10)
         lb = s.lower_bound()
-        assert lb >= prev - 1e-6 * abs(lb)
+        assert lb >= prev - 2e-5 * abs(lb)  # two values, each within LB_RTOL of a monotone FP64 sequence
         prev = lb
     x, cost, ok = s.primal()
     assert ok
     assert not np.any(prob.residual(x))
-    assert prev <= cost + 1e-6 * abs(cost)
+    assert prev <= cost + LB_RTOL * abs(cost)  # FP64 bound <= OPT <= cost; the GPU bound is within LB_RTOL
     s.close()
 
 
