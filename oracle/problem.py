@@ -123,6 +123,24 @@ def closed_one_ring(nv: int, T: np.ndarray) -> np.ndarray:
     return A
 
 
+def nearest_indicators(d: np.ndarray, k: int) -> tuple[np.ndarray, np.ndarray]:
+    """0/1 matrices of the k nearest pairs in each direction (ties to the lower index; only
+    finite costs are ranked): cxy[m, n] = 1 iff n is among the k nearest Y vertices of m,
+    cyx[m, n] = 1 iff m is among the k nearest X vertices of n."""
+    nx, ny = d.shape
+    fin = np.isfinite(d)
+    dr = np.where(fin, d, np.inf)  # non-finite entries sort last and are dropped below
+    cxy = np.zeros((nx, ny), dtype=np.float64)
+    cyx = np.zeros((nx, ny), dtype=np.float64)
+    rows = np.argsort(dr, axis=1, kind="stable")[:, : min(k, ny)]
+    ri = np.broadcast_to(np.arange(nx)[:, None], rows.shape)
+    cxy[ri, rows] = fin[ri, rows]
+    cols = np.argsort(dr, axis=0, kind="stable")[: min(k, nx), :]
+    ci = np.broadcast_to(np.arange(ny)[None, :], cols.shape)
+    cyx[cols, ci] = fin[cols, ci]
+    return cxy, cyx
+
+
 def candidate_pairs(d: np.ndarray, k: int, TX: np.ndarray, TY: np.ndarray) -> np.ndarray:
     """Allowed vertex pairs for the top-k pruned product space.
 
@@ -131,17 +149,8 @@ def candidate_pairs(d: np.ndarray, k: int, TX: np.ndarray, TY: np.ndarray) -> np
     vertices of n (ties to the lower index). Only finite costs are ranked: a row (or
     column) with fewer than k finite entries contributes just those."""
     nx, ny = d.shape
-    fin = np.isfinite(d)
-    dr = np.where(fin, d, np.inf)  # non-finite entries sort last and are dropped below
-    # 0/1 indicator matrices; the products below count ring hits, exact in float64
-    cxy = np.zeros((nx, ny), dtype=np.float64)  # n0 among the k nearest of m
-    cyx = np.zeros((nx, ny), dtype=np.float64)  # m0 among the k nearest of n
-    rows = np.argsort(dr, axis=1, kind="stable")[:, : min(k, ny)]
-    ri = np.broadcast_to(np.arange(nx)[:, None], rows.shape)
-    cxy[ri, rows] = fin[ri, rows]
-    cols = np.argsort(dr, axis=0, kind="stable")[: min(k, nx), :]
-    ci = np.broadcast_to(np.arange(ny)[None, :], cols.shape)
-    cyx[cols, ci] = fin[cols, ci]
+    cxy, cyx = nearest_indicators(d, k)
+    # the products below count ring hits, exact in float64
     AX = closed_one_ring(nx, TX).astype(np.float64)
     AY = closed_one_ring(ny, TY).astype(np.float64)
     return ((cxy @ AY) > 0) | ((AX @ cyx) > 0)

@@ -122,3 +122,26 @@ def test_host_compiler_errors(L):
                                     ctypes.byref(info), None, None, 0, None, 0)
     assert rc == L.DISCO_ERR_INFEASIBLE
     assert b"element" in L.lib().disco_last_error() or b"empty" in L.lib().disco_last_error()
+
+
+@pytest.mark.slow
+def test_host_compiler_matches_oracle_at_full_size(L):
+    """The benchmark workload (5120-triangle icosphere pair, top-16, chunk 32, the default cap
+    of 8 segments per row): product space, presolve fixings, every segment's variables and
+    widths, auxiliary variables and node count, bit for bit (about 75 s of oracle time)."""
+    inst = I.config3()
+    d32 = P.pair_distance(inst.FX, inst.FY).astype(np.float32)
+    allowed = P.candidate_pairs(d32.astype(np.float64), inst.topk, inst.X.T, inst.Y.T)
+    prob = P.build_problem(inst.X.T, inst.Y.T, d32.astype(np.float64), allowed)
+    fixed, const = P.presolve(prob)
+    dec = B.decompose(prob, fixed, const, 32, 8)
+    info, sv, sw, fx = _compile(L, inst, allowed, d32, 32, 8)
+    assert info.nvars == prob.nvars and info.nrows == prob.nrows
+    assert np.array_equal(fx, fixed)
+    assert info.nvars_free == int((fixed < 0).sum())
+    assert info.nvars_aux == dec.nvars_total - dec.nvars
+    assert info.nbdds == dec.nb
+    assert np.array_equal(sv, dec.layer_var)
+    assert np.array_equal(sw, np.diff(dec.layer_node_ptr))
+    assert info.nnodes == dec.n_nodes == 6019316
+    assert info.constant == pytest.approx(const, abs=1e-6)
