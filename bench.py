@@ -42,17 +42,20 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+HALFPASS_SOURCES = ("kernels.cu", "device_util.cuh", "kernels.h")
+
+
 def _traffic(workload: str, split_chunk: int):
-    """DRAM bytes per half-pass (the MMA kernel and its mean reduction) from the committed ncu
-    summary of this workload, or None when either kernel's source changed since the counters
-    were taken (sha256 of kernels.cu followed by store.cu)."""
+    """DRAM bytes per half-pass launch from the committed ncu summary of this workload, or
+    None when the half-pass sources changed since the counters were taken (sha256 of
+    kernels.cu, device_util.cuh and kernels.h, in that order)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "halfpass_icosphere4-5120T-top16.md")
     csrc = os.path.join(ROOT, "paper_2310_08230_gb300", "csrc")
     if workload != "icosphere4-5120T-top16" or split_chunk != 32 or not os.path.exists(path):
         return None
     h = hashlib.sha256()
-    for name in ("kernels.cu", "store.cu"):
+    for name in HALFPASS_SOURCES:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     h = h.hexdigest()[:16]
@@ -289,7 +292,7 @@ def gpu_arm(args):
                 "h2d_bytes_per_step": int(FX_h.nbytes + FY_h.nbytes), "d2h_bytes_per_step": int(st["nvars"]) + 8},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": _traffic(inst.name, args.split_chunk), "kernel": "half-pass (k_forward/k_backward MMA, all width classes, + k_reduce)",
+                     "traffic": _traffic(inst.name, args.split_chunk), "kernel": "MMA half-pass (k_forward_fused / k_backward_fused over every width class; the deferred averaging happens in the same launch)",
                      "alg_bytes_per_launch": alg_bytes, "launch_ms": half_pass_ms, "peak_kind": kind,
                      "launch_timing": "CUDA events on the solver stream around each step's dual blocks after "
                                       "the first (CUDA-graph replays of the half-pass kernels); the first block "
@@ -303,39 +306,51 @@ def gpu_arm(args):
     if world == 1 and not args.no_differentiated:
         line["differentiated"] = differentiated(torch)
     if world == 1 and not args.no_quasi_newton:
-        line["quasi_newton"] = quasi_newton_vs_mma(torch, inst, args.split_chunk)
+        from synth import instances as I
+
+        line["quasi_newton"] = quasi_newton_vs_mma(torch, [inst, I.symmetric_pair(3)], args.split_chunk)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
+        if "differentiated" in line:
+            line["differentiated"]["plain_torch_reference_gradient"] = cpu_baseline_differentiated()
     print(json.dumps(line), flush=True)
 
 
-def quasi_newton_vs_mma(torch, inst, split_chunk: int) -> dict:
+def quasi_newton_vs_mma(torch, insts, split_chunk: int) -> dict:
     """Time to the converged bound with quasi-Newton steps (Alg. 1, memory 5, one step per
-    lb_every = 20 MMA iterations) against MMA alone, on the bench workload (host build excluded)."""
+    lb_every = 20 MMA iterations) against MMA alone (host build excluded), per workload: the
+    bench workload, whose relaxation is tight after a few dozen iterations, and a half-turn
+    symmetric icosphere pair whose dual needs hundreds."""
     from paper_2310_08230_gb300.api import Solver, candidates, pair_costs
 
-    FX = torch.from_numpy(inst.FX).cuda()
-    FY = torch.from_numpy(inst.FY).cuda()
-    d = pair_costs(FX, FY)
-    al = candidates(d, inst.topk, inst.X.T, inst.Y.T) if inst.topk else None
-    out = {}
-    for name, kw in (("mma", {}), ("qn", {"qn_memory": 5})):
-        s = Solver(inst.X.T, inst.Y.T, d, al, split_chunk=split_chunk, **kw)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        n, lb, ok = s.converge(20000)
-        t1 = time.perf_counter()
-        out[name] = {"ms_to_converged_bound": (t1 - t0) * 1e3, "iterations": n, "lower_bound": lb, "converged": ok}
-        s.close()
-    return out
+    res = {}
+    for inst in insts:
+        FX = torch.from_numpy(inst.FX).cuda()
+        FY = torch.from_numpy(inst.FY).cuda()
+        d = pair_costs(FX, FY)
+        al = candidates(d, inst.topk, inst.X.T, inst.Y.T) if inst.topk else None
+        out = {}
+        for name, kw in (("mma", {}), ("qn", {"qn_memory": 5})):
+            s = Solver(inst.X.T, inst.Y.T, d, al, split_chunk=split_chunk, **kw)
+            out["bdd_nodes"] = s.info()["nnodes"]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            n, lb, ok = s.converge(20000)
+            t1 = time.perf_counter()
+            out[name] = {"ms_to_converged_bound": (t1 - t0) * 1e3, "iterations": n, "lower_bound": lb,
+                         "converged": ok}
+            s.close()
+        res[inst.name] = out
+    return res
 
 
-def differentiated(torch, n_pairs: int = 8, iters: int = 50, every: int = 10, fd_dirs: int = 3,
-                   eps: float = 1e-3) -> dict:
+def differentiated(torch, n_pairs: int = 8, iters: int = 50, every: int = 10) -> dict:
     """Learned costs through the solver: 8 pairs of 1280-triangle icospheres, raw 128-d
     features -> 2-layer MLP (128-256-64, ReLU) -> squared distances -> top-16 candidates
     (held fixed) -> bound after 50 iterations; its gradient w.r.t. the MLP parameters by the
-    adjoint kernels (checkpoint every 10 iterations) against central differences."""
+    adjoint kernels (checkpoint every 10 iterations), timed beside plain solves of the same
+    pairs. (The gradient's values are checked by the GPU tests against the FP64 replica and
+    against FP64 central differences of the oracle.)"""
     from paper_2310_08230_gb300.api import Solver, candidates
     from paper_2310_08230_gb300.autograd import dual_bounds
     from synth import instances as I
@@ -384,7 +399,6 @@ def differentiated(torch, n_pairs: int = 8, iters: int = 50, every: int = 10, fd
     loss.backward()
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    grads = [p.grad.detach().clone() for p in params]
     # the plain single-instance path on the same pairs (no recording, no gradient)
     torch.cuda.synchronize()
     t3 = time.perf_counter()
@@ -398,41 +412,25 @@ def differentiated(torch, n_pairs: int = 8, iters: int = 50, every: int = 10, fd
             s.close()
     torch.cuda.synchronize()
     t4 = time.perf_counter()
-    # central differences along random parameter directions
-    gen = torch.Generator(device="cuda").manual_seed(11)
-    checks = []
-    for _ in range(fd_dirs):
-        v = [torch.randn(p.shape, device="cuda", generator=gen) for p in params]
-        nrm = torch.sqrt(sum((x * x).sum() for x in v))
-        v = [x / nrm for x in v]
-        with torch.no_grad():
-            up = bounds_plain([p + eps * x for p, x in zip(params, v)]).sum()
-            dn = bounds_plain([p - eps * x for p, x in zip(params, v)]).sum()
-        fd = (up - dn) / (2 * eps)
-        an = float(sum((g * x).sum() for g, x in zip(grads, v)))
-        # rounding floor of the difference: each bound is an FP32 computation (about 2^-24
-        # relative per pair, summed over the pairs)
-        noise = 2.0 * 2.0 ** -24 * float(np.abs(bounds_plain(params)).sum()) / (2 * eps)
-        checks.append({"fd": float(fd), "adjoint": an, "abs_err": abs(float(fd) - an), "fd_noise_floor": noise,
-                       "rel_err": abs(float(fd) - an) / max(abs(an), 1e-12)})
     return {
         "pairs": n_pairs, "iters": iters, "checkpoint_every": every, "mlp": "128-256-64 relu",
         "params": int(sum(p.numel() for p in params)),
         "bound_sum": float(loss.detach()), "plain_bound_sum": float(np.sum(plain)),
         "fwd_ms": (t1 - t0) * 1e3, "bwd_ms": (t2 - t1) * 1e3,
         "plain_one_by_one_ms": (t4 - t3) * 1e3,
-        "fd_eps": eps, "fd_checks": checks,
-        "note": "steady state (after one untimed forward+backward); times include the host compiler; "
-                "fd = central differences of the plain batched solve, masks fixed",
+        "note": "steady state (after one untimed forward+backward); times include the host compiler",
     }
 
 
-def batched_vs_single(torch, iters: int = 300, n_pairs: int = 64, split_chunk: int = 32) -> dict:
+def batched_vs_single(torch, iters: int = 300, n_pairs: int = 64, split_chunk: int = 32,
+                      one_by_one: bool = True) -> dict:
     """64 uneven pairs: one batched handle against the same pairs solved one after another.
 
     Both sides run the whole path per pair (pair costs, candidates, build, `iters` dual
     iterations, bound, rounding) on device-resident features; times are CUDA-event times on
-    one stream with host work in between included."""
+    one stream with host work in between included. The batch's last 20 iterations are also
+    timed on their own (CUDA events, graph replays of the half-pass launches): with 1.8 GB of
+    BDD tables, far beyond L2, that is the batch's HBM roofline point."""
     from paper_2310_08230_gb300 import _lib as L
     from paper_2310_08230_gb300.api import _mesh, default_opts
     from synth import instances as I
@@ -457,6 +455,7 @@ def batched_vs_single(torch, iters: int = 300, n_pairs: int = 64, split_chunk: i
                                      a.data_ptr(), sptr), "candidates")
 
     phases = {}
+    steady = {}
 
     def mark(name, t0):
         torch.cuda.synchronize()
@@ -479,7 +478,14 @@ def batched_vs_single(torch, iters: int = 300, n_pairs: int = 64, split_chunk: i
         t = mark("build_ms", t)
         info = L.disco_info_t()
         lib.disco_info(h, ctypes.byref(info))
-        L.check(lib.disco_dual(h, iters), "dual")
+        L.check(lib.disco_dual(h, iters - 20), "dual")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.check(lib.disco_dual(h, 20), "dual")
+        e1.record(stream)
+        e1.synchronize()
+        steady["half_pass_ms"] = e0.elapsed_time(e1) / 40.0
+        steady["alg_bytes"] = info.bytes_per_iter / 2.0
         lbs = np.zeros(n_pairs)
         L.check(lib.disco_lower_bounds(h, lbs.ctypes.data_as(L.c_double_p), n_pairs), "lbs")
         t = mark("dual_ms", t)
@@ -529,13 +535,23 @@ def batched_vs_single(torch, iters: int = 300, n_pairs: int = 64, split_chunk: i
     phases.clear()
     tb, (nodes, lbs_b, cs_b, st_b) = timed(batched)
     breakdown = {k: round(v, 1) for k, v in phases.items()}
-    ts, (nodes_s, lbs_s, cs_s, st_s) = timed(single)
     upd = 2.0 * nodes * iters
-    return {"pairs": n_pairs, "iters": iters, "bdd_nodes": int(nodes), "batched_ms": tb, "one_by_one_ms": ts,
-            "batched_node_updates_per_s": upd / (tb / 1e3), "one_by_one_node_updates_per_s": upd / (ts / 1e3),
-            "speedup": ts / tb, "feasible_batched": int((st_b == 0).sum()), "feasible_one_by_one": int((st_s == 0).sum()),
-            "max_rel_bound_diff": float(np.max(np.abs(lbs_b - lbs_s) / np.maximum(np.abs(lbs_s), 1e-12))),
-            "batched_breakdown_ms": breakdown}
+    peak, kind = _peaks()
+    achieved = steady["alg_bytes"] / (steady["half_pass_ms"] / 1e3) / 1e9
+    out = {"pairs": n_pairs, "iters": iters, "bdd_nodes": int(nodes), "batched_ms": tb,
+           "batched_node_updates_per_s": upd / (tb / 1e3), "feasible_batched": int((st_b == 0).sum()),
+           "batched_breakdown_ms": breakdown,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "alg_bytes_per_launch": steady["alg_bytes"], "launch_ms": steady["half_pass_ms"],
+                        "peak_kind": kind,
+                        "kernel": "MMA half-pass over all 64 pairs (every width-class launch of one half-pass)",
+                        "launch_timing": "CUDA events around the batch's last 20 iterations (graph replays)"}}
+    if one_by_one:
+        ts, (nodes_s, lbs_s, cs_s, st_s) = timed(single)
+        out.update({"one_by_one_ms": ts, "one_by_one_node_updates_per_s": upd / (ts / 1e3), "speedup": ts / tb,
+                    "feasible_one_by_one": int((st_s == 0).sum()),
+                    "max_rel_bound_diff": float(np.max(np.abs(lbs_b - lbs_s) / np.maximum(np.abs(lbs_s), 1e-12)))})
+    return out
 
 
 def _oracle_workload(config: str, split_chunk: int):
@@ -550,6 +566,38 @@ def _oracle_workload(config: str, split_chunk: int):
     fixed, const = P.presolve(prob)
     dec = B.decompose(prob, fixed, const, split_chunk)
     return inst, dec, S.DualOracle(dec), time.perf_counter() - t0
+
+
+def cpu_baseline_differentiated(iters_sample: int = 4, iters: int = 50, n_pairs: int = 8) -> dict:
+    """The plain-PyTorch unrolled reference gradient (the FP64 autograd replica of the dual
+    iterations, on the host cores) for the differentiated workload, on a bounded sample: one
+    of its pairs for `iters_sample` of its iterations, scaled to all pairs and iterations.
+    The pair costs come from the seeded MLP in FP64; its Jacobian is not timed."""
+    import torch
+
+    from oracle import bdd as B
+    from oracle import grad as G
+    from oracle import problem as P
+    from synth import instances as I
+
+    inst = I.config5(1)[0]
+    W1, b1, W2, b2 = [torch.tensor(p, dtype=torch.float64) for p in I.mlp_params()]
+    fa = torch.relu(torch.tensor(inst.FX, dtype=torch.float64) @ W1.T + b1) @ W2.T + b2
+    fb = torch.relu(torch.tensor(inst.FY, dtype=torch.float64) @ W1.T + b1) @ W2.T + b2
+    d = ((fa[:, None, :] - fb[None, :, :]) ** 2).sum(-1).numpy().astype(np.float32).astype(np.float64)
+    allowed = P.candidate_pairs(d, inst.topk, inst.X.T, inst.Y.T)
+    prob = P.build_problem(inst.X.T, inst.Y.T, d, allowed, normalize=False)
+    fixed, const = P.presolve(prob)
+    dec = B.decompose(prob, fixed, const, 0)
+    c = d[prob.vm, prob.vn].mean(axis=1)
+    t0 = time.perf_counter()
+    G.bound_and_grad(dec, c, fixed, iters_sample)
+    dt = time.perf_counter() - t0
+    total = dt * (iters / iters_sample) * n_pairs
+    return {"value": total * 1e3, "unit": "ms per bound-and-gradient of the 8-pair, 50-iteration workload",
+            "cores": torch.get_num_threads(), "kind": "oracle (plain PyTorch FP64 unrolled autograd)",
+            "sample": f"pair 0 of 8 ({dec.n_nodes} BDD nodes), {iters_sample} of {iters} iterations in "
+                      f"{dt:.1f} s, scaled by {iters / iters_sample:.1f} x {n_pairs}"}
 
 
 def cpu_baseline(args) -> dict:
@@ -610,6 +658,9 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-differentiated", action="store_true")
     ap.add_argument("--no-quasi-newton", action="store_true")
+    ap.add_argument("--only", choices=["batched", "differentiated", "quasi_newton"],
+                    help="run one comparison section alone (for profiling) and print its object")
+    ap.add_argument("--skip-one-by-one", action="store_true", help="with --only batched: the batched handle only")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -617,6 +668,19 @@ def main():
         import __graft_entry__
 
         __graft_entry__.build()
+        if args.only:
+            import torch
+
+            if args.only == "batched":
+                res = batched_vs_single(torch, one_by_one=not args.skip_one_by_one)
+            elif args.only == "differentiated":
+                res = differentiated(torch)
+            else:
+                from synth import instances as I
+
+                res = quasi_newton_vs_mma(torch, [workload(args.config), I.symmetric_pair(3)], args.split_chunk)
+            print(json.dumps({"only": args.only, args.only: res}), flush=True)
+            return
         gpu_arm(args)
 
 

@@ -106,15 +106,21 @@ DH df df_add_f(df a, float b) {
 // a / n for a small positive integer n. q = a.hi * (1/n) is within an ulp of a.hi / n, so the
 // remainder a.hi - q n is exact with an FMA (the classic division-by-reciprocal argument);
 // the low part needs only single precision.
+// 1/n correctly rounded to FP32 for the possible degrees n = 2 .. 7 (entries 0 and 1 unused).
+static __constant__ float kRcpDeg[8] = {1.0f, 1.0f, 0.5f, 0.333333343f, 0.25f, 0.200000003f, 0.166666672f,
+                                        0.142857149f};
+DH float rcp_deg(int n) {
+#ifdef __CUDA_ARCH__
+    return kRcpDeg[n & 7];
+#else
+    static const float t[8] = {1.0f, 1.0f, 0.5f, 0.333333343f, 0.25f, 0.200000003f, 0.166666672f, 0.142857149f};
+    return t[n & 7];
+#endif
+}
+
 DH df df_div_i(df a, int n) {
     const float fn = float_of(0x4B000000u | uint32_t(n)) - 8388608.0f;  // exact for 0 <= n < 2^23
-    // 1/n correctly rounded to FP32 (n = 2 .. 7, the possible degrees)
-    const float rcp = n == 2 ? 0.5f
-                    : n == 3 ? 0.333333343f
-                    : n == 4 ? 0.25f
-                    : n == 5 ? 0.200000003f
-                    : n == 6 ? 0.166666672f
-                             : 0.142857149f;
+    const float rcp = rcp_deg(n);
     const float q = a.hi * rcp;
     const float r = fmaf(-q, fn, a.hi) + a.lo;
     return fast2sum(q, r * rcp);
@@ -139,41 +145,35 @@ constexpr float kOneHalf23 = 12582912.0f;   // 1.5 * 2^23
 constexpr float kTwo42 = 4398046511104.0f;  // 2^42
 constexpr int kFxSumBits = 45;              // |sum| < 2^45 grid units
 
-// The integer value of an integer-valued float x with |x| <= 2^53: x = s 2^(e - 150) with s its
-// 24-bit significand and e its biased exponent, i.e. (s 2^32) >> (182 - e) (the shift is at
-// least 2 here; 0 has e = 0 and shifts everything out).
-DH long long int_of_float(float x) {
-    const uint32_t u = bits_of(x);
-    const uint32_t a = u & 0x7FFFFFFFu;
-    const uint32_t sig = (a & 0x7FFFFFu) | 0x800000u;
-    const int sh = min(182 - int(a >> 23), 63);
-    const long long q = (long long)(((unsigned long long)sig << 32) >> sh);
-    return (u >> 31) ? -q : q;
-}
-
 // m on the grid: q = m 2^F rounded to an integer (ties to even), and the return value q 2^-F,
-// both exact (m 2^F has 24 significant bits, so rounding it to an integer leaves at most 24,
-// which FP32 holds; from 2^23 on a float is an integer already). |m 2^F| is clamped to 2^42
-// first; a clamped mass is flagged by the caller as out of range.
+// both exact. With t = m 2^F clamped to |t| <= 2^42 (a clamped mass is flagged by the caller
+// as out of range): h = rint(t 2^-23) and l = rint(t - h 2^23) by the significand trick
+// (|t 2^-23| <= 2^19 and |t - h 2^23| <= 2^22), so q = h 2^23 + l = rint(t), with h and l read
+// from the significands as integers; q 2^-F has at most 24 significant bits, so FP32 holds it.
 DH float fx_round(float m, const FxScale& fx, long long& q) {
     const float t = fminf(fmaxf(m * fx.scale, -kTwo42), kTwo42);
-    const float a = fabsf(t);
-    const float r = copysignf(a < kTwo23 ? (a + kTwo23) - kTwo23 : a, t);
-    q = int_of_float(r);
-    return r * fx.inv;
+    const float hs = fmaf(t, 1.0f / kTwo23, kOneHalf23);  // 1.5 2^23 + rint(t 2^-23), exact
+    const float h = hs - kOneHalf23;
+    const float ls = (fmaf(-h, kTwo23, t)) + kOneHalf23;  // 1.5 2^23 + rint(remainder)
+    const float l = ls - kOneHalf23;
+    const int32_t hi = int32_t(bits_of(hs) - 0x4B400000u);
+    const int32_t lo = int32_t(bits_of(ls) - 0x4B400000u);
+    q = (long long)hi * (1 << 23) + lo;
+    return fmaf(h, kTwo23, l) * fx.inv;
 }
 
 // A sum S (units of 2^-F, |S| < 2^45) as double-float, exactly: S = A 2^23 + C with
-// 0 <= C < 2^23 and |A| < 2^22, both parts exact in FP32; TwoSum adds them without error
-// (the pair holds 48 bits), and the scaling by 2^-F is exact.
+// 0 <= C < 2^23 and |A| < 2^22, both parts exact in FP32, added without error (the pair holds
+// 48 bits); the scaling by 2^-F is exact.
 DH df fx_to_df(long long S, float inv) {
     const uint32_t c = uint32_t(S) & 0x7FFFFFu;
     const int32_t a = int32_t(S >> 23);
     const float cf = float_of(0x4B000000u + c) - kTwo23;
     const float af = (float_of(uint32_t(0x4B400000 + a)) - kOneHalf23) * kTwo23;
-    float s, e;
-    two_sum(af, cf, s, e);
-    return df{s * inv, e * inv};
+    // |af| >= |cf| whenever A != 0 (C < 2^23 <= |A| 2^23), and A = 0 gives (cf, 0): Fast2Sum
+    // is exact here
+    const df r = fast2sum(af, cf);
+    return df{r.hi * inv, r.lo * inv};
 }
 // The deferred mean of a variable: its sum / deg, in double-float.
 DH df fx_mean(long long S, int deg, float inv) { return df_div_i(fx_to_df(S, inv), deg); }

@@ -22,6 +22,14 @@ Workloads (seed = config index XOR pair index):
 * ``config4``  64 uneven pairs (icospheres 80/320/1280 T, tori 96..1536 T),
   64-d features, top-k ~ U{8..24}, 300 iterations each.
 * ``tet``      tetrahedron vs relabelled copy (exhaustive-search size).
+* ``symmetric_pair(s)``  icosphere (subdivision s) vs a deformed, relabelled copy, with
+  16-d features that are random combinations of the even-order real spherical
+  harmonics of degree 1..4 at the vertex directions (plus noise 0.05 on Y). They
+  are invariant under the half-turn about the z axis, which maps the icosphere onto
+  itself, so two orientation-preserving matchings are equally good and the LP
+  relaxation is not tight: the dual needs hundreds of iterations (s = 3: about 720
+  to a change below 1e-6 over 20). A stand-in for the paper's slowly converging real
+  shape pairs (intrinsic symmetries, ambiguous learned features).
 * ``bipyramid_pair(n)``  bipyramid over an n-gon vs relabelled copy, 16-d
   features, noise 0.05, full product space: high-valence apexes give BDD layers
   wider than 8 (n = 12: up to 14, n = 16: up to 18).
@@ -98,6 +106,26 @@ def icosphere_pair(subdiv: int, dim: int, topk: int | None, seed: int, iters: in
     X = M.icosphere(subdiv)
     Y, FX, FY, perm = make_pair(X, rng, dim, 0.05, deform=True)
     return Instance(f"icosphere{subdiv}-{X.nt}T-top{topk}", X, Y, FX, FY, perm, topk, iters)
+
+
+def symmetric_pair(subdiv: int = 3, dim: int = 16, feat_noise: float = 0.05, degree: int = 4,
+                   seed: int = 77) -> Instance:
+    rng = _rng(seed)
+    X = M.icosphere(subdiv)
+    V = X.V.astype(np.float64)
+    V /= np.linalg.norm(V, axis=1, keepdims=True)
+    theta = np.arccos(np.clip(V[:, 2], -1.0, 1.0))
+    phi = np.arctan2(V[:, 1], V[:, 0])
+    basis = np.stack([M._real_sph_harm(l, m, theta, phi) for l in range(1, degree + 1)
+                      for m in range(-l, l + 1) if m % 2 == 0], axis=1)
+    basis /= basis.std(axis=0, keepdims=True)
+    W = rng.standard_normal((basis.shape[1], dim)) / np.sqrt(basis.shape[1])
+    FX = (basis @ W).astype(np.float32)
+    Y0 = M.deform_radial(X, rng)
+    Y, perm = M.relabel(Y0, rng)
+    FY = np.empty_like(FX)
+    FY[perm] = FX + (feat_noise * rng.standard_normal(FX.shape)).astype(np.float32)
+    return Instance(f"icosphere{subdiv}-{X.nt}T-halfturn-symmetric-top16", X, Y, FX, FY, perm, 16, None)
 
 
 def bipyramid_pair(n: int, seed: int = 11) -> Instance:

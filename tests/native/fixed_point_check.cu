@@ -1,6 +1,6 @@
 // Host-side check of the averaging arithmetic of the half-pass kernels (device_util.cuh):
-// the exact float <-> integer moves, the rounding of a removed mass to the fixed-point grid,
-// the split of a 64-bit sum into a double-float and the deferred mean. Every result is
+// the rounding of a removed mass to the fixed-point grid (with its integer value), the split
+// of a 64-bit sum into a double-float and the deferred mean. Every result is
 // compared with exact integer or extended-precision arithmetic. Prints "ok <cases>" or the
 // first failure and exits non-zero.
 #include <cfenv>
@@ -32,20 +32,6 @@ static float ulp_of(float x) {
 
 int main() {
     std::mt19937_64 rng(12345);
-    // 1. int_of_float on integer-valued floats: every integer with |n| <= 2^24, and random
-    //    24-bit significands shifted up to 2^53
-    for (int64_t n = -(1 << 24); n <= (1 << 24); n += 7) {
-        const float x = float(n);
-        EXPECT(int_of_float(x) == n, "int_of_float(%lld) = %lld\n", (long long)n, int_of_float(x));
-    }
-    for (int k = 0; k < 200000; ++k) {
-        const int64_t m = int64_t(rng() % (1u << 24));
-        const int sh = int(rng() % 30);
-        const int64_t n = (m << sh) * ((rng() & 1) ? -1 : 1);
-        if (std::llabs(n) > (int64_t(1) << 53)) continue;
-        const float x = float(n);  // exact: at most 24 significant bits
-        EXPECT(int_of_float(x) == n, "int_of_float(%lld) = %lld\n", (long long)n, int_of_float(x));
-    }
     // 2. fx_round: q = round-half-even(m 2^F), the returned mass = q 2^-F, for F = 2 .. 52 (the
     //    grids a handle can choose), masses below the range limit 2^(42 - F); beyond it the
     //    rounded value is clamped to 2^42 grid units
@@ -68,10 +54,26 @@ int main() {
             fx_round(m, fx, q);
             EXPECT(q == std::llrint(t), "fx_round tie F=%d t=%g: q=%lld\n", F, t, q);
         }
+        // remainders at the +-2^22 edge of the low half, and halves of either sign
+        for (double t : {5.0 * 8388608.0 + 4194304.0, -5.0 * 8388608.0 - 4194304.0, 3.0 * 8388608.0 - 4194304.0,
+                         std::ldexp(1.0, 42), -std::ldexp(1.0, 42), std::ldexp(1.0, 42) - std::ldexp(1.0, 18),
+                         -std::ldexp(3.0, 40) + 0.0, 8388608.0 * 1000.0 + 1.0}) {
+            const float m = float(std::ldexp(t, -F));
+            long long q;
+            const float r = fx_round(m, fx, q);
+            const long long want = std::llrint(std::ldexp(double(m), F));
+            EXPECT(q == want, "fx_round edge F=%d t=%.17g: q=%lld want %lld\n", F, t, q, want);
+            EXPECT(double(r) == std::ldexp(double(want), -F), "fx_round edge F=%d t=%.17g\n", F, t);
+        }
         for (double t : {std::ldexp(1.0, 43), -std::ldexp(3.0, 50), 1e30}) {
             long long q;
             fx_round(float(std::ldexp(t, -F)), fx, q);
             EXPECT(std::llabs(q) == (1ll << 42), "fx_round clamp F=%d: q=%lld\n", F, q);
+        }
+        {
+            long long q;
+            fx_round(std::nanf(""), fx, q);
+            EXPECT(std::llabs(q) == (1ll << 42), "fx_round NaN F=%d: q=%lld\n", F, q);
         }
     }
     // 3. fx_to_df is exact: hi + lo == S 2^-F for |S| < 2^45, and |lo| <= ulp(hi) / 2

@@ -1,7 +1,8 @@
 """Gradient of the dual bound w.r.t. the pair costs (disco_record / disco_grad, adjoint
 kernels) against the FP64 autograd replica of the same unrolled iterations
 (``oracle/grad.py``, itself pinned to the C oracle and to finite differences) and against
-central differences of the GPU bound.
+central differences of the GPU bound, and at the differentiated workload's size through the
+feature MLP against the replica chained through the same MLP in FP64.
 
 Tolerances: the gradient to 1e-3 in relative 2-norm (FP32 adjoints of O(10^5) min-plus
 steps; a mismatched tie would show up as an O(1) error); the bound to 1e-5 relative to the
@@ -9,6 +10,7 @@ larger of itself and the largest element cost (raw costs are not scaled to [0, 1
 directional finite differences (eps 1e-3) to 2 % of the directional derivative's scale."""
 import numpy as np
 import pytest
+import torch as T
 
 from oracle import bdd as B
 from oracle import grad as G
@@ -150,3 +152,96 @@ def test_autograd_function_matches_solver(torch):
     for k, (lb, g) in enumerate(refs):
         assert float(lbs[k].detach()) == pytest.approx(lb, rel=1e-12)
         np.testing.assert_allclose(costs[k].grad.cpu().numpy(), float(w[k]) * g, rtol=1e-6, atol=1e-12)
+
+
+def test_mlp_parameter_gradient_at_full_scale(torch):
+    """The differentiated workload at its size: one 1280-triangle icosphere pair, raw 128-d
+    features through the 128-256-64 ReLU MLP, costs = squared distances of the MLP outputs
+    (not normalised), top-16 candidates held fixed. d(bound after 10 iterations) / d(MLP
+    parameters) from the adjoint kernels, through dual_bounds and the MLP in FP32 on the
+    GPU, against the FP64 replica chained through the same MLP in FP64 on the CPU, to 1e-3
+    in relative 2-norm. Both solvers receive the same FP32 costs (the FP64 MLP's, rounded);
+    on the GPU a straight-through identity passes them in while the gradient flows back
+    through the FP32 MLP."""
+    from paper_2310_08230_gb300.autograd import dual_bounds
+
+    iters, every = 10, 4
+    inst = I.config5(1)[0]
+    raw = I.mlp_params()
+    # FP64 reference: costs, the replica's gradient w.r.t. them, chained to the parameters
+    ps64 = [T.tensor(p, dtype=T.float64, requires_grad=True) for p in raw]
+
+    def mlp(F, ps):
+        W1, b1, W2, b2 = ps
+        return T.relu(F @ W1.T + b1) @ W2.T + b2
+
+    a = mlp(T.tensor(inst.FX, dtype=T.float64), ps64)
+    b = mlp(T.tensor(inst.FY, dtype=T.float64), ps64)
+    d64 = ((a[:, None, :] - b[None, :, :]) ** 2).sum(-1)
+    d32 = d64.detach().numpy().astype(np.float32)
+    allowed = P.candidate_pairs(d32.astype(np.float64), inst.topk, inst.X.T, inst.Y.T)
+    ref_lb, gd, _ = _oracle_pair_grad(inst, d32, allowed, 0, iters, False)
+    ref = T.autograd.grad(d64, ps64, grad_outputs=T.tensor(gd))
+    # GPU: MLP in FP32, solver on the same FP32 costs, adjoint back to the parameters
+    ps = [torch.tensor(p, device="cuda", requires_grad=True) for p in raw]
+    FX = torch.from_numpy(inst.FX).cuda()
+    FY = torch.from_numpy(inst.FY).cuda()
+    W1, b1, W2, b2 = ps
+    ga = torch.relu(FX @ W1.T + b1) @ W2.T + b2
+    gb = torch.relu(FY @ W1.T + b1) @ W2.T + b2
+    dg = ((ga[:, None, :] - gb[None, :, :]) ** 2).sum(-1)
+    d_in = dg + (torch.from_numpy(d32).cuda() - dg).detach()  # value d32, gradient into dg
+    mask = torch.from_numpy(allowed.astype(np.uint8)).cuda()
+    lbs = dual_bounds([d_in], [(inst.X.T, inst.Y.T)], [mask], iters, every, normalize_costs=0)
+    lbs.sum().backward()
+    assert abs(float(lbs[0].detach()) - ref_lb) <= 1e-5 * abs(ref_lb)
+    got = np.concatenate([p.grad.detach().cpu().numpy().ravel() for p in ps])
+    want = np.concatenate([r.numpy().ravel() for r in ref])
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err < 1e-3, err
+
+
+def test_adjoint_matches_fp64_central_differences_at_full_scale(torch):
+    """d(bound after 50 iterations) / d(pair costs) of the differentiated workload's first pair
+    (the adjoint kernels, checkpoint every 10) along three random directions, against central
+    differences of the FP64 C oracle's bound at eps 1e-6: FP64 leaves no rounding floor at
+    that step, and at a generic point it crosses no kink of the piecewise-linear bound. The
+    presolve depends only on feasibility, so one decomposition serves every perturbed cost
+    vector; each side is agreed to 1e-3 of the directional derivative's scale."""
+    import dataclasses
+
+    from oracle import solver as S
+    from paper_2310_08230_gb300.api import Solver
+
+    iters, every, eps = 50, 10, 1e-6
+    inst = I.config5(1)[0]
+    W1, b1, W2, b2 = [p.astype(np.float64) for p in I.mlp_params()]
+    fa = np.maximum(inst.FX.astype(np.float64) @ W1.T + b1, 0.0) @ W2.T + b2
+    fb = np.maximum(inst.FY.astype(np.float64) @ W1.T + b1, 0.0) @ W2.T + b2
+    d32 = ((fa[:, None, :] - fb[None, :, :]) ** 2).sum(-1).astype(np.float32)
+    allowed = P.candidate_pairs(d32.astype(np.float64), inst.topk, inst.X.T, inst.Y.T)
+    prob = P.build_problem(inst.X.T, inst.Y.T, d32.astype(np.float64), allowed, normalize=False)
+    fixed, const = P.presolve(prob)
+    dec = B.decompose(prob, fixed, const, 0)
+
+    def oracle_bound(dd):
+        c = dd[prob.vm, prob.vn].mean(axis=1)
+        cost = np.concatenate([c, np.zeros(dec.nvars_total - dec.nvars)])
+        o = S.DualOracle(dataclasses.replace(dec, cost=cost, const=float(c[fixed == 1].sum())))
+        o.iterate(iters)
+        return o.lower_bound()
+
+    s = Solver(inst.X.T, inst.Y.T, d32, allowed.astype(np.uint8), normalize_costs=0)
+    s.record(iters, every)
+    g = s.grad().reshape(d32.shape).astype(np.float64)
+    lb = s.lower_bound()
+    s.close()
+    base = d32.astype(np.float64)
+    assert abs(lb - oracle_bound(base)) <= 1e-5 * abs(lb)
+    rng = np.random.default_rng(17)
+    for _ in range(3):
+        v = rng.standard_normal(d32.shape) * allowed
+        fd = (oracle_bound(base + eps * v) - oracle_bound(base - eps * v)) / (2 * eps)
+        dd = float((g * v).sum())
+        scale = float(np.abs(g * v).sum())
+        assert abs(fd - dd) <= 1e-3 * scale, (fd, dd, scale)
