@@ -146,3 +146,32 @@ def test_tile_order_on_a_single_pair(lib):
     assert ok1 and ok2
     np.testing.assert_array_equal(x2, x1)
     assert c2 == pytest.approx(c1, rel=1e-12)
+
+
+def test_sixteen_pair_batch_runs_clean(lib):
+    """The first 16 pairs of the uneven batch (about 111 M nodes, 102 k tiles, rows up to 587
+    layers), the shape on which an ncu capture once ended with LaunchFailed: 300 iterations,
+    bounds and rounding with every return code OK and the device status word clear. Built
+    with DISCO_BOUNDS_CHECK=1, the same test also checks every index of the half-pass kernels
+    (a failing check would surface as DISCO_ERR_INTERNAL)."""
+    import torch
+
+    from paper_2310_08230_gb300.api import candidates, pair_costs
+
+    Solver = lib
+    insts = I.config4(16)
+    pairs = []
+    for i in insts:
+        d = pair_costs(torch.from_numpy(i.FX).cuda(), torch.from_numpy(i.FY).cuda())
+        a = candidates(d, i.topk, i.X.T, i.Y.T)
+        pairs.append((i.X.T, i.Y.T, d.cpu().numpy(), a.cpu().numpy()))
+    s = Solver.batch(pairs, split_chunk=32)
+    info = s.info()
+    assert info["nnodes"] > 100_000_000 and info["ntiles"] > 100_000
+    s.dual(300)
+    lbs = s.lower_bounds()  # raises on a status bit
+    assert np.all(np.isfinite(lbs))
+    xs, costs, ok = s.primal_batch()
+    assert ok.all()
+    assert np.all(lbs <= costs + 1e-5 * np.abs(costs))
+    s.close()
