@@ -799,8 +799,20 @@ int run_iterations(disco_handle* h, int iters) {
     }
     const int G = h->opts.graph_iters;
     if (G > 0 && (h->tuned || !h->opts.autotune)) {
+        // the first time a block is replayed, the graphs of all three starting phases are
+        // captured together (capturing runs nothing), so that no later call pays for one
+        if (!h->graph_failed && iters - t >= G && !h->iter_graph[h->phase]) {
+            const int ph0 = h->phase;
+            for (int q = 0; q < 3 && !h->graph_failed; ++q) {
+                h->phase = (ph0 + q) % 3;
+                if (!h->iter_graph[h->phase] && (rc = capture_iterations(h))) {
+                    h->phase = ph0;
+                    return rc;
+                }
+            }
+            h->phase = ph0;
+        }
         while (!h->graph_failed && iters - t >= G) {
-            if (!h->iter_graph[h->phase] && (rc = capture_iterations(h))) return rc;
             if (!h->iter_graph[h->phase]) break;
             CK(cudaGraphLaunch(h->iter_graph[h->phase], h->stream));
             g_launches.fetch_add(h->graph_launches[h->phase], std::memory_order_relaxed);
