@@ -182,11 +182,10 @@ def gpu_arm(args):
 
     def step(e2e: bool, stats: dict):
         t0 = time.perf_counter()
-        with torch.cuda.stream(stream):
-            if e2e:
-                FX.copy_(FX_pin, non_blocking=True)
-                FY.copy_(FY_pin, non_blocking=True)
-        L.check(lib.disco_pair_costs(FX.data_ptr(), FY.data_ptr(), nvx, nvy, dim, d.data_ptr(), sptr), "pair_costs")
+        # end to end: the features go in as pinned host buffers through the C ABI (the
+        # library copies them to the device); otherwise they are resident in HBM
+        fx, fy = (FX_pin, FY_pin) if e2e else (FX, FY)
+        L.check(lib.disco_pair_costs(fx.data_ptr(), fy.data_ptr(), nvx, nvy, dim, d.data_ptr(), sptr), "pair_costs")
         L.check(lib.disco_candidates(d.data_ptr(), nvx, nvy, inst.topk, ctypes.byref(mx), ctypes.byref(my),
                                      allowed.data_ptr(), sptr), "candidates")
         t1 = time.perf_counter()

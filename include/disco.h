@@ -133,8 +133,10 @@ int disco_default_opts(disco_opts *opts);
 
 /*
  * Pair costs (Eq. 2 variant used by the workloads): d[m*nvy + n] = (1/dim) * sum_k
- * (FX[m,k] - FY[n,k])^2, FP32. FX: nvx*dim, FY: nvy*dim, d: nvx*nvy, all DEVICE pointers.
- * Asynchronous on `stream` (cudaStream_t, NULL = legacy default stream).
+ * (FX[m,k] - FY[n,k])^2, FP32. FX: nvx*dim and FY: nvy*dim, host or device (host arrays are
+ * copied in on `stream` through a buffer from the library's device pool; pinned host memory
+ * makes the copy asynchronous); d: nvx*nvy, a DEVICE pointer. Asynchronous on `stream`
+ * (cudaStream_t, NULL = legacy default stream). Errors: INVALID_ARG, CUDA.
  */
 int disco_pair_costs(const float *FX, const float *FY, int32_t nvx, int32_t nvy, int32_t dim,
                      float *d, void *stream);

@@ -83,6 +83,10 @@ struct disco_handle {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // the width groups after the first run on `side`, concurrently with the first (a fork /
+    // join per pass; captured into the iteration graphs as a parallel branch)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // averaging state (kernels.h, KArgs): three rotating buffers of one fixed-point sum per
     // variable. msum[phase] is the buffer the next update pass writes (all zero between
     // passes), msum[(phase + 2) % 3] holds the current state (the sums of the last update
@@ -229,10 +233,21 @@ struct disco_handle {
         return a;
     }
 
-    // One pass over every width class (an update pass moves the averaging phase on).
+    // One pass over every width class (an update pass moves the averaging phase on). The
+    // groups touch disjoint tiles, slots and per-variable entries and share only commuting
+    // integer atomics, so they run concurrently and the results do not depend on it.
     int pass(Pass p) {
         const bool bwd = p == Pass::BwdMMA || p == Pass::BwdMMARound || p == Pass::BwdMM || p == Pass::BwdReset;
-        for (const WidthClass& c : classes) CK(launch_pass(p, c.W, args(c, bwd), stream, geometry));
+        if (classes.size() > 1 && side) {
+            CK(cudaEventRecord(ev_fork, stream));
+            CK(cudaStreamWaitEvent(side, ev_fork, 0));
+            CK(launch_pass(p, classes[0].W, args(classes[0], bwd), stream, geometry));
+            for (size_t c = 1; c < classes.size(); ++c) CK(launch_pass(p, classes[c].W, args(classes[c], bwd), side, geometry));
+            CK(cudaEventRecord(ev_join, side));
+            CK(cudaStreamWaitEvent(stream, ev_join, 0));
+        } else {
+            for (const WidthClass& c : classes) CK(launch_pass(p, c.W, args(c, bwd), stream, geometry));
+        }
         if (p == Pass::FwdMMA || p == Pass::BwdMMA || p == Pass::FwdMMARound || p == Pass::BwdMMARound)
             phase = (phase + 1) % 3;
         return DISCO_OK;
@@ -270,6 +285,12 @@ struct disco_handle {
         if (h_counters) cudaFreeHost(h_counters);
         if (h_scalar) cudaFreeHost(h_scalar);
         if (h_status) cudaFreeHost(h_status);
+        if (side) {
+            cudaStreamSynchronize(side);
+            cudaStreamDestroy(side);
+        }
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
         if (qn_hpart) cudaFreeHost(qn_hpart);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
@@ -540,6 +561,11 @@ int upload(disco_handle* h) {
     h->ntiles = int64_t(tiles.size());
     h->nslots_tile = slot_base;
     h->nnodes_tile = node_base;
+    if (h->classes.size() > 1) {
+        CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    }
     // backward order (locality only): inside each launch group, the runs of tiles of one block
     // in reverse order, each run's tiles (longest first) kept in order
     std::vector<TileInfo> tiles_bwd;
@@ -909,22 +935,60 @@ const char* disco_last_error(void) { return g_last_error.c_str(); }
 
 int64_t disco_kernel_launches(void) { return g_launches.load(); }
 
-int disco_pair_costs(const float* FX, const float* FY, int32_t nvx, int32_t nvy, int32_t dim, float* d, void* stream) {
-    if (!FX || !FY || !d || nvx <= 0 || nvy <= 0 || dim <= 0) return fail(DISCO_ERR_INVALID_ARG, "pair_costs: bad arguments");
-    if (!is_device_ptr(FX) || !is_device_ptr(FY) || !is_device_ptr(d))
-        return fail(DISCO_ERR_INVALID_ARG, "pair_costs: FX, FY and d must be device pointers");
-    CK(launch_pair_costs(FX, FY, nvx, nvy, dim, d, static_cast<cudaStream_t>(stream)));
+}  // extern "C"
+
+namespace {
+
+// Pair costs (norm = false) or distances (norm = true) from features that may be host or
+// device arrays: host arrays are staged through one stream-ordered device buffer from the
+// library's pool (returned to it on the same stream).
+int pair_kernel(const char* what, const float* FX, const float* FY, int32_t nvx, int32_t nvy, int32_t dim, float* d,
+                void* stream, bool norm) {
+    if (!FX || !FY || !d || nvx <= 0 || nvy <= 0 || dim <= 0) return fail(DISCO_ERR_INVALID_ARG, std::string(what) + ": bad arguments");
+    if (!is_device_ptr(d)) return fail(DISCO_ERR_INVALID_ARG, std::string(what) + ": d must be a device pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool hx = !is_device_ptr(FX), hy = !is_device_ptr(FY);
+    if (!hx && !hy) {
+        CK(launch_pair_costs(FX, FY, nvx, nvy, dim, d, s, norm));
+        return DISCO_OK;
+    }
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    CK(pool_for(dev, &pool));
+    const size_t bx = size_t(nvx) * size_t(dim) * sizeof(float), by = size_t(nvy) * size_t(dim) * sizeof(float);
+    float* buf = nullptr;
+    CK(cudaMallocFromPoolAsync(reinterpret_cast<void**>(&buf), (hx ? bx : 0) + (hy ? by : 0), pool, s));
+    const float* fx = FX;
+    const float* fy = FY;
+    cudaError_t e = cudaSuccess;
+    if (hx) {
+        e = cudaMemcpyAsync(buf, FX, bx, cudaMemcpyHostToDevice, s);
+        fx = buf;
+    }
+    if (e == cudaSuccess && hy) {
+        float* dst = buf + (hx ? size_t(nvx) * size_t(dim) : 0);
+        e = cudaMemcpyAsync(dst, FY, by, cudaMemcpyHostToDevice, s);
+        fy = dst;
+    }
+    if (e == cudaSuccess) e = launch_pair_costs(fx, fy, nvx, nvy, dim, d, s, norm);
+    const cudaError_t ef = cudaFreeAsync(buf, s);
+    if (e != cudaSuccess || ef != cudaSuccess)
+        return fail(DISCO_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e != cudaSuccess ? e : ef));
     return DISCO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int disco_pair_costs(const float* FX, const float* FY, int32_t nvx, int32_t nvy, int32_t dim, float* d, void* stream) {
+    return pair_kernel("pair_costs", FX, FY, nvx, nvy, dim, d, stream, false);
 }
 
 int disco_pair_distances(const float* FX, const float* FY, int32_t nvx, int32_t nvy, int32_t dim, float* d,
                          void* stream) {
-    if (!FX || !FY || !d || nvx <= 0 || nvy <= 0 || dim <= 0)
-        return fail(DISCO_ERR_INVALID_ARG, "pair_distances: bad arguments");
-    if (!is_device_ptr(FX) || !is_device_ptr(FY) || !is_device_ptr(d))
-        return fail(DISCO_ERR_INVALID_ARG, "pair_distances: FX, FY and d must be device pointers");
-    CK(launch_pair_costs(FX, FY, nvx, nvy, dim, d, static_cast<cudaStream_t>(stream), true));
-    return DISCO_OK;
+    return pair_kernel("pair_distances", FX, FY, nvx, nvy, dim, d, stream, true);
 }
 
 int disco_candidates(const float* d, int32_t nvx, int32_t nvy, int32_t k, const disco_mesh* X, const disco_mesh* Y,

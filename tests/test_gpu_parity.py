@@ -74,6 +74,32 @@ def test_pair_costs_ragged_tiles(torch):
         np.testing.assert_allclose(d, P.pair_distance(FX, FY), rtol=1e-5, atol=1e-7)
 
 
+def test_pair_costs_from_host_arrays(torch):
+    """disco_pair_costs and disco_pair_distances take host feature arrays (copied in by the
+    library) as well as device ones, with the same results."""
+    from paper_2310_08230_gb300 import _lib as L
+
+    inst = I.config2()
+    FX = np.ascontiguousarray(inst.FX)
+    FY = np.ascontiguousarray(inst.FY)
+    nvx, nvy, D = FX.shape[0], FY.shape[0], FX.shape[1]
+    lib = L.lib()
+    for fn, ref in ((lib.disco_pair_costs, P.pair_distance(FX, FY)),
+                    (lib.disco_pair_distances, P.pair_euclid(FX, FY))):
+        got = []
+        for fx, fy in ((FX, FY), (torch.from_numpy(FX).cuda(), FY), (torch.from_numpy(FX).cuda(),
+                                                                     torch.from_numpy(FY).cuda())):
+            d = torch.empty((nvx, nvy), dtype=torch.float32, device="cuda")
+            px = fx.ctypes.data if isinstance(fx, np.ndarray) else fx.data_ptr()
+            py = fy.ctypes.data if isinstance(fy, np.ndarray) else fy.data_ptr()
+            L.check(fn(px, py, nvx, nvy, D, d.data_ptr(), None), "pair kernel")
+            torch.cuda.synchronize()
+            got.append(d.cpu().numpy())
+        np.testing.assert_array_equal(got[0], got[2])
+        np.testing.assert_array_equal(got[1], got[2])
+        np.testing.assert_allclose(got[2], ref, rtol=1e-5, atol=1e-7)
+
+
 def test_candidates_match_oracle(torch):
     from paper_2310_08230_gb300.api import candidates
 
