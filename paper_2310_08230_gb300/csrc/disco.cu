@@ -369,7 +369,7 @@ int upload(disco_handle* h) {
             for (double c : h->plans[i].cost) cmax = std::max(cmax, std::fabs(c));
         int e = 0;
         std::frexp(std::max(cmax, std::ldexp(1.0, -20)), &e);  // cmax < 2^e
-        e = std::min(e, 30);
+        e = std::min(e, 100);  // 2^F and 2^(42 - F) stay normal FP32 numbers
         const int F = 32 - e;
         h->fx = FxScale{std::ldexp(1.0f, F), std::ldexp(1.0f, -F), std::ldexp(1.0f, 42 - F)};
     }

@@ -251,3 +251,42 @@ def test_errors_are_codes_not_crashes(torch):
     s.dual(3)
     assert np.isfinite(s.lower_bound())
     s.close()
+
+
+@pytest.mark.parametrize("scale", [1e6, 1e13])
+def test_unnormalised_costs_of_any_scale(torch, scale):
+    """The averaging grid follows the largest cost (2^-F with 2^(32 - F) above it), so raw
+    costs far from [0, 1] still match the oracle to the bound tolerance."""
+    inst, prob, d, allowed, fixed, dec = _oracle("config1", 0)
+    d2 = (d * scale).astype(np.float32)
+    p2 = P.build_problem(inst.X.T, inst.Y.T, d2.astype(np.float64), None, normalize=False)
+    f2, c2 = P.presolve(p2)
+    o = S.DualOracle(B.decompose(p2, f2, c2, 0))
+    o.iterate(60)
+    s = _solver(inst, d2, allowed, normalize_costs=0)
+    s.dual(60)
+    lb, ref = s.lower_bound(), o.lower_bound()
+    assert abs(lb - ref) <= LB_RTOL * abs(ref), (lb, ref)
+    s.close()
+
+
+def test_out_of_range_state_is_reported(torch):
+    """A deferred mean outside the averaging sums' range (here imported by set_state) is
+    clamped and flagged: the next synchronising call raises DISCO_ERR_RANGE, and the handle
+    works again once a valid state is set."""
+    from paper_2310_08230_gb300 import _lib as L
+
+    inst, prob, d, allowed, fixed, dec = _oracle("tet", 0)
+    s = _solver(inst, d, allowed)
+    s.dual(10)
+    lam, pend = s.get_state()
+    lb = s.lower_bound()
+    bad = pend.copy()
+    bad[0] = 1e30
+    s.set_state(lam, bad)
+    with pytest.raises(L.DiscoError) as e:
+        s.lower_bound()
+    assert e.value.code == L.DISCO_ERR_RANGE
+    s.set_state(lam, pend)
+    assert s.lower_bound() == pytest.approx(lb, rel=1e-6)
+    s.close()
