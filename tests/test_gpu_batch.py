@@ -175,3 +175,43 @@ def test_sixteen_pair_batch_runs_clean(lib):
     assert ok.all()
     assert np.all(lbs <= costs + 1e-5 * np.abs(costs))
     s.close()
+
+
+def test_full_batch_sampled_pairs_match_oracle(lib):
+    """The 64-pair uneven batch at its size (about 340 M nodes) in the benchmark's
+    configuration (chunk 32, 300 iterations, graph replay, autotuned launch geometry): every
+    pair's rounding is feasible; on two sampled pairs, the one with the fewest and the one with
+    the most BDD nodes, the bound (1e-5 rel), every min-marginal (1e-4 abs) and the primal cost
+    (1e-4 rel) match the oracle. Both sides get the oracle's FP32 costs and candidate masks."""
+    from oracle import primal as PR
+
+    Solver = lib
+    insts = I.config4(64)
+    ds, masks = [], []
+    for i in insts:
+        d32 = P.pair_distance(i.FX, i.FY).astype(np.float32)
+        ds.append(d32)
+        masks.append(P.candidate_pairs(d32.astype(np.float64), i.topk, i.X.T, i.Y.T))
+    s = Solver.batch([(i.X.T, i.Y.T, d, a.astype(np.uint8)) for i, d, a in zip(insts, ds, masks)], split_chunk=32)
+    infos = [s.instance_info(k) for k in range(len(insts))]
+    assert sum(x["nnodes"] for x in infos) > 300_000_000
+    s.dual(300)
+    lbs = s.lower_bounds()
+    mm = s.min_marginals()
+    offs = np.concatenate([[0], np.cumsum([x["nslots"] for x in infos])])
+    xs, costs, ok = s.primal_batch()
+    s.close()
+    assert ok.all()
+    nodes = [x["nnodes"] for x in infos]
+    for k in (int(np.argmin(nodes)), int(np.argmax(nodes))):
+        i = insts[k]
+        prob = P.build_problem(i.X.T, i.Y.T, ds[k].astype(np.float64), masks[k])
+        fixed, const = P.presolve(prob)
+        o = S.DualOracle(B.decompose(prob, fixed, const, 32))
+        o.iterate(300)
+        ref = o.lower_bound()
+        assert abs(lbs[k] - ref) <= 1e-5 * abs(ref), (k, lbs[k], ref)
+        np.testing.assert_allclose(mm[offs[k]:offs[k + 1]], o.min_marginals(), atol=1e-4, rtol=0)
+        r = PR.round_primal(o, prob, fixed)
+        assert r.ok and not np.any(prob.residual(xs[k]))
+        assert abs(costs[k] - r.cost) <= 1e-4 * abs(r.cost), (k, costs[k], r.cost)
