@@ -155,7 +155,36 @@ struct Elems {  // matching elements, structure of arrays
         ye.push_back(y);
     }
     size_t size() const { return type.size(); }
+    // k more elements of type ty, X element x; returns the first one's index
+    size_t grow(size_t k, int ty, int x) {
+        const size_t b = size();
+        m.resize(3 * (b + k));
+        n.resize(3 * (b + k));
+        type.resize(b + k, uint8_t(ty));
+        xe.resize(b + k, x);
+        ye.resize(b + k);
+        return b;
+    }
 };
+
+// Sorts distinct codes in [0, range) ascending. Unless they are very sparse in their range, one pass
+// over a bit set (`bits`: range / 64 zero words, left zero) replaces the comparison sort.
+template <class T>
+void sort_codes(std::vector<T>* c, int64_t range, std::vector<uint64_t>* bits) {
+    const size_t k = c->size();
+    const int64_t words = (range + 63) / 64;
+    if (k < 16 || int64_t(k) * 32 < words) {  // a sort costs about k log k branchy steps
+        std::sort(c->begin(), c->end());
+        return;
+    }
+    if (int64_t(bits->size()) < words) bits->assign(size_t(words), 0);
+    uint64_t* b = bits->data();
+    for (const T x : *c) b[x >> 6] |= uint64_t(1) << (x & 63);
+    size_t o = 0;
+    for (int64_t w = 0; w < words && o < k; ++w)
+        for (uint64_t x = b[w]; x; x &= x - 1) (*c)[o++] = T(w * 64 + __builtin_ctzll(x));
+    for (const T x : *c) b[x >> 6] = 0;
+}
 
 
 // Candidate pairs: a bit row per X vertex (cache resident) and the allowed Y vertices of
@@ -217,6 +246,7 @@ void enumerate(const MeshTopo& X, const MeshTopo& Y, const Allowed& A, int threa
     }
     run_jobs(jobs, threads, out, [&](const Job& j, Elems* o) {
         const int lo = j.lo, hi = j.hi;
+        std::vector<uint64_t> bits;  // sort_codes' bit set
         switch (j.type) {
             case 0: {  // type 0: X triangle t, Y triangle s, rotation r: corner v -> (t_v, s_{(v+r)%3})
             std::vector<int64_t> cand;
@@ -229,10 +259,18 @@ void enumerate(const MeshTopo& X, const MeshTopo& Y, const Allowed& A, int threa
                         if (A(m1, TY[3 * s + (r + 1) % 3]) && A(m2, TY[3 * s + (r + 2) % 3])) cand.push_back(int64_t(s) * 3 + r);
                     });
                 });
-                std::sort(cand.begin(), cand.end());
-                for (int64_t c : cand) {
-                    int s = int(c / 3), r = int(c % 3);
-                    o->push(m0, m1, m2, TY[3 * s + r], TY[3 * s + (r + 1) % 3], TY[3 * s + (r + 2) % 3], 0, t, s);
+                sort_codes(&cand, int64_t(Y.nt) * 3, &bits);
+                const size_t b = o->grow(cand.size(), 0, t);
+                int32_t* om = o->m.data() + 3 * b;
+                int32_t* on = o->n.data() + 3 * b;
+                int32_t* oy = o->ye.data() + b;
+                for (const int64_t c : cand) {
+                    const int s = int(c / 3), r = int(c % 3);
+                    om[0] = m0; om[1] = m1; om[2] = m2;
+                    on[0] = TY[3 * s + r]; on[1] = TY[3 * s + (r + 1) % 3]; on[2] = TY[3 * s + (r + 2) % 3];
+                    *oy++ = s;
+                    om += 3;
+                    on += 3;
                 }
             }
                 break;
@@ -254,11 +292,19 @@ void enumerate(const MeshTopo& X, const MeshTopo& Y, const Allowed& A, int threa
                             cand.push_back(int64_t(e) * 6 + __builtin_ctz(x));
                     });
                 });
-                std::sort(cand.begin(), cand.end());
-                for (int64_t c : cand) {
-                    int e = int(c / 6), p = int(c % 6);
-                    int ab[2] = {Y.edges[e].first, Y.edges[e].second};
-                    o->push(m[0], m[1], m[2], ab[kEdgePattern[p][0]], ab[kEdgePattern[p][1]], ab[kEdgePattern[p][2]], 1, t, e);
+                sort_codes(&cand, int64_t(Y.edges.size()) * 6, &bits);
+                const size_t b = o->grow(cand.size(), 1, t);
+                int32_t* om = o->m.data() + 3 * b;
+                int32_t* on = o->n.data() + 3 * b;
+                int32_t* oy = o->ye.data() + b;
+                for (const int64_t c : cand) {
+                    const int e = int(c / 6), p = int(c % 6);
+                    const int ab[2] = {Y.edges[e].first, Y.edges[e].second};
+                    om[0] = m[0]; om[1] = m[1]; om[2] = m[2];
+                    on[0] = ab[kEdgePattern[p][0]]; on[1] = ab[kEdgePattern[p][1]]; on[2] = ab[kEdgePattern[p][2]];
+                    *oy++ = e;
+                    om += 3;
+                    on += 3;
                 }
             }
                 break;
@@ -282,11 +328,18 @@ void enumerate(const MeshTopo& X, const MeshTopo& Y, const Allowed& A, int threa
                         });
                     });
                 }
-                std::sort(cand.begin(), cand.end());
-                for (int64_t c : cand) {
-                    int s = int(c / 6), p = int(c % 6);
-                    o->push(ab[kEdgePattern[p][0]], ab[kEdgePattern[p][1]], ab[kEdgePattern[p][2]], TY[3 * s], TY[3 * s + 1],
-                            TY[3 * s + 2], 2, e, s);
+                sort_codes(&cand, int64_t(Y.nt) * 6, &bits);
+                const size_t b = o->grow(cand.size(), 2, e);
+                int32_t* om = o->m.data() + 3 * b;
+                int32_t* on = o->n.data() + 3 * b;
+                int32_t* oy = o->ye.data() + b;
+                for (const int64_t c : cand) {
+                    const int s = int(c / 6), p = int(c % 6);
+                    om[0] = ab[kEdgePattern[p][0]]; om[1] = ab[kEdgePattern[p][1]]; om[2] = ab[kEdgePattern[p][2]];
+                    on[0] = TY[3 * s]; on[1] = TY[3 * s + 1]; on[2] = TY[3 * s + 2];
+                    *oy++ = s;
+                    om += 3;
+                    on += 3;
                 }
             }
                 break;
@@ -309,8 +362,18 @@ void enumerate(const MeshTopo& X, const MeshTopo& Y, const Allowed& A, int threa
                         if (A(mv, TY[3 * s + 1]) && A(mv, TY[3 * s + 2])) cand.push_back(s);
                     });
                 });
-                std::sort(cand.begin(), cand.end());
-                for (int s : cand) o->push(mv, mv, mv, TY[3 * s], TY[3 * s + 1], TY[3 * s + 2], 4, mv, s);
+                sort_codes(&cand, int64_t(Y.nt), &bits);
+                const size_t b = o->grow(cand.size(), 4, mv);
+                int32_t* om = o->m.data() + 3 * b;
+                int32_t* on = o->n.data() + 3 * b;
+                int32_t* oy = o->ye.data() + b;
+                for (const int s : cand) {
+                    om[0] = mv; om[1] = mv; om[2] = mv;
+                    on[0] = TY[3 * s]; on[1] = TY[3 * s + 1]; on[2] = TY[3 * s + 2];
+                    *oy++ = s;
+                    om += 3;
+                    on += 3;
+                }
             }
                 break;
             }
@@ -746,6 +809,18 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     const int64_t nr = P->nrows;
 
     tr.mark("projection rows");
+    // row chunks of about equal entry counts (projection rows are long, closedness rows
+    // short), taken dynamically by the threads; the results do not depend on the chunking
+    const int64_t n_entries = P->row_ptr[size_t(nr)];
+    const int nrc = std::max(1, std::min<int>(nth * 8, int(nr / 1024) + 1));
+    std::vector<int64_t> row_cut(size_t(nrc) + 1, nr);
+    row_cut[0] = 0;
+    for (int c = 1; c < nrc; ++c) {
+        const int64_t want = n_entries * c / nrc;
+        row_cut[size_t(c)] = std::max<int64_t>(
+            row_cut[size_t(c) - 1],
+            int64_t(std::lower_bound(P->row_ptr.begin(), P->row_ptr.begin() + nr, want) - P->row_ptr.begin()));
+    }
     // ---- presolve: saturated rows force all their free variables, to a fixpoint. Rows and
     // variables are split into contiguous ranges, one per thread, and each thread alone
     // writes the state of its ranges. A round is bulk-synchronous: (1) the owners of the
@@ -754,9 +829,90 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     // value is a conflict) and send (row, coefficient, value) to the owners of the
     // variable's rows; (3) row owners update the free counts and the residual and queue each
     // updated row once for the next round. The fixed values are the unique arc-consistent
-    // closure whatever the thread count.
+    // closure whatever the thread count and whatever the order of the rounds.
+    //
+    // While a round fixes many variables (the first rounds fix most of the ones presolve
+    // fixes), dense rounds do the same work with sequential access: every acting row proposes
+    // the values it forces (a different proposal for the same variable is a conflict), the
+    // proposals become fixings, and every row's residual and free counts are recounted from
+    // its entries. The incremental rounds then continue from the recounted state.
     P->fixed.assign(size_t(nv), -1);
+    int dense_rounds = 0;
+    bool dense_conflict = false;
     {
+        std::vector<int8_t> prop(static_cast<size_t>(nv), -1);
+        std::atomic<bool> bad{false};
+        std::vector<int64_t> nfix(static_cast<size_t>(nth), 0);
+        for (;;) {
+            // (1) decide: a first round acts on every saturated or violated row (nothing is
+            // fixed yet), later ones on those with free entries
+            const bool first = dense_rounds == 0;
+            parallel_tasks(nrc, nth, [&](int64_t c) {
+                for (int64_t r = row_cut[size_t(c)]; r < row_cut[size_t(c) + 1]; ++r) {
+                    const RowState q = rs[r];
+                    if (q.np + q.nn == 0) {
+                        if (first && q.res != 0) bad.store(true, std::memory_order_relaxed);
+                        continue;
+                    }
+                    if (q.res > q.np || q.res < -q.nn) {
+                        bad.store(true, std::memory_order_relaxed);
+                        continue;
+                    }
+                    int up;
+                    if (q.res == q.np) up = 1;
+                    else if (q.res == -q.nn) up = 0;
+                    else continue;
+                    for (int64_t e = P->row_ptr[r]; e < P->row_ptr[r + 1]; ++e) {
+                        const int32_t v = P->row_var[e];
+                        if (P->fixed[v] >= 0) continue;
+                        const int8_t val = int8_t(P->row_coef[e] > 0 ? up : 1 - up);
+                        int8_t seen = -1;
+                        if (!__atomic_compare_exchange_n(&prop[size_t(v)], &seen, val, false, __ATOMIC_RELAXED,
+                                                         __ATOMIC_RELAXED) &&
+                            seen != val)
+                            bad.store(true, std::memory_order_relaxed);
+                    }
+                }
+            });
+            ++dense_rounds;
+            if (bad.load()) {
+                dense_conflict = true;
+                break;
+            }
+            // (2) the proposals become fixings
+            parallel_chunks(nv, nth, [&](int c, int64_t lo, int64_t hi) {
+                int64_t k = 0;
+                for (int64_t v = lo; v < hi; ++v)
+                    if (prop[size_t(v)] >= 0) {
+                        P->fixed[size_t(v)] = prop[size_t(v)];
+                        prop[size_t(v)] = -1;
+                        ++k;
+                    }
+                nfix[size_t(c)] = k;
+            });
+            int64_t fixed_now = 0;
+            for (int64_t k : nfix) fixed_now += k;
+            if (tr.on) std::fprintf(stderr, "disco build  dense round %d fixes %lld\n", dense_rounds, (long long)fixed_now);
+            if (fixed_now == 0) break;  // no row acts: the state is already the closure's
+            // (3) recount every row from its entries
+            parallel_tasks(nrc, nth, [&](int64_t c) {
+                for (int64_t r = row_cut[size_t(c)]; r < row_cut[size_t(c) + 1]; ++r) {
+                    int32_t res = P->rhs[size_t(r)], np = 0, nn = 0;
+                    for (int64_t e = P->row_ptr[r]; e < P->row_ptr[r + 1]; ++e) {
+                        const int8_t f = P->fixed[P->row_var[e]];
+                        const bool pos = P->row_coef[e] > 0;
+                        if (f < 0) ++(pos ? np : nn);
+                        else res -= pos ? f : -f;
+                    }
+                    rs[r] = RowState{res, np, nn, 0};
+                }
+            });
+            // each fixing updates about five rows in an incremental round
+            if (5 * fixed_now < n_entries / 8) break;
+        }
+    }
+    tr.mark("presolve dense");
+    if (!dense_conflict) {
         const int nt = nth;
         // owner of row r / variable v: table lookup by blocks of 4096
         auto owners = [&](int64_t n) {
@@ -773,9 +929,10 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         };
         std::vector<std::vector<int32_t>> frontier(nt);
         parallel_chunks(nt, nt, [&](int t, int64_t, int64_t) {
-            // nothing is fixed yet: only saturated or violated rows can act in round 1
+            // rows with free entries that are saturated or violated after the dense rounds
             for (int64_t r = row_lo(t), r1 = row_lo(t + 1); r < r1; ++r)
-                if (rs[r].res >= rs[r].np || rs[r].res <= -rs[r].nn) frontier[t].push_back(int32_t(r));
+                if (rs[r].np + rs[r].nn > 0 && (rs[r].res >= rs[r].np || rs[r].res <= -rs[r].nn))
+                    frontier[t].push_back(int32_t(r));
         });
         struct Upd {
             int32_t row;
@@ -864,8 +1021,9 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
             });
         }
         if (any([&](int t) { return bad[t] != 0; })) { *err = "presolve: a row has no solution"; return DISCO_ERR_INFEASIBLE; }
-        if (tr.on) std::fprintf(stderr, "disco build  presolve rounds: %d\n", rounds);
+        if (tr.on) std::fprintf(stderr, "disco build  presolve rounds: %d dense + %d\n", dense_rounds, rounds);
     }
+    if (dense_conflict) { *err = "presolve: a row has no solution"; return DISCO_ERR_INFEASIBLE; }
     {
         std::atomic<bool> violated{false};
         parallel_chunks(nr, nth, [&](int, int64_t lo, int64_t hi) {
@@ -931,20 +1089,6 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
             deg_free[v] = uint8_t(3 + (er[size_t(i)].proj[0] >= 0) + (er[size_t(i)].proj[1] >= 0));
         }
     });
-    // row chunks of about equal entry counts (projection rows are long, closedness rows
-    // short), taken dynamically by the threads; the result does not depend on the chunking
-    const int nrc = std::max(1, std::min<int>(nth * 8, int(nr / 1024) + 1));
-    std::vector<int64_t> row_cut(size_t(nrc) + 1, nr);
-    {
-        const int64_t ntot = P->row_ptr[size_t(nr)];
-        row_cut[0] = 0;
-        for (int c = 1; c < nrc; ++c) {
-            const int64_t want = ntot * c / nrc;
-            row_cut[size_t(c)] = std::max<int64_t>(
-                row_cut[size_t(c) - 1],
-                int64_t(std::lower_bound(P->row_ptr.begin(), P->row_ptr.begin() + nr, want) - P->row_ptr.begin()));
-        }
-    }
     std::vector<RowChunk> chunks(nrc);
     parallel_tasks(nrc, nth, [&](int64_t c) {
         std::vector<int32_t> fv, lo, wd;
