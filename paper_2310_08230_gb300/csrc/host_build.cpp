@@ -710,8 +710,9 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     P->row_coef.resize(size_t(ne + nproj_entries));
     pod_vector<int32_t> row_ent(static_cast<size_t>(ne + nproj_entries));  // corner (0..2) or 3 + side
     // the rows of every element in one record (presolve reads all of them per fixing):
-    // closed[v] = closedness row of corner v << 1 | (coefficient there > 0); proj[side] = the
-    // X / Y projection row, -1 if none
+    // closed[v] = closedness row of corner v << 1 | (coefficient there > 0), filled after the
+    // dense presolve rounds for the variables still free; proj[side] = the X / Y projection
+    // row, -1 if none
     struct ElemRows {
         uint32_t closed[3];
         int32_t proj[2];
@@ -735,7 +736,6 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                 P->row_var[e] = int32_t(id / 3);
                 P->row_coef[e] = neg ? -1 : 1;
                 row_ent[e] = int32_t(id % 3);
-                er[id / 3].closed[id % 3] = uint32_t(r) << 1 | (neg ? 0u : 1u);
                 ++(neg ? rs[r].nn : rs[r].np);
             }
         }
@@ -832,15 +832,16 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     // closure whatever the thread count and whatever the order of the rounds.
     //
     // While a round fixes many variables (the first rounds fix most of the ones presolve
-    // fixes), dense rounds do the same work with sequential access: every acting row proposes
-    // the values it forces (a different proposal for the same variable is a conflict), the
-    // proposals become fixings, and every row's residual and free counts are recounted from
-    // its entries. The incremental rounds then continue from the recounted state.
+    // fixes), dense rounds do the same work with sequential access: every acting row flags
+    // the values it forces (one flag per value, so a variable flagged both ways is a
+    // conflict; plain stores, no read-modify-write), the flags become fixings, and every row's
+    // residual and free counts are recounted from its entries. The incremental rounds then
+    // continue from the recounted state.
     P->fixed.assign(size_t(nv), -1);
     int dense_rounds = 0;
     bool dense_conflict = false;
     {
-        std::vector<int8_t> prop(static_cast<size_t>(nv), -1);
+        std::vector<uint8_t> to0(static_cast<size_t>(nv), 0), to1(static_cast<size_t>(nv), 0);
         std::atomic<bool> bad{false};
         std::vector<int64_t> nfix(static_cast<size_t>(nth), 0);
         for (;;) {
@@ -865,12 +866,8 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                     for (int64_t e = P->row_ptr[r]; e < P->row_ptr[r + 1]; ++e) {
                         const int32_t v = P->row_var[e];
                         if (P->fixed[v] >= 0) continue;
-                        const int8_t val = int8_t(P->row_coef[e] > 0 ? up : 1 - up);
-                        int8_t seen = -1;
-                        if (!__atomic_compare_exchange_n(&prop[size_t(v)], &seen, val, false, __ATOMIC_RELAXED,
-                                                         __ATOMIC_RELAXED) &&
-                            seen != val)
-                            bad.store(true, std::memory_order_relaxed);
+                        const bool one = (P->row_coef[e] > 0) == (up == 1);
+                        __atomic_store_n(one ? &to1[size_t(v)] : &to0[size_t(v)], uint8_t(1), __ATOMIC_RELAXED);
                     }
                 }
             });
@@ -879,32 +876,43 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                 dense_conflict = true;
                 break;
             }
-            // (2) the proposals become fixings
+            // (2) the flags become fixings
+            std::vector<uint8_t> clash(static_cast<size_t>(nth), 0);
             parallel_chunks(nv, nth, [&](int c, int64_t lo, int64_t hi) {
                 int64_t k = 0;
-                for (int64_t v = lo; v < hi; ++v)
-                    if (prop[size_t(v)] >= 0) {
-                        P->fixed[size_t(v)] = prop[size_t(v)];
-                        prop[size_t(v)] = -1;
-                        ++k;
-                    }
+                uint8_t x = 0;
+                for (int64_t v = lo; v < hi; ++v) {
+                    const uint8_t a = to0[size_t(v)], b = to1[size_t(v)];
+                    x |= a & b;
+                    P->fixed[size_t(v)] = b ? int8_t(1) : (a ? int8_t(0) : P->fixed[size_t(v)]);
+                    to0[size_t(v)] = 0;
+                    to1[size_t(v)] = 0;
+                    k += a | b;
+                }
                 nfix[size_t(c)] = k;
+                clash[size_t(c)] = x;
             });
+            if (std::find(clash.begin(), clash.end(), uint8_t(1)) != clash.end()) {
+                dense_conflict = true;
+                break;
+            }
             int64_t fixed_now = 0;
             for (int64_t k : nfix) fixed_now += k;
             if (tr.on) std::fprintf(stderr, "disco build  dense round %d fixes %lld\n", dense_rounds, (long long)fixed_now);
             if (fixed_now == 0) break;  // no row acts: the state is already the closure's
-            // (3) recount every row from its entries
+            // (3) recount every row that had free entries from its entries
             parallel_tasks(nrc, nth, [&](int64_t c) {
                 for (int64_t r = row_cut[size_t(c)]; r < row_cut[size_t(c) + 1]; ++r) {
-                    int32_t res = P->rhs[size_t(r)], np = 0, nn = 0;
+                    if (rs[r].np + rs[r].nn == 0) continue;
+                    int32_t res = P->rhs[size_t(r)], np = 0, nf = 0;  // branch-free: fixings look random
                     for (int64_t e = P->row_ptr[r]; e < P->row_ptr[r + 1]; ++e) {
-                        const int8_t f = P->fixed[P->row_var[e]];
-                        const bool pos = P->row_coef[e] > 0;
-                        if (f < 0) ++(pos ? np : nn);
-                        else res -= pos ? f : -f;
+                        const int32_t f = P->fixed[P->row_var[e]];
+                        const int32_t c = P->row_coef[e];
+                        nf += f < 0;
+                        np += (f < 0) & (c > 0);
+                        res -= c * (f == 1);
                     }
-                    rs[r] = RowState{res, np, nn, 0};
+                    rs[r] = RowState{res, np, nf - np, 0};
                 }
             });
             // each fixing updates about five rows in an incremental round
@@ -912,6 +920,18 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         }
     }
     tr.mark("presolve dense");
+    if (!dense_conflict) {
+        // closedness rows of the variables still free (only the incremental rounds use them)
+        parallel_tasks(nrc, nth, [&](int64_t c) {
+            for (int64_t r = row_cut[size_t(c)]; r < std::min(row_cut[size_t(c) + 1], n_closed); ++r)
+                for (int64_t e = P->row_ptr[r]; e < P->row_ptr[r + 1]; ++e) {
+                    const int32_t v = P->row_var[e];
+                    if (P->fixed[v] < 0)
+                        er[size_t(v)].closed[row_ent[e]] = uint32_t(r) << 1 | (P->row_coef[e] > 0 ? 1u : 0u);
+                }
+        });
+        tr.mark("free closedness rows");
+    }
     if (!dense_conflict) {
         const int nt = nth;
         // owner of row r / variable v: table lookup by blocks of 4096
@@ -1094,6 +1114,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         std::vector<int32_t> fv, lo, wd;
         std::vector<int8_t> fc;
         std::vector<uint8_t> fr;
+        std::vector<int64_t> cut_aux;  // local id of y_1 of the cut before segment s
         {
             RowChunk& C = chunks[c];
             const int64_t r0 = row_cut[size_t(c)], r1 = row_cut[size_t(c) + 1];
@@ -1140,7 +1161,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                 if (C.rc) break;
                 int nseg = (split_chunk > 0 && n > split_chunk) ? (n + split_chunk - 1) / split_chunk : 1;
                 if (split_max_segments > 0) nseg = std::min(nseg, split_max_segments);
-                std::vector<int64_t> cut_aux(size_t(nseg) + 1, -1);  // local id of y_1 of the cut before segment s
+                cut_aux.assign(size_t(nseg) + 1, -1);
                 for (int s = 1; s < nseg; ++s) {
                     const int b = int(int64_t(s) * n / nseg);
                     if (wd[b] > 1) {
