@@ -32,6 +32,7 @@
 #include <cstdlib>
 #include <memory>
 #include <cstring>
+#include <map>
 #include <numeric>
 #include <string>
 #include <thread>
@@ -42,6 +43,73 @@
 #include "plan.h"
 
 namespace disco {
+
+// ---- cache of large host blocks (declared in plan.h)
+namespace {
+constexpr size_t kCachedMin = size_t(1) << 20;
+struct BlockCache {
+    std::mutex mu;
+    std::multimap<size_t, void*> free_blocks;  // size class -> block
+    size_t held = 0, cap = 0;
+    bool poison = false;  // fill every block with 0xA5 when handed out (tests)
+    BlockCache() {
+        const char* e = std::getenv("DISCO_HOST_CACHE_MB");
+        cap = size_t(e ? std::strtoull(e, nullptr, 10) : 2048) << 20;
+        poison = std::getenv("DISCO_HOST_CACHE_POISON") != nullptr;
+    }
+};
+BlockCache& block_cache() {  // never destroyed: blocks may be freed during static destruction
+    static BlockCache* c = new BlockCache();
+    return *c;
+}
+size_t block_class(size_t b) {
+    const int lg = 63 - __builtin_clzll(uint64_t(b));
+    const size_t step = size_t(1) << (lg - 3);
+    return (b + step - 1) & ~(step - 1);
+}
+}  // namespace
+
+void* host_block_alloc(size_t bytes) {
+    if (bytes < kCachedMin) return ::operator new(bytes);
+    const size_t c = block_class(bytes);
+    BlockCache& k = block_cache();
+    void* p = nullptr;
+    {
+        std::lock_guard<std::mutex> g(k.mu);
+        const auto it = k.free_blocks.find(c);
+        if (it != k.free_blocks.end()) {
+            p = it->second;
+            k.free_blocks.erase(it);
+            k.held -= c;
+        }
+    }
+    if (!p) p = ::operator new(c);
+    if (k.poison) std::memset(p, 0xA5, c);
+    return p;
+}
+
+void host_block_free(void* p, size_t bytes) noexcept {
+    if (!p) return;
+    if (bytes < kCachedMin) {
+        ::operator delete(p);
+        return;
+    }
+    const size_t c = block_class(bytes);
+    BlockCache& k = block_cache();
+    {
+        std::lock_guard<std::mutex> g(k.mu);
+        if (k.held + c <= k.cap) {
+            try {
+                k.free_blocks.emplace(c, p);
+                k.held += c;
+                return;
+            } catch (...) {
+            }
+        }
+    }
+    ::operator delete(p);
+}
+
 namespace {
 
 // vertex sequence of a degenerate triangle over an edge (a < b): 0 -> a, 1 -> b
@@ -571,7 +639,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     if (uint64_t(nvx) * uint64_t(nvy) >= (uint64_t(1) << 32)) { *err = "meshes too large"; return DISCO_ERR_INVALID_ARG; }
     const int64_t ne = 3 * nv;
     if (ne >= (int64_t(1) << 31)) { *err = "product space too large"; return DISCO_ERR_INVALID_ARG; }
-    std::unique_ptr<EdgeEntry[]> ent(new EdgeEntry[size_t(ne)]);
+    pod_vector<EdgeEntry> ent(static_cast<size_t>(ne));
     std::vector<int64_t> bstart(size_t(nvx) + 1, 0);
     {
         // corner v of element i and corner v+1: (m, n) pairs, ordered lexicographically
@@ -657,7 +725,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                     key[e - b0] = p * R + q;
                 }
                 if (!ok) {
-                    std::sort(ent.get() + b0, ent.get() + b1);
+                    std::sort(ent.data() + b0, ent.data() + b1);
                 } else {
                     const int nk = ncand * R;
                     cnt.assign(size_t(nk) + 1, 0);
@@ -683,7 +751,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                         }
                         g0 = g1;
                     }
-                    std::copy(tmp.begin(), tmp.end(), ent.get() + b0);
+                    std::copy(tmp.begin(), tmp.end(), ent.data() + b0);
                 }
                 for (int i = 0; i < R; ++i) rank_of[ring[i]] = -1;
                 int64_t r = 0;
@@ -740,7 +808,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
             }
         }
     });
-    ent.reset();
+    pod_vector<EdgeEntry>().swap(ent);
     P->rhs.assign(size_t(n_closed), 0);
 
     tr.mark("closedness rows");

@@ -22,8 +22,18 @@ namespace disco {
 
 // Allocator that leaves trivially constructible elements uninitialised on resize, so that large
 // arrays are first touched by the (parallel) code that fills them instead of being zeroed.
+// Large host blocks (pod_vector storage: the compiled plans and the compiler's work
+// arrays) come from a process-wide cache. A build that follows a freed one of similar size
+// reuses its pages instead of faulting in, and having the kernel zero, hundreds of MB of
+// fresh memory, and a free returns the pages to the cache instead of unmapping them.
+// Blocks of at least 1 MB are rounded up to a size class (an eighth of a power of two) and
+// kept up to a total of DISCO_HOST_CACHE_MB megabytes (default 2048; 0 turns the cache off).
+void* host_block_alloc(size_t bytes);
+void host_block_free(void* p, size_t bytes) noexcept;
+
 template <class T>
 struct uninit_alloc : std::allocator<T> {
+    using value_type = T;
     template <class U>
     struct rebind {
         using other = uninit_alloc<U>;
@@ -31,6 +41,11 @@ struct uninit_alloc : std::allocator<T> {
     uninit_alloc() = default;
     template <class U>
     uninit_alloc(const uninit_alloc<U>&) noexcept {}
+    T* allocate(size_t n) {
+        if (n > size_t(-1) / sizeof(T)) throw std::bad_array_new_length();
+        return static_cast<T*>(host_block_alloc(n * sizeof(T)));
+    }
+    void deallocate(T* p, size_t n) noexcept { host_block_free(p, n * sizeof(T)); }
     template <class U>
     void construct(U* p) noexcept {
         ::new (static_cast<void*>(p)) U;

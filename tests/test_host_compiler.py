@@ -145,3 +145,46 @@ def test_host_compiler_matches_oracle_at_full_size(L):
     assert np.array_equal(sw, np.diff(dec.layer_node_ptr))
     assert info.nnodes == dec.n_nodes == 6019316
     assert info.constant == pytest.approx(const, abs=1e-6)
+
+
+_POISON_SCRIPT = r"""
+import ctypes, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_2310_08230_gb300 import _lib as L
+from oracle import problem as P
+from synth import instances as I
+inst = I.config3()
+d32 = P.pair_distance(inst.FX, inst.FY).astype(np.float32)
+a8 = P.candidate_pairs(d32.astype(np.float64), inst.topk, inst.X.T, inst.Y.T).astype(np.uint8)
+mx = L.disco_mesh(inst.X.nv, inst.X.nt, None, inst.X.T.ctypes.data)
+my = L.disco_mesh(inst.Y.nv, inst.Y.nt, None, inst.Y.T.ctypes.data)
+info = L.disco_info_t()
+args = (ctypes.byref(mx), ctypes.byref(my), d32.ctypes.data, a8.ctypes.data, 32, 8, ctypes.byref(info))
+L.check(L.lib().disco_compile_host(*args, None, None, 0, None, 0), "compile")
+sv = np.empty(info.nslots, np.int32); sw = np.empty(info.nslots, np.int32); fx = np.empty(info.nvars, np.int8)
+L.check(L.lib().disco_compile_host(*args, sv.ctypes.data, sw.ctypes.data, sv.shape[0], fx.ctypes.data, fx.shape[0]), "compile")
+np.savez(sys.argv[2], sv=sv, sw=sw, fx=fx, meta=np.array([info.nvars, info.nrows, info.nvars_free, info.nvars_aux,
+         info.nbdds, info.nnodes], np.int64), constant=np.array([info.constant]))
+"""
+
+
+@pytest.mark.slow
+def test_host_compiler_ignores_block_contents(L, tmp_path):
+    """Large host blocks are reused across builds without being cleared, so no step of the
+    compiler may depend on what a block held before: with every block filled with 0xA5 when
+    handed out (DISCO_HOST_CACHE_POISON), the 5120-triangle plan is the same bit for bit."""
+    import subprocess
+    import sys
+
+    inst = I.config3()
+    d32 = P.pair_distance(inst.FX, inst.FY).astype(np.float32)
+    allowed = P.candidate_pairs(d32.astype(np.float64), inst.topk, inst.X.T, inst.Y.T)
+    info, sv, sw, fx = _compile(L, inst, allowed, d32, 32, 8)
+    out = str(tmp_path / "poisoned.npz")
+    env = dict(os.environ, DISCO_HOST_CACHE_POISON="1")
+    subprocess.run([sys.executable, "-c", _POISON_SCRIPT, ROOT, out], env=env, cwd=ROOT, check=True, timeout=600)
+    z = np.load(out)
+    assert list(z["meta"]) == [info.nvars, info.nrows, info.nvars_free, info.nvars_aux, info.nbdds, info.nnodes]
+    assert z["constant"][0] == info.constant
+    assert np.array_equal(z["sv"], sv) and np.array_equal(z["sw"], sw) and np.array_equal(z["fx"], fx)
