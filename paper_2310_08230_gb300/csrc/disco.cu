@@ -355,24 +355,29 @@ int upload(disco_handle* h) {
     // Every internal variable lies in 2 to 7 BDD segments: the descriptor holds the degree in
     // 3 bits, and a variable in one segment would have been fixed by the presolve (a row with
     // one free variable forces it). The deferred mean divides by it.
-    for (int64_t i = 0; i < ni; ++i)
-        for (uint8_t dg : h->plans[i].deg)
-            if (dg < 2 || dg > 7)
-                return fail(DISCO_ERR_INVALID_ARG, "build: an internal variable lies in " + std::to_string(int(dg)) +
-                                                       " segments (2 to 7 expected)");
+    for (int64_t i = 0; i < ni; ++i) {
+        uint8_t lo = 255, hi = 0;  // a min / max reduction (vectorised), then the message
+        for (uint8_t dg : h->plans[i].deg) {
+            lo = std::min(lo, dg);
+            hi = std::max(hi, dg);
+        }
+        if (!h->plans[i].deg.empty() && (lo < 2 || hi > 7))
+            return fail(DISCO_ERR_INVALID_ARG, "build: an internal variable lies in " + std::to_string(int(lo < 2 ? lo : hi)) +
+                                                   " segments (2 to 7 expected)");
+    }
     // Fixed-point grid of the averaging sums: 2^-F with 2^(32 - F) >= the largest |cost| (at
     // least 2^-20), so one mass may reach 2^10 times the largest cost before the kernels flag
     // it (the sums stay below 2^45 grid units), and the grid is about 2e-10 of the largest cost.
     {
-        double cmax = 0.0;
-        for (int64_t i = 0; i < ni; ++i)
-            for (double c : h->plans[i].cost) cmax = std::max(cmax, std::fabs(c));
+        double cmax = 0.0;  // the compiler's largest element cost of each instance (costs are >= 0)
+        for (int64_t i = 0; i < ni; ++i) cmax = std::max(cmax, h->plans[i].cost_max);
         int e = 0;
         std::frexp(std::max(cmax, std::ldexp(1.0, -20)), &e);  // cmax < 2^e
         e = std::min(e, 100);  // 2^F and 2^(42 - F) stay normal FP32 numbers
         const int F = 32 - e;
         h->fx = FxScale{std::ldexp(1.0f, F), std::ldexp(1.0f, -F), std::ldexp(1.0f, 42 - F)};
     }
+    tr.mark("degrees, grid");
     // ---- tiles: per instance, segments grouped by width class, longest first; a tile never
     // mixes instances (its bound sum belongs to one instance). Counting sorts by (class,
     // length), then the tiles by (launch group, length): both stable.
@@ -480,10 +485,26 @@ int upload(disco_handle* h) {
                     cnt[size_t(c)][b] = run;
                     run += x;
                 }
+            // the keys travel with the segments, so that the tiles are cut from them in order
+            std::vector<uint32_t> skey(static_cast<size_t>(nseg));
             parallel_chunks(nseg, nch, [&](int c, int64_t k0, int64_t k1) {
-                for (int64_t k = k0; k < k1; ++k) R.seg[size_t(cnt[size_t(c)][key[size_t(k)]]++)] = k;
+                for (int64_t k = k0; k < k1; ++k) {
+                    const int64_t pos = cnt[size_t(c)][key[size_t(k)]]++;
+                    R.seg[size_t(pos)] = k;
+                    skey[size_t(pos)] = key[size_t(k)];
+                }
             });
-            cut_tiles(0, nseg);
+            const uint32_t kl = uint32_t(maxL + 1);  // key = class * (maxL + 1) + maxL - length
+            for (int64_t k = 0; k < nseg;) {
+                const uint32_t W = skey[size_t(k)] / kl;
+                const int L = maxL - int(skey[size_t(k)] % kl);
+                const int64_t first = k;
+                int q = 0;
+                while (q < 32 && k < nseg && skey[size_t(k)] / kl == W) ++q, ++k;
+                R.tiles.push_back(TileInfo{0, 0, L, int(W)});
+                R.first.push_back(first);
+                R.count.push_back(q);
+            }
         }
     });
     {
@@ -547,6 +568,7 @@ int upload(disco_handle* h) {
         tile_inst.swap(i2);
         tile_block.swap(b2);
     }
+    tr.mark("tile sort");
     h->classes.clear();
     int64_t slot_base = 0, node_base = 0;
     for (size_t t = 0; t < tiles.size(); ++t) {

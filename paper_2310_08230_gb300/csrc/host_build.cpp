@@ -619,7 +619,9 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         const double cmax = *std::max_element(cmaxs.begin(), cmaxs.end());
         P->cost_scale = 1.0;
         P->cost_scale_elem = -1;
+        P->cost_max = cmax;
         if (normalize && cmax > 0) {
+            P->cost_max = 1.0;  // x / cmax is at most 1, and exactly 1 for the largest
             P->cost_scale = cmax;
             for (int64_t i = 0; i < nv; ++i)
                 if (P->cost[i] == cmax) { P->cost_scale_elem = i; break; }

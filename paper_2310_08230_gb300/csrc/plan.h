@@ -20,8 +20,6 @@
 
 namespace disco {
 
-// Allocator that leaves trivially constructible elements uninitialised on resize, so that large
-// arrays are first touched by the (parallel) code that fills them instead of being zeroed.
 // Large host blocks (pod_vector storage: the compiled plans and the compiler's work
 // arrays) come from a process-wide cache. A build that follows a freed one of similar size
 // reuses its pages instead of faulting in, and having the kernel zero, hundreds of MB of
@@ -31,6 +29,8 @@ namespace disco {
 void* host_block_alloc(size_t bytes);
 void host_block_free(void* p, size_t bytes) noexcept;
 
+// Allocator that leaves trivially constructible elements uninitialised on resize, so that large
+// arrays are first touched by the (parallel) code that fills them instead of being zeroed.
 template <class T>
 struct uninit_alloc : std::allocator<T> {
     using value_type = T;
@@ -227,6 +227,7 @@ struct Plan {
     pod_vector<int32_t> vm, vn;         // 3 per variable: X / Y vertex of each corner
     pod_vector<double> cost;            // c_p per variable (normalised unless disabled)
     double cost_scale = 1.0;            // c_p = (mean of its pair costs) / cost_scale
+    double cost_max = 0.0;              // largest c_p (1 when normalised)
     int64_t cost_scale_elem = -1;       // the element whose raw cost is cost_scale (normalised)
     std::vector<double> area_x, area_y; // cost model 1 (Eq. 2): mixed vertex areas; else empty
     // per row, the mesh region its variables sit in (a tile-order key): a closedness row the
