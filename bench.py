@@ -49,10 +49,18 @@ def _traffic(workload: str, split_chunk: int):
     """DRAM bytes per half-pass launch from the committed ncu summary of this workload, or
     None when the half-pass sources changed since the counters were taken (sha256 of
     kernels.cu, device_util.cuh and kernels.h, in that order)."""
+    profiles = {"icosphere4-5120T-top16": "halfpass_icosphere4-5120T-top16.md",
+                "batch64-uneven": "halfpass_batch64-uneven.md"}
+    if workload not in profiles or split_chunk != 32:
+        return None
+    return _profile_traffic(profiles[workload])
+
+
+def _profile_traffic(profile: str):
     import hashlib
-    path = os.path.join(ROOT, "profiles", "halfpass_icosphere4-5120T-top16.md")
+    path = os.path.join(ROOT, "profiles", profile)
     csrc = os.path.join(ROOT, "paper_2310_08230_gb300", "csrc")
-    if workload != "icosphere4-5120T-top16" or split_chunk != 32 or not os.path.exists(path):
+    if not os.path.exists(path):
         return None
     h = hashlib.sha256()
     for name in HALFPASS_SOURCES:
@@ -543,6 +551,7 @@ def batched_vs_single(torch, iters: int = 300, n_pairs: int = 64, split_chunk: i
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "alg_bytes_per_launch": steady["alg_bytes"], "launch_ms": steady["half_pass_ms"],
                         "peak_kind": kind,
+                        "traffic": _traffic("batch64-uneven", split_chunk) if n_pairs == 64 else None,
                         "kernel": "MMA half-pass over all 64 pairs (every width-class launch of one half-pass)",
                         "launch_timing": "CUDA events around the batch's last 20 iterations (graph replays)"}}
     if one_by_one:
