@@ -290,3 +290,38 @@ def test_out_of_range_state_is_reported(torch):
     s.set_state(lam, pend)
     assert s.lower_bound() == pytest.approx(lb, rel=1e-6)
     s.close()
+
+
+@pytest.mark.parametrize("which", ["tet", "config1", "config2"])
+def test_instance_that_presolve_solves(torch, which):
+    """Only the ground-truth pairs allowed: presolve fixes every element (no slot, no tile).
+    The bound is the constant at any iteration count, rounding returns the true matching,
+    and d(bound)/d(pair costs) is the closed form of the bound sum_e c_e / c_max over the
+    fixed elements, c_e the mean of e's three pair costs (Sec. 3.1; Eq. D with no BDD)."""
+    inst = getattr(I, which)()
+    d32 = P.pair_distance(inst.FX, inst.FY).astype(np.float32)
+    d = d32.astype(np.float64)
+    allowed = np.zeros((inst.X.nv, inst.Y.nv), bool)
+    allowed[np.arange(inst.X.nv), inst.perm] = True
+    prob = P.build_problem(inst.X.T, inst.Y.T, d, allowed)
+    raw = sum(d[prob.vm[:, v], prob.vn[:, v]] for v in range(3)) / 3.0
+    C, cmax, emax = raw.sum(), raw.max(), int(np.argmax(raw))
+    from paper_2310_08230_gb300.api import Solver
+
+    s = Solver(inst.X.T, inst.Y.T, d32, allowed.astype(np.uint8))
+    assert s.info()["nslots"] == 0 and s.info()["nvars_free"] == 0
+    for iters in (0, 5):
+        s.dual(iters)
+        assert s.lower_bound() == pytest.approx(C / cmax, rel=1e-12)
+    assert s.min_marginals().shape == (0,)
+    x, cost, ok = s.primal()
+    assert ok and np.all(x == 1) and not np.any(prob.residual(x))
+    assert cost == pytest.approx(C / cmax, rel=1e-12)
+    s.record(10, 5)
+    g = s.grad().reshape(inst.X.nv, inst.Y.nv).astype(np.float64)
+    ref = np.zeros_like(g)
+    for v in range(3):
+        np.add.at(ref, (prob.vm[:, v], prob.vn[:, v]), 1.0 / (3.0 * cmax))
+        ref[prob.vm[emax, v], prob.vn[emax, v]] -= C / (3.0 * cmax * cmax)
+    assert np.abs(g - ref).max() <= 1e-5 * np.abs(ref).max()
+    s.close()

@@ -188,3 +188,22 @@ def test_host_compiler_ignores_block_contents(L, tmp_path):
     assert list(z["meta"]) == [info.nvars, info.nrows, info.nvars_free, info.nvars_aux, info.nbdds, info.nnodes]
     assert z["constant"][0] == info.constant
     assert np.array_equal(z["sv"], sv) and np.array_equal(z["sw"], sw) and np.array_equal(z["fx"], fx)
+
+
+@pytest.mark.parametrize("which", ["tet", "config1", "config2"])
+def test_host_compiler_when_presolve_fixes_everything(L, which):
+    """With only the ground-truth vertex pairs allowed, the product space is the true
+    triangle pairs (a degenerate element needs two X corners on one Y vertex), every
+    projection row holds one element, and presolve fixes all of them to 1: no free variable,
+    no BDD, a constant equal to the sum of the normalised costs (Sec. 3.1, Eq. P)."""
+    inst = getattr(I, which)()
+    d32 = P.pair_distance(inst.FX, inst.FY).astype(np.float32)
+    allowed = np.zeros((inst.X.nv, inst.Y.nv), bool)
+    allowed[np.arange(inst.X.nv), inst.perm] = True
+    prob = P.build_problem(inst.X.T, inst.Y.T, d32.astype(np.float64), allowed)
+    fixed, const = P.presolve(prob)
+    assert prob.nvars == inst.X.nt and np.all(fixed == 1)
+    info, sv, sw, fx = _compile(L, inst, allowed, d32, 0, 8)
+    assert info.nvars == prob.nvars and info.nvars_free == 0 and info.nbdds == 0 and info.nslots == 0
+    assert np.array_equal(fx, fixed)
+    assert info.constant == pytest.approx(prob.cost.sum(), rel=1e-12)
