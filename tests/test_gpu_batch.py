@@ -215,3 +215,32 @@ def test_full_batch_sampled_pairs_match_oracle(lib):
         r = PR.round_primal(o, prob, fixed)
         assert r.ok and not np.any(prob.residual(xs[k]))
         assert abs(costs[k] - r.cost) <= 1e-4 * abs(r.cost), (k, costs[k], r.cost)
+
+
+def test_batch_with_a_pair_that_presolve_solves(lib):
+    """A pair whose candidates are its ground truth has no slot and no tile (presolve fixes
+    every element). Between two ordinary pairs in one batch, it keeps its constant bound
+    and its true matching, and the others give their single-pair results bit for bit."""
+    Solver = lib
+    (t, dt, at), (c1, d1, a1) = _pairs()[:2]
+    inst = I.config2()
+    d2 = P.pair_distance(inst.FX, inst.FY).astype(np.float32)
+    a2 = np.zeros((inst.X.nv, inst.Y.nv), np.uint8)
+    a2[np.arange(inst.X.nv), inst.perm] = 1
+    prob2 = P.build_problem(inst.X.T, inst.Y.T, d2.astype(np.float64), a2.astype(bool))
+    const2 = float(prob2.cost.sum())
+    pairs = [(t.X.T, t.Y.T, dt.astype(np.float32), at), (inst.X.T, inst.Y.T, d2, a2),
+             (c1.X.T, c1.Y.T, d1.astype(np.float32), a1)]
+    batch = Solver.batch(pairs, split_chunk=16)
+    assert batch.instance_info(1)["nslots"] == 0
+    batch.dual(40)
+    lbs = batch.lower_bounds()
+    assert lbs[1] == pytest.approx(const2, rel=1e-12)
+    for k in (0, 2):
+        s = Solver(*pairs[k], split_chunk=16)
+        s.dual(40)
+        assert lbs[k] == s.lower_bound()
+        s.close()
+    xs, costs, ok = batch.primal_batch()
+    assert ok.all() and np.all(xs[1] == 1) and costs[1] == pytest.approx(const2, rel=1e-12)
+    batch.close()
