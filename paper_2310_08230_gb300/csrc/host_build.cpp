@@ -449,6 +449,187 @@ void enumerate(const MeshTopo& X, const MeshTopo& Y, const Allowed& A, int threa
     });
 }
 
+// The same product space by bit-set algebra, for candidate masks that are dense enough: per X
+// vertex m, TB[m][c] has bit s set iff (m, corner c of Y triangle s) is allowed, and EB[m][j]
+// bit e iff (m, end j of Y edge e) is allowed (built from the candidate rows, 12 bits per
+// candidate on average). An element is allowed iff its three corner pairs are, so each type
+// is the AND of three such rows, one word at a time, and reading the set bits in ascending
+// order per word, then rotation or pattern ascending, gives the canonical order that the
+// sorted codes of enumerate() give.
+bool dense_enumeration(const MeshTopo& X, const MeshTopo& Y, const Allowed& A) {
+    if (const char* e = std::getenv("DISCO_HOST_ENUM")) return std::strcmp(e, "sparse") != 0 && !A.full;
+    if (A.full) return false;
+    const double wt = double((Y.nt + 63) / 64), we = double((int64_t(Y.edges.size()) + 63) / 64);
+    if (double(X.nv) * (3 * wt + 2 * we) * 8.0 > double(int64_t(1) << 30)) return false;  // bit sets above 1 GB
+    const double dense = double(X.nt) * (9 * wt + 18 * we + 3 * A.words) + double(X.edges.size()) * 18 * wt +
+                         double(X.nv) * 3 * wt;
+    const double cand = double(A.row.ptr[size_t(X.nv)]) / double(std::max(1, X.nv));
+    const double sparse = cand * (12.0 * X.nt + 24.0 * double(X.edges.size()) + 6.0 * X.nv);
+    return dense < 4.0 * sparse;  // a word AND is far cheaper than a random bit lookup and branch
+}
+
+void enumerate_dense(const MeshTopo& X, const MeshTopo& Y, const Allowed& A, int threads, Elems* out) {
+    const int32_t* TX = X.T;
+    const int32_t* TY = Y.T;
+    const int64_t WT = (Y.nt + 63) / 64, WE = (int64_t(Y.edges.size()) + 63) / 64, WV = A.words;
+    pod_vector<uint64_t> TB(static_cast<size_t>(int64_t(X.nv) * 3 * WT)), EB(static_cast<size_t>(int64_t(X.nv) * 2 * WE));
+    parallel_chunks(X.nv, threads, [&](int, int64_t lo, int64_t hi) {
+        for (int64_t m = lo; m < hi; ++m) {
+            uint64_t* tb = TB.data() + m * 3 * WT;
+            uint64_t* eb = EB.data() + m * 2 * WE;
+            std::fill(tb, tb + 3 * WT, uint64_t(0));
+            std::fill(eb, eb + 2 * WE, uint64_t(0));
+            A.row.for_each(int(m), [&](int n) {
+                Y.tri_at.for_each(n, [&](std::pair<int, int> sc) {
+                    tb[sc.second * WT + (sc.first >> 6)] |= uint64_t(1) << (sc.first & 63);
+                });
+                Y.edge_at.for_each(n, [&](int e) {
+                    eb[(Y.edges[size_t(e)].first == n ? 0 : 1) * WE + (e >> 6)] |= uint64_t(1) << (e & 63);
+                });
+            });
+        }
+    });
+    auto tb_row = [&](int m, int c) { return TB.data() + (int64_t(m) * 3 + c) * WT; };
+    auto eb_row = [&](int m, int j) { return EB.data() + (int64_t(m) * 2 + j) * WE; };
+    const int count[5] = {X.nt, X.nt, int(X.edges.size()), X.nt, X.nv};
+    std::vector<Job> jobs;
+    for (int ty = 0; ty < 5; ++ty) {
+        const int nch = std::max(1, std::min(threads * 4, count[ty] / 16 + 1));
+        for (int c = 0; c < nch; ++c)
+            jobs.push_back(Job{ty, int(int64_t(count[ty]) * c / nch), int(int64_t(count[ty]) * (c + 1) / nch)});
+    }
+    run_jobs(jobs, threads, out, [&](const Job& j, Elems* o) {
+        std::vector<uint64_t> x;  // the AND words of each rotation / pattern of one X element
+        // K rows of W words in x: the elements in (bit, row) order, handed to emit(row, bit index)
+        auto for_bits = [&](int K, int64_t W, auto&& emit) {
+            for (int64_t w = 0; w < W; ++w) {
+                uint64_t u = 0;
+                for (int r = 0; r < K; ++r) u |= x[size_t(r * W + w)];
+                for (; u; u &= u - 1) {
+                    const int b = __builtin_ctzll(u);
+                    for (int r = 0; r < K; ++r)
+                        if ((x[size_t(r * W + w)] >> b) & 1u) emit(r, int(w * 64 + b));
+                }
+            }
+        };
+        auto and3 = [&](int r, int64_t W, const uint64_t* p, const uint64_t* q, const uint64_t* u) {
+            size_t k = 0;
+            uint64_t* d = x.data() + r * W;
+            for (int64_t w = 0; w < W; ++w) {
+                d[w] = p[w] & q[w] & u[w];
+                k += size_t(__builtin_popcountll(d[w]));
+            }
+            return k;
+        };
+        switch (j.type) {
+            case 0: {  // X triangle t, Y triangle s, rotation r: corner v -> (t_v, s_{(v+r)%3})
+                x.resize(size_t(3 * WT));
+                for (int t = j.lo; t < j.hi; ++t) {
+                    const int m0 = TX[3 * t], m1 = TX[3 * t + 1], m2 = TX[3 * t + 2];
+                    size_t k = 0;
+                    for (int r = 0; r < 3; ++r)
+                        k += and3(r, WT, tb_row(m0, r), tb_row(m1, (r + 1) % 3), tb_row(m2, (r + 2) % 3));
+                    const size_t b = o->grow(k, 0, t);
+                    int32_t* om = o->m.data() + 3 * b;
+                    int32_t* on = o->n.data() + 3 * b;
+                    int32_t* oy = o->ye.data() + b;
+                    for_bits(3, WT, [&](int r, int s) {
+                        om[0] = m0; om[1] = m1; om[2] = m2;
+                        on[0] = TY[3 * s + r]; on[1] = TY[3 * s + (r + 1) % 3]; on[2] = TY[3 * s + (r + 2) % 3];
+                        *oy++ = s;
+                        om += 3;
+                        on += 3;
+                    });
+                }
+                break;
+            }
+            case 1: {  // X triangle t, Y edge e = (a < b), pattern p: corner v -> (t_v, pattern symbol v)
+                x.resize(size_t(6 * WE));
+                for (int t = j.lo; t < j.hi; ++t) {
+                    const int m[3] = {TX[3 * t], TX[3 * t + 1], TX[3 * t + 2]};
+                    size_t k = 0;
+                    for (int p = 0; p < 6; ++p)
+                        k += and3(p, WE, eb_row(m[0], kEdgePattern[p][0]), eb_row(m[1], kEdgePattern[p][1]),
+                                  eb_row(m[2], kEdgePattern[p][2]));
+                    const size_t b = o->grow(k, 1, t);
+                    int32_t* om = o->m.data() + 3 * b;
+                    int32_t* on = o->n.data() + 3 * b;
+                    int32_t* oy = o->ye.data() + b;
+                    for_bits(6, WE, [&](int p, int e) {
+                        const int ab[2] = {Y.edges[size_t(e)].first, Y.edges[size_t(e)].second};
+                        om[0] = m[0]; om[1] = m[1]; om[2] = m[2];
+                        on[0] = ab[kEdgePattern[p][0]]; on[1] = ab[kEdgePattern[p][1]]; on[2] = ab[kEdgePattern[p][2]];
+                        *oy++ = e;
+                        om += 3;
+                        on += 3;
+                    });
+                }
+                break;
+            }
+            case 2: {  // X edge e = (a < b), Y triangle s, pattern p: corner v -> (pattern symbol v, s_v)
+                x.resize(size_t(6 * WT));
+                for (int e = j.lo; e < j.hi; ++e) {
+                    const int ab[2] = {X.edges[size_t(e)].first, X.edges[size_t(e)].second};
+                    size_t k = 0;
+                    for (int p = 0; p < 6; ++p)
+                        k += and3(p, WT, tb_row(ab[kEdgePattern[p][0]], 0), tb_row(ab[kEdgePattern[p][1]], 1),
+                                  tb_row(ab[kEdgePattern[p][2]], 2));
+                    const size_t b = o->grow(k, 2, e);
+                    int32_t* om = o->m.data() + 3 * b;
+                    int32_t* on = o->n.data() + 3 * b;
+                    int32_t* oy = o->ye.data() + b;
+                    for_bits(6, WT, [&](int p, int s) {
+                        om[0] = ab[kEdgePattern[p][0]]; om[1] = ab[kEdgePattern[p][1]]; om[2] = ab[kEdgePattern[p][2]];
+                        on[0] = TY[3 * s]; on[1] = TY[3 * s + 1]; on[2] = TY[3 * s + 2];
+                        *oy++ = s;
+                        om += 3;
+                        on += 3;
+                    });
+                }
+                break;
+            }
+            case 3: {  // X triangle t, Y vertex n
+                x.resize(size_t(WV));
+                for (int t = j.lo; t < j.hi; ++t) {
+                    const int m0 = TX[3 * t], m1 = TX[3 * t + 1], m2 = TX[3 * t + 2];
+                    const size_t k = and3(0, WV, A.bits.data() + size_t(m0) * WV, A.bits.data() + size_t(m1) * WV,
+                                          A.bits.data() + size_t(m2) * WV);
+                    const size_t b = o->grow(k, 3, t);
+                    int32_t* om = o->m.data() + 3 * b;
+                    int32_t* on = o->n.data() + 3 * b;
+                    int32_t* oy = o->ye.data() + b;
+                    for_bits(1, WV, [&](int, int n) {
+                        om[0] = m0; om[1] = m1; om[2] = m2;
+                        on[0] = n; on[1] = n; on[2] = n;
+                        *oy++ = n;
+                        om += 3;
+                        on += 3;
+                    });
+                }
+                break;
+            }
+            case 4: {  // X vertex m, Y triangle s
+                x.resize(size_t(WT));
+                for (int mv = j.lo; mv < j.hi; ++mv) {
+                    const size_t k = and3(0, WT, tb_row(mv, 0), tb_row(mv, 1), tb_row(mv, 2));
+                    const size_t b = o->grow(k, 4, mv);
+                    int32_t* om = o->m.data() + 3 * b;
+                    int32_t* on = o->n.data() + 3 * b;
+                    int32_t* oy = o->ye.data() + b;
+                    for_bits(1, WT, [&](int, int s) {
+                        om[0] = mv; om[1] = mv; om[2] = mv;
+                        on[0] = TY[3 * s]; on[1] = TY[3 * s + 1]; on[2] = TY[3 * s + 2];
+                        *oy++ = s;
+                        om += 3;
+                        on += 3;
+                    });
+                }
+                break;
+            }
+        }
+    });
+}
+
 // One boundary edge of one element: its smaller product vertex (m, n) is implied by the
 // bucket (m) and `lo_n`; `hi` is the larger product vertex m' * nvy + n'; `id` packs the
 // entry 3 * element + corner and the direction bit.
@@ -572,7 +753,10 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     tr.mark("candidate rows");
     // ---- product space
     Elems E;
-    enumerate(X, Y, A, threads, &E);
+    if (dense_enumeration(X, Y, A))
+        enumerate_dense(X, Y, A, threads, &E);
+    else
+        enumerate(X, Y, A, threads, &E);
     const int64_t nv = int64_t(E.size());
     if (nv == 0) { *err = "empty product space"; return DISCO_ERR_INFEASIBLE; }
     if (nv >= (int64_t(1) << 31)) { *err = "product space too large"; return DISCO_ERR_INVALID_ARG; }
@@ -701,8 +885,8 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         std::vector<int32_t> pos_of(static_cast<size_t>(nvy), -1);
         std::vector<int32_t> rank_of(static_cast<size_t>(nvx), -1);
         std::vector<int32_t> ring;
-        std::vector<int64_t> cnt;
-        std::vector<int32_t> key;
+        std::vector<int64_t> cnt, cnt2;
+        std::vector<int32_t> key, key2, ny;
         std::vector<EdgeEntry> tmp;
         {
             for (int64_t m = int64_t(nvx) * c / nbc; m < int64_t(nvx) * (c + 1) / nbc; ++m) {
@@ -718,6 +902,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                 const int R = int(ring.size());
                 for (int i = 0; i < R; ++i) rank_of[ring[i]] = i;
                 key.resize(size_t(nb));
+                ny.resize(size_t(nb));
                 bool ok = true;
                 for (int64_t e = b0; e < b1 && ok; ++e) {
                     const int32_t p = pos_of[ent[e].lo_n];
@@ -725,35 +910,28 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                     const int32_t q = rank_of[mh];
                     ok = p >= 0 && p < ncand && cand[p] == int32_t(ent[e].lo_n) && q >= 0 && q < R && ring[q] == mh;
                     key[e - b0] = p * R + q;
+                    ny[e - b0] = int32_t(ent[e].hi - uint32_t(mh) * uint32_t(nvy));  // n' of the larger vertex
                 }
                 if (!ok) {
                     std::sort(ent.data() + b0, ent.data() + b1);
                 } else {
+                    // two stable counting sorts: by n' (inside a key group, hi orders by n'),
+                    // then by the key; entries of one product edge keep their entry order
                     const int nk = ncand * R;
-                    cnt.assign(size_t(nk) + 1, 0);
-                    for (int64_t e = 0; e < nb; ++e) ++cnt[size_t(key[e]) + 1];
-                    for (int i = 0; i < nk; ++i) cnt[i + 1] += cnt[i];
+                    cnt2.assign(size_t(nvy) + 1, 0);
+                    for (int64_t e = 0; e < nb; ++e) ++cnt2[size_t(ny[e]) + 1];
+                    for (int i = 0; i < nvy; ++i) cnt2[i + 1] += cnt2[i];
                     tmp.resize(size_t(nb));
-                    for (int64_t e = 0; e < nb; ++e) tmp[size_t(cnt[key[e]]++)] = ent[b0 + e];
-                    // cnt[i] is now the end of key group i: order by hi (n' here) by insertion
-                    int64_t g0 = 0;
-                    for (int i = 0; i < nk; ++i) {
-                        const int64_t g1 = cnt[i];
-                        EdgeEntry* g = tmp.data() + g0;
-                        const int64_t ng = g1 - g0;
-                        if (ng <= 64) {
-                            for (int64_t x = 1; x < ng; ++x) {
-                                const EdgeEntry v = g[x];
-                                int64_t y = x;
-                                for (; y > 0 && g[y - 1].hi > v.hi; --y) g[y] = g[y - 1];
-                                g[y] = v;
-                            }
-                        } else {
-                            std::stable_sort(g, g + ng, [](const EdgeEntry& a, const EdgeEntry& b) { return a.hi < b.hi; });
-                        }
-                        g0 = g1;
+                    key2.resize(size_t(nb));
+                    for (int64_t e = 0; e < nb; ++e) {
+                        const int64_t o = cnt2[size_t(ny[e])]++;
+                        tmp[size_t(o)] = ent[b0 + e];
+                        key2[size_t(o)] = key[e];
                     }
-                    std::copy(tmp.begin(), tmp.end(), ent.data() + b0);
+                    cnt.assign(size_t(nk) + 1, 0);
+                    for (int64_t e = 0; e < nb; ++e) ++cnt[size_t(key2[e]) + 1];
+                    for (int i = 0; i < nk; ++i) cnt[i + 1] += cnt[i];
+                    for (int64_t e = 0; e < nb; ++e) ent[b0 + cnt[size_t(key2[e])]++] = tmp[size_t(e)];
                 }
                 for (int i = 0; i < R; ++i) rank_of[ring[i]] = -1;
                 int64_t r = 0;
@@ -763,6 +941,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
             }
         }
     });
+    tr.mark("closedness sort");
     for (int m = 0; m < nvx; ++m) brows[m + 1] += brows[m];
     const int64_t n_closed = brows[nvx];
     P->n_closed = n_closed;
@@ -793,6 +972,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         int32_t res, np, nn, queued;
     };
     pod_vector<RowState> rs(static_cast<size_t>(n_closed + X.nt + Y.nt));
+    tr.mark("closedness arrays");
     parallel_chunks(nvx, nth * 4, [&](int, int64_t lo, int64_t hi) {
         for (int64_t m = lo; m < hi; ++m) {
             int64_t r = brows[m] - 1;
@@ -994,7 +1174,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         // closedness rows of the variables still free (only the incremental rounds use them)
         parallel_tasks(nrc, nth, [&](int64_t c) {
             for (int64_t r = row_cut[size_t(c)]; r < std::min(row_cut[size_t(c) + 1], n_closed); ++r)
-                for (int64_t e = P->row_ptr[r]; e < P->row_ptr[r + 1]; ++e) {
+                for (int64_t e = P->row_ptr[r]; e < P->row_ptr[r + 1] && rs[r].np + rs[r].nn > 0; ++e) {
                     const int32_t v = P->row_var[e];
                     if (P->fixed[v] < 0)
                         er[size_t(v)].closed[row_ent[e]] = uint32_t(r) << 1 | (P->row_coef[e] > 0 ? 1u : 0u);
@@ -1197,6 +1377,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                 C.nodes += w;
             };
             for (int64_t r = r0; r < r1 && !C.rc; ++r) {
+                if (rs[r].np + rs[r].nn == 0) continue;  // presolve left no free entry (its counts are exact)
                 fv.clear();
                 fc.clear();
                 fr.clear();

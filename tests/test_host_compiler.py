@@ -190,6 +190,43 @@ def test_host_compiler_ignores_block_contents(L, tmp_path):
     assert np.array_equal(z["sv"], sv) and np.array_equal(z["sw"], sw) and np.array_equal(z["fx"], fx)
 
 
+def _batch_pair(k):
+    return I.config4(64)[k]
+
+
+@pytest.mark.parametrize("which", ["config1-top4", "config2", "batch5", "batch17", "truth-only"])
+def test_dense_and_sparse_enumeration_give_the_same_plan(L, monkeypatch, which):
+    """The product space is enumerated either from the candidate rows (a bit lookup per
+    candidate corner pair) or by AND-ing per-vertex bit sets over Y triangles and edges; the
+    compiler picks one by an operation count. Both must give the same elements in the same
+    canonical order: the plan (fixings per element, every segment's variables and widths,
+    constant) is compared bit for bit with each path forced (DISCO_HOST_ENUM)."""
+    if which == "config1-top4":
+        inst = I.config1()
+        k = 4
+    elif which.startswith("batch"):
+        inst = _batch_pair(int(which[5:]))
+        k = inst.topk
+    else:
+        inst = I.config2()
+        k = inst.topk
+    d32 = P.pair_distance(inst.FX, inst.FY).astype(np.float32)
+    if which == "truth-only":
+        allowed = np.zeros((inst.X.nv, inst.Y.nv), bool)
+        allowed[np.arange(inst.X.nv), inst.perm] = True
+    else:
+        allowed = P.candidate_pairs(d32.astype(np.float64), k, inst.X.T, inst.Y.T)
+    plans = {}
+    for mode in ("sparse", "dense"):
+        monkeypatch.setenv("DISCO_HOST_ENUM", mode)
+        plans[mode] = _compile(L, inst, allowed, d32, 32, 8)
+    (ia, sva, swa, fxa), (ib, svb, swb, fxb) = plans["sparse"], plans["dense"]
+    assert (ia.nvars, ia.nrows, ia.nvars_free, ia.nvars_aux, ia.nbdds, ia.nnodes) == \
+        (ib.nvars, ib.nrows, ib.nvars_free, ib.nvars_aux, ib.nbdds, ib.nnodes)
+    assert ia.constant == ib.constant
+    assert np.array_equal(fxa, fxb) and np.array_equal(sva, svb) and np.array_equal(swa, swb)
+
+
 @pytest.mark.parametrize("which", ["tet", "config1", "config2"])
 def test_host_compiler_when_presolve_fixes_everything(L, which):
     """With only the ground-truth vertex pairs allowed, the product space is the true
