@@ -945,6 +945,8 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
     for (int m = 0; m < nvx; ++m) brows[m + 1] += brows[m];
     const int64_t n_closed = brows[nvx];
     P->n_closed = n_closed;
+    // room for the projection rows and the end mark, so that appending them moves nothing
+    P->row_ptr.reserve(size_t(n_closed) + size_t(X.nt) + size_t(Y.nt) + 1);
     P->row_ptr.resize(size_t(n_closed));  // every row start is written below
     // projection entries: elements whose X (Y) side is a triangle; all rows are sized once
     std::vector<int64_t> nproj_part(size_t(nth), 0);
@@ -991,6 +993,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         }
     });
     pod_vector<EdgeEntry>().swap(ent);
+    P->rhs.reserve(size_t(n_closed) + size_t(X.nt) + size_t(Y.nt));
     P->rhs.assign(size_t(n_closed), 0);
 
     tr.mark("closedness rows");
@@ -1034,14 +1037,20 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
             for (int side = 0; side < 2; ++side) {
                 const int t = ab[side];
                 er[size_t(i)].proj[side] = t >= 0 ? int32_t(row0 + t) : -1;
-                if (t < 0) continue;
-                const int64_t pos = o[t]++;
-                P->row_var[size_t(pos)] = int32_t(i);
-                P->row_coef[size_t(pos)] = 1;
-                row_ent[size_t(pos)] = 3 + side;
+                if (t >= 0) P->row_var[size_t(o[t]++)] = int32_t(i);
             }
         }
     });
+    // coefficients (all +1) and entry codes (3 + side) of the projection entries, in order
+    {
+        const int64_t ybeg = P->row_ptr[size_t(row0 + ntx)];
+        parallel_chunks(proj_end - ne, nth, [&](int, int64_t lo, int64_t hi) {
+            for (int64_t k = ne + lo; k < ne + hi; ++k) {
+                P->row_coef[size_t(k)] = 1;
+                row_ent[size_t(k)] = k < ybeg ? 3 : 4;
+            }
+        });
+    }
     P->rhs.resize(P->rhs.size() + size_t(ntri), 1);
     P->n_projx = X.nt;
     P->n_projy = Y.nt;
