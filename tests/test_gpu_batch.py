@@ -244,3 +244,28 @@ def test_batch_with_a_pair_that_presolve_solves(lib):
     xs, costs, ok = batch.primal_batch()
     assert ok.all() and np.all(xs[1] == 1) and costs[1] == pytest.approx(const2, rel=1e-12)
     batch.close()
+
+
+@pytest.mark.parametrize("groups", [1, 2, 3])
+def test_pipelined_groups_match_one_batch(lib, groups):
+    """solve_batch_pipelined splits the pairs into batched stores on their own streams, so
+    that the host compiles one store while the GPU iterates on the previous one. Every
+    pair's bound, matching and cost must be the one-batch result bit for bit, whatever the
+    grouping (each pair's arithmetic and bound sum are independent of its store)."""
+    Solver = lib
+    from paper_2310_08230_gb300.api import solve_batch_pipelined
+
+    pairs = _pairs()
+    args = [(i.X.T, i.Y.T, d.astype(np.float32), a) for i, d, a in pairs]
+    iters = 60
+    batch = Solver.batch(args, split_chunk=16)
+    batch.dual(iters)
+    lbs = batch.lower_bounds()
+    xs, costs, ok = batch.primal_batch()
+    batch.close()
+    out = solve_batch_pipelined(args, iters, groups=groups, split_chunk=16)
+    assert [r["lower_bound"] for r in out] == list(lbs)
+    assert [r["cost"] for r in out] == list(costs)
+    assert [r["feasible"] for r in out] == list(ok)
+    for r, x in zip(out, xs):
+        np.testing.assert_array_equal(r["x"], x)
