@@ -430,7 +430,7 @@ def differentiated(torch, n_pairs: int = 8, iters: int = 50, every: int = 10) ->
 
 
 def batched_vs_single(torch, iters: int = 300, n_pairs: int = 64, split_chunk: int = 32,
-                      one_by_one: bool = True, pipeline_groups=(2, 3)) -> dict:
+                      one_by_one: bool = True, pipeline_groups=(2, 3, 4)) -> dict:
     """64 uneven pairs: one batched handle against the same pairs solved one after another.
 
     Both sides run the whole path per pair (pair costs, candidates, build, `iters` dual
