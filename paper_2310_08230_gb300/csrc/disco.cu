@@ -1134,15 +1134,19 @@ int build_handle(int32_t n, const disco_mesh* X, const disco_mesh* Y, const floa
     std::vector<int32_t> order(static_cast<size_t>(n));
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return est[a] > est[b]; });
-    // a pair holding more than half a thread's share of the work (1/hw of the total) would
-    // finish last on one thread, so it gets one thread per half share, up to all of them, and
-    // at least an even split of the threads when there are fewer pairs than threads (the
-    // largest pairs start first; the plan does not depend on the thread count)
+    // threads per pair (the plan does not depend on them; the largest pairs start first):
+    // * no more pairs than threads: the threads in proportion to each pair's share of the
+    //   work (1/hw of the total per thread), at least one, so that a large pair does not
+    //   finish last on an even split;
+    // * more pairs than threads: a pair holding more than half a thread's share would finish
+    //   last on one thread, so it gets one thread per half share, up to 4.
+    (void)inner;
     const double total = std::max<double>(1.0, double(std::accumulate(est.begin(), est.end(), int64_t(0))));
     parallel_chunks(n, n, [&](int c, int64_t, int64_t) {
         const int32_t i = order[c];
         const double share = double(est[i]) * hw / total;
-        const int th = std::max(n <= hw ? inner : 1, std::min(hw, int(std::ceil(2.0 * share - 1e-9))));
+        const int th = n <= hw ? std::max(1, std::min(hw, int(std::lround(share))))
+                               : std::max(1, std::min(4, int(std::ceil(2.0 * share - 1e-9))));
         rcs[i] = build_plan(MeshIn{X[i].nv, X[i].nt, X[i].T, X[i].V}, MeshIn{Y[i].nv, Y[i].nt, Y[i].T, Y[i].V}, hd[i].data(),
                             (allowed && allowed[i]) ? ha[i].data() : nullptr, o.split_chunk, o.split_max_segments,
                             th, &h->plans[i], &errs[i], o.normalize_costs != 0, o.cost_model);
