@@ -194,7 +194,8 @@ def _batch_pair(k):
     return I.config4(64)[k]
 
 
-@pytest.mark.parametrize("which", ["config1-top4", "config2", "batch5", "batch17", "truth-only"])
+@pytest.mark.parametrize("which", ["config1-top4", "config2", "batch5", "batch17", "truth-only", "bipyramid12-random",
+                                   "bipyramid16-random", "config2-random"])
 def test_dense_and_sparse_enumeration_give_the_same_plan(L, monkeypatch, which):
     """The product space is enumerated either from the candidate rows (a bit lookup per
     candidate corner pair) or by AND-ing per-vertex bit sets over Y triangles and edges; the
@@ -210,9 +211,17 @@ def test_dense_and_sparse_enumeration_give_the_same_plan(L, monkeypatch, which):
     else:
         inst = I.config2()
         k = inst.topk
+    if which.startswith("bipyramid"):
+        inst = I.bipyramid_pair(int(which[9:11]))  # apexes of valence 12 / 16
     d32 = P.pair_distance(inst.FX, inst.FY).astype(np.float32)
     if which == "truth-only":
         allowed = np.zeros((inst.X.nv, inst.Y.nv), bool)
+        allowed[np.arange(inst.X.nv), inst.perm] = True
+    elif which.endswith("-random"):
+        # irregular masks: each pair kept with probability 0.6 (bipyramids) or 0.3, plus the
+        # ground truth so that every triangle keeps an element
+        rng = np.random.Generator(np.random.PCG64(len(which)))
+        allowed = rng.random((inst.X.nv, inst.Y.nv)) < (0.6 if which.startswith("bipyramid") else 0.3)
         allowed[np.arange(inst.X.nv), inst.perm] = True
     else:
         allowed = P.candidate_pairs(d32.astype(np.float64), k, inst.X.T, inst.Y.T)
