@@ -439,7 +439,7 @@ def batched_vs_single(torch, iters: int = 300, n_pairs: int = 64, split_chunk: i
     timed on their own (CUDA events, graph replays of the half-pass launches): with 1.8 GB of
     BDD tables, far beyond L2, that is the batch's HBM roofline point."""
     from paper_2310_08230_gb300 import _lib as L
-    from paper_2310_08230_gb300.api import _mesh, default_opts
+    from paper_2310_08230_gb300.api import _mesh, balanced_groups, default_opts
     from synth import instances as I
 
     lib = L.lib()
@@ -518,13 +518,7 @@ def batched_vs_single(torch, iters: int = 300, n_pairs: int = 64, split_chunk: i
         for k in range(n_pairs):
             costs(k)
         torch.cuda.synchronize()  # the costs (on `stream`) are complete before any build reads them
-        w = [insts[k].X.nt * insts[k].topk for k in range(n_pairs)]
-        load, members = [0] * G, [[] for _ in range(G)]
-        for k in sorted(range(n_pairs), key=lambda k: -w[k]):
-            g = min(range(G), key=lambda g: load[g])
-            members[g].append(k)
-            load[g] += w[k]
-        members = [sorted(m) for m in members if m]
+        members = balanced_groups([insts[k].X.nt * insts[k].topk for k in range(n_pairs)], G)
         hs = []
         for g, m in enumerate(members):
             MX = (L.disco_mesh * len(m))(*[meshes[k][0][0] for k in m])

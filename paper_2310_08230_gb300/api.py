@@ -125,6 +125,21 @@ def solve_coarse_to_fine(levels, costs, rings: int = 1, iters: int = 100, **opts
     return out
 
 
+def balanced_groups(weights, groups: int) -> list[list[int]]:
+    """Indices 0 .. n-1 split into at most ``groups`` groups of about equal total weight:
+    heaviest first onto the lightest group (ties to the lower group), each group in
+    ascending index order, empty groups dropped."""
+    n = len(weights)
+    g = max(1, min(int(groups), n))
+    load = [0.0] * g
+    members = [[] for _ in range(g)]
+    for i in sorted(range(n), key=lambda i: -weights[i]):
+        k = min(range(g), key=lambda k: load[k])
+        members[k].append(i)
+        load[k] += weights[i]
+    return [sorted(m) for m in members if m]
+
+
 def solve_batch_pipelined(pairs, iters: int, groups: int = 2, weights=None, **opts) -> list[dict]:
     """Many pairs as ``groups`` batched handles, pipelined between host and GPU.
 
@@ -142,15 +157,8 @@ def solve_batch_pipelined(pairs, iters: int, groups: int = 2, weights=None, **op
     torch = _torch()
     opts.setdefault("autotune", 0)
     n = len(pairs)
-    g = max(1, min(int(groups), n))
     w = [float(np.prod(p[2].shape)) for p in pairs] if weights is None else [float(x) for x in weights]
-    load = [0.0] * g
-    members = [[] for _ in range(g)]
-    for i in sorted(range(n), key=lambda i: -w[i]):
-        k = min(range(g), key=lambda k: load[k])
-        members[k].append(i)
-        load[k] += w[i]
-    members = [sorted(m) for m in members if m]
+    members = balanced_groups(w, groups)
     streams = [torch.cuda.Stream() for _ in members]
     torch.cuda.synchronize()  # inputs computed on other streams are complete
     solvers = []
