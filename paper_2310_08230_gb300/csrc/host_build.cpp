@@ -974,6 +974,10 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         int32_t res, np, nn, queued;
     };
     pod_vector<RowState> rs(static_cast<size_t>(n_closed + X.nt + Y.nt));
+    // right-hand sides: 0 for the closedness rows (written by the fill below, in parallel),
+    // 1 for the projection rows appended later
+    P->rhs.reserve(size_t(n_closed) + size_t(X.nt) + size_t(Y.nt));
+    P->rhs.resize(size_t(n_closed));
     tr.mark("closedness arrays");
     parallel_chunks(nvx, nth * 4, [&](int, int64_t lo, int64_t hi) {
         for (int64_t m = lo; m < hi; ++m) {
@@ -982,6 +986,7 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
                 if (e == bstart[m] || !ent[e].same_edge(ent[e - 1])) {
                     P->row_ptr[++r] = e;
                     rs[r] = RowState{0, 0, 0, 0};
+                    P->rhs[size_t(r)] = 0;
                 }
                 const uint32_t id = ent[e].id >> 1;
                 const bool neg = ent[e].id & 1u;
@@ -993,8 +998,6 @@ int build_plan(const MeshIn& Xin, const MeshIn& Yin, const float* d, const uint8
         }
     });
     pod_vector<EdgeEntry>().swap(ent);
-    P->rhs.reserve(size_t(n_closed) + size_t(X.nt) + size_t(Y.nt));
-    P->rhs.assign(size_t(n_closed), 0);
 
     tr.mark("closedness rows");
     // ---- projection rows (counting sort keeps the element order inside a row): one row per X

@@ -237,7 +237,7 @@ struct Plan {
     pod_vector<int64_t> row_ptr;        // rows: closedness, X projection, Y projection
     pod_vector<int32_t> row_var;
     pod_vector<int8_t> row_coef;
-    std::vector<int32_t> rhs;
+    pod_vector<int32_t> rhs;
     // ---- presolve
     std::vector<int8_t> fixed;           // per variable: -1 free, 0 / 1 fixed
     double constant = 0.0;               // sum of c over variables fixed to 1
